@@ -1,0 +1,247 @@
+"""Seeded synthetic inputs: immersed-body meshes and the lattice cases.
+
+This module builds inputs only (meshes, initial fields, parameters).  It
+holds none of the method's arithmetic and imports neither the CUDA library
+nor the oracle, so both sides can take their inputs from it.
+
+The paper's own cases (a sphere settling in a walled box, capsules and
+spheroids between two counter-moving walls; Sec. 3.2-3.5) depend on
+experimental and literature data that are not available; the cases below
+keep their shapes: lattice sizes, relaxation times, surface meshes with
+three to five markers per cell, shear rates and density ratios.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+PERIODIC, WALL = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP16_DEV, PREC_BF16_DEV = 0, 1, 2, 3
+
+
+# ---------------------------------------------------------------------------------------
+# Meshes
+# ---------------------------------------------------------------------------------------
+
+def _icosahedron():
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array([[-1, p, 0], [1, p, 0], [-1, -p, 0], [1, -p, 0],
+                  [0, -1, p], [0, 1, p], [0, -1, -p], [0, 1, -p],
+                  [p, 0, -1], [p, 0, 1], [-p, 0, -1], [-p, 0, 1]], dtype=np.float64)
+    f = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+                  [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+                  [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+                  [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v, f
+
+
+def _orient_outward(v, f):
+    """Make every triangle counter-clockwise seen from outside a star-shaped body."""
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    n = np.cross(b - a, c - a)
+    cen = (a + b + c) / 3.0
+    flip = np.einsum("ij,ij->i", n, cen - v.mean(axis=0)) < 0
+    f = f.copy()
+    f[flip] = f[flip][:, [0, 2, 1]]
+    return f
+
+
+def icosphere(level: int, radius: float = 1.0, center=(0.0, 0.0, 0.0), axes=None):
+    """Unit icosahedron subdivided `level` times (midpoints projected to the
+    sphere), scaled to `radius` (or to semi-axes `axes`) and moved to `center`.
+    V = 10*4^L + 2 vertices, F = 20*4^L triangles, outward orientation."""
+    v, f = _icosahedron()
+    verts = [tuple(x) for x in v]
+    faces = [tuple(x) for x in f]
+    for _ in range(level):
+        cache = {}
+        new_faces = []
+
+        def mid(i, j):
+            key = (min(i, j), max(i, j))
+            if key not in cache:
+                m = (np.array(verts[i]) + np.array(verts[j])) / 2.0
+                m /= np.linalg.norm(m)
+                verts.append(tuple(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        for (a, b, c) in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new_faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = new_faces
+    V = np.array(verts, dtype=np.float64)
+    F = np.array(faces, dtype=np.int64)
+    F = _orient_outward(V, F)
+    if axes is None:
+        V = V * float(radius)
+    else:
+        V = V * np.asarray(axes, dtype=np.float64)[None, :]
+    V = V + np.asarray(center, dtype=np.float64)[None, :]
+    return np.ascontiguousarray(V), np.ascontiguousarray(F.astype(np.int32))
+
+
+def cube_mesh(side: float = 1.0, center=(0.0, 0.0, 0.0)):
+    """Closed cube of 8 vertices and 12 outward triangles."""
+    h = side / 2.0
+    v = np.array([[x, y, z] for z in (-h, h) for y in (-h, h) for x in (-h, h)], dtype=np.float64)
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5)]
+    f = []
+    for a, b, c, d in quads:
+        f += [(a, b, c), (a, c, d)]
+    f = _orient_outward(v, np.array(f, dtype=np.int64))
+    return v + np.asarray(center)[None, :], f.astype(np.int32)
+
+
+def perturb(verts, amplitude: float, seed: int):
+    rng = np.random.default_rng(seed)
+    return verts + amplitude * rng.standard_normal(verts.shape)
+
+
+# ---------------------------------------------------------------------------------------
+# Parameter helpers (inputs derived from dimensionless groups of the paper)
+# ---------------------------------------------------------------------------------------
+
+def viscosity(tau: float) -> float:
+    """Lattice kinematic viscosity for relaxation time tau (c_s^2 = 1/3)."""
+    return (tau - 0.5) / 3.0
+
+
+def ks0_from_capillary(Ca: float, tau: float, shear_rate: float, radius: float, rho: float = 1.0) -> float:
+    """Global membrane stiffness from the capillary number Ca = rho nu u_ref / k_s0
+    with u_ref = shear rate x radius (Sec. 2.3 and Sec. 3.4)."""
+    return rho * viscosity(tau) * shear_rate * radius / Ca
+
+
+def settling_gravity(Re: float, gamma: float, d: float, tau: float) -> float:
+    """Gravity for a terminal Reynolds number Re = d u_inf / nu at density ratio
+    gamma, from Abraham's drag law C_d = C0 (1 + delta0/sqrt(Re))^2 with
+    C0 delta0^2 = 24, delta0 = 9.06, and u_inf^2 = 4 g d (gamma - 1) / (3 C_d)
+    (Sec. 3.2)."""
+    delta0 = 9.06
+    C0 = 24.0 / delta0 ** 2
+    Cd = C0 * (1.0 + delta0 / math.sqrt(Re)) ** 2
+    u_inf = Re * viscosity(tau) / d
+    return 3.0 * Cd * u_inf ** 2 / (4.0 * d * (gamma - 1.0))
+
+
+# ---------------------------------------------------------------------------------------
+# Cases
+# ---------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Body:
+    verts: np.ndarray
+    tris: np.ndarray
+    rigid: bool = False
+    ks0: float = 0.0
+    Eb: float = 0.0
+    kv: float = 0.0
+    thickness: float = 1.0
+    density_ratio: float = 1.0
+    ref_radius: float = 1.0
+    gravity: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    u0: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    omega0: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    bend_variant: int = 0
+
+    def kwargs(self):
+        return dict(rigid=self.rigid, ks0=self.ks0, Eb=self.Eb, kv=self.kv, thickness=self.thickness,
+                    density_ratio=self.density_ratio, ref_radius=self.ref_radius, gravity=self.gravity,
+                    u0=self.u0, omega0=self.omega0, bend_variant=self.bend_variant)
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    n: Tuple[int, int, int]
+    tau: float
+    bc: Tuple[int, int, int]
+    wall_u: np.ndarray                  # (6, 3): faces -x,+x,-y,+y,-z,+z
+    gext: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    precision: int = PREC_FP32
+    steps: int = 100
+    bodies: List[Body] = dataclasses.field(default_factory=list)
+    rho0: Optional[np.ndarray] = None   # (ncell,)
+    u0: Optional[np.ndarray] = None     # (ncell, 3)
+
+    @property
+    def ncell(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def initial_fields(self):
+        rho = np.ones(self.ncell) if self.rho0 is None else self.rho0
+        u = np.zeros((self.ncell, 3)) if self.u0 is None else self.u0
+        return np.ascontiguousarray(rho, np.float64), np.ascontiguousarray(u, np.float64)
+
+
+def couette_profile(n, U: float):
+    """Linear shear u_x(z) = U (2 z/(nz-1) - 1) between walls at z = 0 and nz-1,
+    the exact steady state; x fastest in the flattened index."""
+    nx, ny, nz = n
+    z = np.arange(nz, dtype=np.float64)
+    ux = U * (2.0 * z / (nz - 1) - 1.0)
+    u = np.zeros((nz, ny, nx, 3))
+    u[..., 0] = ux[:, None, None]
+    return u.reshape(-1, 3)
+
+
+def shear_walls(U: float):
+    w = np.zeros((6, 3))
+    w[4, 0] = -U   # z = 0 face moves along -x
+    w[5, 0] = +U   # z = nz-1 face moves along +x
+    return w
+
+
+def case_couette_sphere(n=32, tau=1.0, U=0.01, level=3, radius=4.0, steps=200, precision=PREC_FP64):
+    """32^3 Couette cell, z walls at -+U, one neutrally buoyant rigid sphere
+    (radius 4, 642 markers) at the centre, FP64."""
+    c = (n - 1) / 2.0
+    v, f = icosphere(level, radius, (c, c, c))
+    body = Body(v, f, rigid=True, density_ratio=1.0, ref_radius=radius)
+    return Case("couette_rigid_sphere_32", (n, n, n), tau, (PERIODIC, PERIODIC, WALL), shear_walls(U),
+                precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), U))
+
+
+def case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=0.05, Eb=0.01, kv=10.0,
+                       density_ratio=1.0, steps=20000, precision=PREC_FP32, center=None):
+    """Deformable capsule in a Couette cell: 96^3, tau 0.8, shear rate 1e-4,
+    radius 10 (2562 markers, 5120 triangles), k_v = 10, mass ratio 1."""
+    U = shear_rate * (n - 1) / 2.0
+    c = (n - 1) / 2.0
+    v, f = icosphere(level, radius, center if center is not None else (c, c, c))
+    body = Body(v, f, rigid=False, ks0=ks0_from_capillary(Ca, tau, shear_rate, radius), Eb=Eb, kv=kv,
+                density_ratio=density_ratio, ref_radius=radius)
+    return Case(f"capsule_shear_{n}_Ca{Ca:g}", (n, n, n), tau, (PERIODIC, PERIODIC, WALL), shear_walls(U),
+                precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), U))
+
+
+def case_settling(nx=160, ny=160, nz=480, tau=0.7, radius=8.0, level=5, Re=5.0, gamma=1.3, steps=50000,
+                  precision=PREC_FP32, prolate=False):
+    """Rigid sphere (radius 8, 10242 markers) settling along -z in a closed
+    no-slip box 160x160x480, tau 0.7, g from the target Re and gamma."""
+    d = 2.0 * radius
+    g = settling_gravity(Re, gamma, d, tau)
+    cen = ((nx - 1) / 2.0, (ny - 1) / 2.0, 0.75 * (nz - 1))
+    axes = (radius, radius / 2.0, radius / 2.0) if prolate else None
+    v, f = icosphere(level, radius, cen, axes=axes)
+    body = Body(v, f, rigid=True, density_ratio=gamma, ref_radius=radius, gravity=(0.0, 0.0, -g))
+    name = f"settling_{'prolate' if prolate else 'sphere'}_{nx}x{ny}x{nz}"
+    return Case(name, (nx, ny, nz), tau, (WALL, WALL, WALL), np.zeros((6, 3)), precision=precision,
+                steps=steps, bodies=[body])
+
+
+def case_empty(n=(16, 12, 10), tau=0.8, bc=(PERIODIC, PERIODIC, PERIODIC), wall_u=None, gext=(0, 0, 0),
+               precision=PREC_FP64, seed=0, amplitude=1e-2):
+    """Lattice without bodies from a seeded random smooth-ish initial field."""
+    rng = np.random.default_rng(seed)
+    ncell = n[0] * n[1] * n[2]
+    rho = 1.0 + amplitude * rng.standard_normal(ncell)
+    u = amplitude * rng.standard_normal((ncell, 3))
+    return Case(f"empty_{n[0]}x{n[1]}x{n[2]}", tuple(n), tau, tuple(bc),
+                np.zeros((6, 3)) if wall_u is None else np.asarray(wall_u, np.float64),
+                gext=tuple(gext), precision=precision, rho0=rho, u0=u)

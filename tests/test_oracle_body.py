@@ -1,0 +1,150 @@
+"""Pins of the oracle's structure update and fluid-structure coupling (Sec. 2.3).
+
+References: hand-computed integrator sequences, exactness of the backward
+formulas on polynomials, Galilean invariance (a body moving with a uniform
+flow feels no force), a stress-free membrane in a fluid at rest stays put,
+the pressure-jump force of a linear density field (closed form), Stokes'
+result that a neutrally buoyant sphere in simple shear spins at half the
+shear rate, and the printed constants of Abraham's drag law.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_06029_gb300 import workloads as W
+
+
+def test_verlet_hand_computed():
+    """Eqs. (verletPos, verletVel), dt = 1."""
+    # start-up (x(t-dt) = x(t)), U = 1, no force: tentative x = 1,
+    # u = 1.5*1 - 2*0 + 0.5*0 = 1.5, x(t+dt) = 1.5
+    xn, un = oracle.verlet([0, 0, 0], [0, 0, 0], [1, 0, 0], [0, 0, 0])
+    assert np.array_equal(xn, [1.5, 0, 0]) and np.array_equal(un, [1.5, 0, 0])
+    # uniform motion with the fluid is reproduced exactly
+    xn, un = oracle.verlet([1, 2, 3], [0, 1, 2], [1, 1, 1], [0, 0, 0])
+    assert np.array_equal(xn, [2, 3, 4]) and np.array_equal(un, [1, 1, 1])
+    # constant acceleration a = 0.2, at rest: x~ = 0.1, u = 0.15, x = 0.25
+    xn, un = oracle.verlet([0, 0, 0], [0, 0, 0], [0, 0, 0], [0.2, 0, 0])
+    assert abs(xn[0] - 0.25) < 1e-16 and abs(un[0] - 0.15) < 1e-16
+
+
+def test_bdf2_exact_for_linear_history():
+    """Eqs. (linearVelRig, angularVelRig) reproduce v(t) = v0 + a t exactly."""
+    v0, a = np.array([0.3, -0.1, 0.2]), np.array([0.01, 0.02, -0.03])
+    for n in range(2, 6):
+        out = oracle.bdf2(v0 + a * (n - 1), v0 + a * (n - 2), a)
+        assert np.abs(out - (v0 + a * n)).max() < 1e-15
+
+
+def test_rigid_body_galilean_invariance():
+    """A rigid sphere translating with a uniform periodic flow: every probe
+    sees the same state on both sides, the interpolated velocity equals the
+    body's, and nothing changes except the translation."""
+    n, U0 = 20, np.array([0.02, -0.01, 0.015])
+    v, f = W.icosphere(2, 3.0, (9.7, 10.2, 9.9))
+    s = oracle.Sim((n, n, n), 0.8)
+    s.set_fields(np.ones(n ** 3), np.tile(U0, (n ** 3, 1)))
+    s.add_body(v, f, rigid=True, density_ratio=1.5, ref_radius=3.0, u0=tuple(U0))
+    assert s.step(20) == 0
+    rho, u = s.fields()
+    assert np.abs(u - U0).max() < 1e-15 and np.abs(rho - 1).max() < 1e-14
+    X, Ub, Fl = s.markers(0)
+    assert np.abs(Fl).max() < 1e-15
+    assert np.abs(X - (v + 20 * U0)).max() < 1e-12
+    assert np.abs(s.body(0)["omega"]).max() < 1e-15
+
+
+def test_membrane_at_rest_stays_at_rest():
+    """Stress-free capsule in a fluid at rest: all forces vanish, so nothing
+    moves beyond round-off."""
+    n = 20
+    v, f = W.icosphere(2, 4.0, (9.6, 9.4, 10.3))
+    s = oracle.Sim((n, n, n), 0.7, bc=(0, 1, 0))
+    # k_v = 1: the explicit update is stable for the collective radial mode
+    # only while 1.25 * 3 k_v / (rho_s T r) < 2
+    s.add_body(v, f, ks0=0.01, Eb=0.01, kv=1.0, ref_radius=4.0)
+    assert s.step(15) == 0
+    X, Ub, Fl = s.markers(0)
+    assert np.abs(X - v).max() < 1e-13 and np.abs(Fl).max() < 1e-14
+    rho, u = s.fields()
+    assert np.abs(u).max() < 1e-14
+
+
+def test_pressure_jump_of_linear_density(paper_const):
+    """Eq. (hydroForP) on the field rho = 1 + beta.x, u = 0: the MLS fits are
+    exact, p+ - p- = c_s^2 beta.(2 * 1.2 n), so
+    F = -c_s^2 2.4 (beta.n) n A; Eq. (hydroForNu) adds nothing."""
+    n = (16, 16, 16)
+    nx, ny, nz = n
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    beta = np.array([1e-3, -2e-3, 5e-4])
+    rho = (1.0 + beta[0] * x + beta[1] * y + beta[2] * z).ravel()
+    u = np.zeros((rho.size, 3))
+    v, f = W.icosphere(1, 3.0, (7.3, 7.9, 8.1))
+    cs2, L = paper_const["cs2"], paper_const["probe_length"]
+    for t in f[:10]:
+        F = oracle.hydro_force_fields(n, (0, 0, 0), 0.1, rho, u, v, t)
+        a, b, c = v[t[0]], v[t[1]], v[t[2]]
+        N = np.cross(b - a, c - a)
+        A = 0.5 * np.linalg.norm(N)
+        nn = N / np.linalg.norm(N)
+        ref = -cs2 * (2 * L) * (beta @ nn) * nn * A
+        assert np.abs(F - ref).max() < 1e-15
+
+
+def test_viscous_jump_vanishes_for_linear_flow():
+    """A linear velocity field has the same stress on both probes."""
+    n = (16, 16, 16)
+    nx, ny, nz = n
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    G = np.array([[0.0, 1e-3, 2e-4], [3e-4, -1e-4, 0.0], [1e-4, 5e-4, 1e-4]])
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1).astype(np.float64)
+    u = pos @ G.T
+    rho = np.ones(pos.shape[0])
+    v, f = W.icosphere(1, 3.0, (7.3, 7.9, 8.1))
+    for t in f[:10]:
+        F = oracle.hydro_force_fields(n, (0, 0, 0), 0.1, rho, u, v, t)
+        # round-off relative to the stress scale nu |G| A ~ 1e-4
+        assert np.abs(F).max() < 1e-14
+
+
+def test_neutral_sphere_spins_at_half_shear_rate():
+    """Stokes: a free, neutrally buoyant sphere in simple shear rotates with
+    omega = shear_rate/2 about the vorticity axis and stays at the centre.
+    32^3 Couette cell, radius 4 (confinement a/H = 0.13), Re ~ 0.06."""
+    case = W.case_couette_sphere(steps=200)
+    s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
+    s.set_fields(*case.initial_fields())
+    b = case.bodies[0]
+    s.add_body(b.verts, b.tris, **b.kwargs())
+    assert s.step(200) == 0
+    st = s.body(0)
+    gamma = 0.02 / 31.0
+    assert abs(st["omega"][1] / (gamma / 2) - 1.0) < 0.02
+    assert abs(st["omega"][0]) < 1e-12 and abs(st["omega"][2]) < 1e-12
+    assert np.abs(st["xc"] - 15.5).max() < 1e-10
+
+
+def test_settling_gravity_inverts_abraham_law(paper_const):
+    """g from (Re, gamma) satisfies u_inf = sqrt(4 g d (gamma-1)/(3 C_d)) with
+    C_d = C0 (1 + delta0/sqrt(Re))^2, C0 delta0^2 = 24, delta0 = 9.06."""
+    d0 = paper_const["abraham_delta0"]
+    C0 = paper_const["abraham_C0_delta0_sq"] / d0 ** 2
+    for Re, gamma, d, tau in [(1.5, 1.14, 16, 0.7), (31.9, 1.16, 30, 0.6), (5, 1.3, 16, 0.7)]:
+        g = W.settling_gravity(Re, gamma, d, tau)
+        Cd = C0 * (1 + d0 / math.sqrt(Re)) ** 2
+        u_inf = math.sqrt(4 * g * d * (gamma - 1) / (3 * Cd))
+        assert abs(u_inf * d / ((tau - 0.5) / 3) - Re) < 1e-10 * Re
+
+
+def test_support_reaching_a_wall_is_an_error():
+    """A marker whose support touches a wall node stops the run with the
+    body-wall error, and the error is sticky."""
+    n = 16
+    v, f = W.icosphere(1, 2.0, (8.0, 8.0, 3.2))
+    s = oracle.Sim((n, n, n), 0.8, bc=(0, 0, 1))
+    s.add_body(v, f, rigid=True, ref_radius=2.0)
+    assert s.step(1) == oracle.EBODY_WALL
+    assert s.step(1) == oracle.EBODY_WALL

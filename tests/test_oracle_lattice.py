@@ -1,0 +1,256 @@
+"""Pins of the oracle's fluid part (Sec. 2.1) against the paper and closed forms.
+
+Nothing here compares the oracle with itself: the references are the
+printed lattice (tests/golden), moment identities of the D3Q19 molecule,
+conservation laws, a streaming step built from numpy array shifts, and
+exact discrete steady states (linear Couette, parabolic Poiseuille interior).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_06029_gb300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def test_lattice_matches_printed_matrix(paper_e, paper_const):
+    e, w = oracle.lattice()
+    assert np.array_equal(e, paper_e)
+    assert w[0] == pytest.approx(paper_const["w0"], abs=1e-16)
+    assert np.allclose(w[1:7], paper_const["w1_6"], atol=1e-16, rtol=0)
+    assert np.allclose(w[7:], paper_const["w7_18"], atol=1e-16, rtol=0)
+
+
+def test_lattice_isotropy(paper_e, paper_const):
+    """Moments of the weights up to fourth order: the conditions under which
+    the equilibrium of Eq. (eqfunc) gives the Navier-Stokes moments."""
+    _, w = oracle.lattice()
+    e = paper_e.astype(np.float64)
+    cs2 = paper_const["cs2"]
+    d = np.eye(3)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.abs(np.einsum("i,ia->a", w, e)).max() < 1e-16
+    assert np.abs(np.einsum("i,ia,ib->ab", w, e, e) - cs2 * d).max() < 1e-15
+    assert np.abs(np.einsum("i,ia,ib,ic->abc", w, e, e, e)).max() < 1e-16
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e)
+    ref = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    # fourth-order isotropy; the diagonal moment sum w e_a^4 = 1/3 equals
+    # 3 c_s^4 only because 3 c_s^2 = 1 on this lattice
+    assert np.abs(m4 - ref).max() < 1e-15
+    # every vector has its opposite
+    for i in range(19):
+        assert any(np.array_equal(paper_e[j], -paper_e[i]) for j in range(19))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments(seed, paper_e, paper_const):
+    """Eq. (eqfunc): sum feq = rho, sum feq e = rho u,
+    sum feq e e = rho cs^2 I + rho u u (closed form)."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.1 * rng.standard_normal()
+    u = 0.05 * rng.standard_normal(3)
+    f = oracle.feq(rho, u)
+    e = paper_e.astype(np.float64)
+    cs2 = paper_const["cs2"]
+    assert abs(f.sum() - rho) < 1e-15
+    assert np.abs(f @ e - rho * u).max() < 1e-16
+    P = np.einsum("i,ia,ib->ab", f, e, e)
+    assert np.abs(P - (rho * cs2 * np.eye(3) + rho * np.outer(u, u))).max() < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_guo_forcing_moments(seed, paper_e):
+    """Eq. (forcing): zeroth moment 0, first moment (1 - 1/2tau) F, second
+    moment (1 - 1/2tau)(u F + F u)."""
+    rng = np.random.default_rng(100 + seed)
+    u = 0.05 * rng.standard_normal(3)
+    F = 1e-3 * rng.standard_normal(3)
+    tau = 0.55 + rng.random()
+    g = oracle.guo(u, F, tau)
+    e = paper_e.astype(np.float64)
+    c = 1.0 - 1.0 / (2.0 * tau)
+    assert abs(g.sum()) < 1e-18
+    assert np.abs(g @ e - c * F).max() < 1e-18
+    S = np.einsum("i,ia,ib->ab", g, e, e)
+    assert np.abs(S - c * (np.outer(u, F) + np.outer(F, u))).max() < 1e-18
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_collision_conservation(seed, paper_e):
+    """Eq. (evoleq) with u = (sum f e + F/2)/rho: mass is conserved and the
+    momentum gain per node is exactly f_lb."""
+    rng = np.random.default_rng(200 + seed)
+    f = oracle.feq(1.0, 0.03 * rng.standard_normal(3)) + 1e-3 * rng.standard_normal(19)
+    F = 1e-3 * rng.standard_normal(3)
+    tau = 0.51 + 1.5 * rng.random()
+    e = paper_e.astype(np.float64)
+    fs, rho, u = oracle.collide(f, tau, F)
+    assert abs(fs.sum() - f.sum()) < 1e-15
+    assert np.abs(fs @ e - (f @ e + F)).max() < 1e-16
+    assert np.abs(rho * u - (f @ e + 0.5 * F)).max() < 1e-16
+
+
+def test_collision_without_force_is_bgk(paper_e):
+    """f_lb = 0 reduces to BGK relaxation: the non-equilibrium part is scaled
+    by (1 - 1/tau); tau = 1 gives the equilibrium exactly."""
+    rng = np.random.default_rng(7)
+    f = oracle.feq(1.02, np.array([0.01, -0.02, 0.005])) + 1e-3 * rng.standard_normal(19)
+    e = paper_e.astype(np.float64)
+    rho = f.sum()
+    u = (f @ e) / rho
+    fe = oracle.feq(rho, u)
+    for tau in (0.6, 1.0, 1.7):
+        fs, _, _ = oracle.collide(f, tau, np.zeros(3))
+        assert np.abs((fs - fe) - (1 - 1 / tau) * (f - fe)).max() < 1e-16
+
+
+def _roll_stream(fpost, n):
+    """Pull streaming on a periodic lattice with numpy shifts:
+    f_i(x) = f*_i(x - e_i)."""
+    e, _ = oracle.lattice()
+    nx, ny, nz = n
+    f = fpost.reshape(nz, ny, nx, 19)
+    out = np.empty_like(f)
+    for i in range(19):
+        out[..., i] = np.roll(f[..., i], shift=(e[i, 2], e[i, 1], e[i, 0]), axis=(0, 1, 2))
+    return out.reshape(-1, 19)
+
+
+def test_streaming_brute_force_periodic():
+    """A step with tau so large that collision is the identity to 1e-15 is
+    exactly the shift permutation of each population plane."""
+    n = (3, 4, 5)
+    rng = np.random.default_rng(11)
+    ncell = n[0] * n[1] * n[2]
+    f0 = 0.05 + rng.random((ncell, 19))
+    s = oracle.Sim(n, tau=1e15)
+    s.set_populations(f0.ravel())
+    s.step(1)
+    assert np.abs(s.populations() - _roll_stream(f0, n)).max() < 1e-14
+
+
+def test_global_conservation_periodic():
+    """Periodic lattice, no force: total mass and momentum are invariant."""
+    case = W.case_empty(n=(7, 6, 5), tau=0.7, seed=3)
+    s = oracle.Sim(case.n, case.tau)
+    s.set_fields(*case.initial_fields())
+    e, _ = oracle.lattice()
+    f0 = s.populations()
+    m0, p0 = f0.sum(), (f0 @ e).sum(0)
+    s.step(25)
+    f1 = s.populations()
+    assert abs(f1.sum() - m0) / m0 < 1e-14
+    assert np.abs((f1 @ e).sum(0) - p0).max() < 1e-13
+
+
+def test_uniform_body_force_momentum_gain():
+    """Periodic lattice with a uniform body force g: the total momentum grows
+    by exactly N_cells * g per step (momentum gain f_lb per node)."""
+    g = np.array([1e-5, -2e-6, 3e-6])
+    case = W.case_empty(n=(6, 5, 4), tau=0.9, seed=5)
+    s = oracle.Sim(case.n, case.tau, gext=g)
+    s.set_fields(*case.initial_fields())
+    e, _ = oracle.lattice()
+    p0 = (s.populations() @ e).sum(0)
+    s.step(10)
+    p1 = (s.populations() @ e).sum(0)
+    assert np.abs(p1 - p0 - 10 * case.ncell * g).max() < 1e-13
+
+
+FACES = [(a, sgn) for a in range(3) for sgn in (+1, -1)]
+
+
+@pytest.mark.parametrize("axis,sign", FACES)
+def test_zouhe_imposes_wall_moments(axis, sign, paper_e):
+    """After the Zou-He reconstruction the node carries exactly the wall
+    velocity: sum f e = (sum f) u_w."""
+    rng = np.random.default_rng(axis * 10 + (sign > 0))
+    e = paper_e.astype(np.float64)
+    for _ in range(20):
+        uw = 0.05 * rng.standard_normal(3)
+        f = oracle.feq(1.0, 0.03 * rng.standard_normal(3)) + 2e-3 * rng.standard_normal(19)
+        unknown = sign * paper_e[:, axis] > 0
+        f[unknown] = 1e9  # garbage that must be overwritten
+        g = oracle.zouhe_face(f, axis, sign, uw)
+        assert np.abs(g[~unknown] - f[~unknown]).max() == 0.0
+        rho = g.sum()
+        assert np.abs(g @ e - rho * uw).max() < 1e-15
+
+
+@pytest.mark.parametrize("axis,sign", FACES)
+def test_zouhe_recovers_equilibrium(axis, sign, paper_e):
+    """An equilibrium state at the wall velocity is reconstructed exactly."""
+    rng = np.random.default_rng(50 + axis)
+    uw = 0.04 * rng.standard_normal(3)
+    uw[axis] = 0.0
+    rho = 1.0 + 0.05 * rng.standard_normal()
+    fe = oracle.feq(rho, uw)
+    f = fe.copy()
+    unknown = sign * paper_e[:, axis] > 0
+    f[unknown] = -7.0
+    g = oracle.zouhe_face(f, axis, sign, uw)
+    assert np.abs(g - fe).max() < 1e-16
+
+
+def test_corner_rule_at_rest(paper_e):
+    """Edge/corner rule: a resting equilibrium is left unchanged."""
+    fe = oracle.feq(1.0, np.zeros(3))
+    for axes, signs in [((0, 2), (1, -1)), ((0, 1, 2), (-1, 1, 1)), ((1, 2), (1, 1))]:
+        f = fe.copy()
+        unknown = np.zeros(19, bool)
+        for a, s in zip(axes, signs):
+            unknown |= s * paper_e[:, a] > 0
+        f[unknown] = 3.0
+        g = oracle.wall_multi(f, axes, signs, np.zeros(3 * len(axes)))
+        assert np.abs(g - fe).max() < 1e-16
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8, 0.6])
+def test_couette_linear_profile_is_exact(tau):
+    """Linear shear between z walls moving at -+U is an exact discrete steady
+    state: from the exact profile it stays exact at every step."""
+    n, U = (4, 4, 32), 0.01
+    s = oracle.Sim(n, tau, bc=(0, 0, 1), wall_u=W.shear_walls(U).ravel())
+    u0 = W.couette_profile(n, U)
+    s.set_fields(np.ones(s.ncell), u0)
+    for _ in range(4):
+        s.step(25)
+        rho, u = s.fields()
+        # round-off only (100 steps of ~1e-16 each)
+        assert np.abs(u - u0).max() < 1e-13
+        assert np.abs(rho - 1).max() < 1e-13
+
+
+def test_couette_from_rest_converges():
+    """From rest, the walls drive the flow to the linear profile."""
+    n, U, tau = (2, 2, 12), 0.01, 1.0
+    s = oracle.Sim(n, tau, bc=(0, 0, 1), wall_u=W.shear_walls(U).ravel())
+    s.step(3000)
+    _, u = s.fields()
+    assert np.abs(u - W.couette_profile(n, U)).max() < 1e-10
+
+
+def test_poiseuille_interior_parabola():
+    """Body-force-driven channel between resting z walls: at steady state the
+    interior profile has the exact second difference -g/nu of the
+    Navier-Stokes balance nu u'' + g = 0 and is symmetric."""
+    n, tau, g = (2, 2, 17), 0.8, 1e-5
+    nu = (tau - 0.5) / 3
+    s = oracle.Sim(n, tau, gext=(g, 0, 0), bc=(0, 0, 1))
+    s.step(12000)
+    _, u = s.fields()
+    ux = u.reshape(n[2], n[1], n[0], 3)[:, 0, 0, 0]
+    d2 = ux[3:-1] - 2 * ux[2:-2] + ux[1:-3]
+    assert np.abs(d2 + g / nu).max() < 1e-12
+    assert np.abs(ux - ux[::-1]).max() < 1e-15
+
+
+def test_walled_box_mass_at_rest():
+    """A closed box at rest stays at rest (every wall rule is consistent with
+    the resting equilibrium)."""
+    s = oracle.Sim((5, 6, 7), 0.7, bc=(1, 1, 1))
+    s.step(10)
+    rho, u = s.fields()
+    assert np.abs(rho - 1).max() < 1e-15 and np.abs(u).max() < 1e-16
