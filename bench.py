@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark: D3Q19 + dynamic-IB lattice updates per second on GB300.
+
+Workload (one step = the whole hot path: MLS interpolation at markers and
+hydrodynamic probes, membrane forces + Verlet + spreading, fused
+stream/wall/collide sweep): the 96^3 deformable-capsule Couette cell,
+tau 0.8, shear rate 1e-4, capsule radius 10 (2562 markers, 5120
+triangles), Ca 0.05, FP32 populations.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbib|reference]
+
+Multi-GPU runs (torchrun, one process per GPU) are independent replicas of
+the workload (the method has no exchange between separate runs); the
+value is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19+IB MLUPS & % HBM peak; served runs/h, p50/p99 latency vs plain"
+UNIT = "MLUPS"
+WORKLOAD = "capsule_shear_96^3_Ca0.05_fp32"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_case():
+    from paper_2207_06029_gb300 import workloads as W
+    return W.case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=0.05, Eb=0.01, kv=1.0,
+                                precision=W.PREC_FP32)
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "lbib_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2207_06029_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current sweep source; else None."""
+    path = os.path.join(ROOT, "profiles", "sweep_fp32_capsule96.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"sweep_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != sweep_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def torch_allocator(torch):
+    """Device allocation through PyTorch's caching allocator."""
+    from paper_2207_06029_gb300 import lbib
+    live = {}
+
+    def _alloc(nbytes, user):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(ptr, user):
+        live.pop(ptr, None)
+
+    return lbib.ALLOC_FN(_alloc), lbib.FREE_FN(_free), live
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2207_06029_gb300 import lbib
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    case = workload_case()
+    alloc_fn, free_fn, live = torch_allocator(torch)
+    params = lbib.make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
+                              stream=stream.cuda_stream)
+    params.alloc, params.free = alloc_fn, free_fn
+    h = lbib.lbib_create(params)
+    rho0, u0 = case.initial_fields()
+    lbib.lbib_set_fields(h, rho0, u0.reshape(-1))
+    b = case.bodies[0]
+    lbib.lbib_add_body(h, b.verts, b.tris, lbib.make_body_params(**b.kwargs()))
+    ncell = case.ncell
+
+    lbib.lbib_step(h, args.warmup)
+    lbib.lbib_sync(h)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _, launches0 = lbib.lbib_counters(h)
+    lbib.lbib_profile(h, 1)
+    lbib.lbib_get_profile(h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps, outside the events
+            starts[k].record(stream)
+            lbib.lbib_step(h, 1)
+            stops[k].record(stream)
+        torch.cuda.synchronize()
+    lbib.lbib_sync(h)
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, stops))
+    sweep_ms, ib_ms, nprof = lbib.lbib_get_profile(h)
+    lbib.lbib_profile(h, 0)
+    _, launches1 = lbib.lbib_counters(h)
+    lbib.lbib_destroy(h)
+    live.clear()
+
+    # end to end through the public API with host buffers: create from host
+    # fields, upload the mesh, K steps each followed by a read of the markers
+    # into pinned host memory, and the fields at the end
+    import numpy as np
+    import ctypes as C
+    Xh = torch.empty((b.verts.shape[0], 3), dtype=torch.float64, pin_memory=True)
+    Vh = torch.empty_like(Xh)
+    Fh = torch.empty_like(Xh)
+    rho_h = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
+    u_h = torch.empty(3 * ncell, dtype=torch.float64, pin_memory=True)
+    rho_in = torch.from_numpy(rho0).pin_memory()
+    u_in = torch.from_numpy(np.ascontiguousarray(u0.reshape(-1))).pin_memory()
+    e2e_steps = max(1, min(args.steps, 100))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p2 = lbib.make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
+                          stream=stream.cuda_stream)
+    p2.alloc, p2.free = alloc_fn, free_fn
+    h2 = lbib.lbib_create(p2)
+    L = lbib.load()
+    L.lbib_set_fields(h2, C.c_void_p(rho_in.data_ptr()), C.c_void_p(u_in.data_ptr()), 0)
+    lbib.lbib_add_body(h2, b.verts, b.tris, lbib.make_body_params(**b.kwargs()))
+    for _ in range(e2e_steps):
+        lbib.lbib_step(h2, 1)
+        L.lbib_get_markers(h2, 0, C.c_void_p(Xh.data_ptr()), C.c_void_p(Vh.data_ptr()), C.c_void_p(Fh.data_ptr()))
+    L.lbib_get_fields(h2, C.c_void_p(rho_h.data_ptr()), C.c_void_p(u_h.data_ptr()), 0)
+    t1 = time.perf_counter()
+    lbib.lbib_destroy(h2)
+    live.clear()
+    e2e_s = t1 - t0
+    h2d = (rho0.nbytes + u0.nbytes + b.verts.nbytes + b.tris.nbytes) / e2e_steps
+    d2h = 3 * Xh.numel() * 8 + (rho_h.numel() + u_h.numel()) * 8 / e2e_steps
+    return {"ms": ms, "sweep_ms": sweep_ms, "ib_ms": ib_ms, "nprof": nprof, "launches": launches1 - launches0,
+            "clocks": clk.summary(), "ncell": ncell, "e2e_s": e2e_s, "e2e_steps": e2e_steps, "h2d": h2d,
+            "d2h": d2h, "nv": int(b.verts.shape[0]), "nt": int(b.tris.shape[0])}
+
+
+def cpu_baseline(seconds=12.0, min_steps=2):
+    """The FP64 oracle on the same workload, on the host cores, for a bounded
+    number of steps (about `seconds` of CPU work)."""
+    import oracle
+    case = workload_case()
+    s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
+    s.set_fields(*case.initial_fields())
+    b = case.bodies[0]
+    s.add_body(b.verts, b.tris, **b.kwargs())
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < seconds:
+        assert s.step(1) == 0
+        steps += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": case.ncell * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of the 96^3 capsule case (FP64 oracle, OpenMP over z-planes)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        # the reference arm is the FP64 oracle on the host cores (rank 0 only)
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            pass
+        import oracle
+        case = workload_case()
+        s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
+        s.set_fields(*case.initial_fields())
+        b = case.bodies[0]
+        s.add_body(b.verts, b.tris, **b.kwargs())
+        s.step(1)
+        ksteps = max(1, min(args.steps, 40))
+        t0 = time.perf_counter()
+        assert s.step(ksteps) == 0
+        dt = time.perf_counter() - t0
+        val = case.ncell * ksteps / dt / 1e6
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": ksteps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / ksteps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "cells": case.ncell},
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{ksteps} steps of the 96^3 capsule case"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = run_gpu(args, rank, world)
+    import torch
+    ms_all = [r["ms"]]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([r["ms"], r["e2e_s"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = [float(t[0])]
+        r["e2e_s"] = float(t[1])
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    ms = ms_all[0]
+    total_updates = r["ncell"] * args.steps * world
+    value = total_updates / (ms * 1e-3) / 1e6
+    peak, peak_kind = hbm_peak()
+    bytes_per_launch = 152.0 * r["ncell"]  # 19 reads + 19 writes of 4 bytes per cell
+    sweep_avg_s = r["sweep_ms"] * 1e-3 / max(r["nprof"], 1)
+    achieved = bytes_per_launch / sweep_avg_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
+                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write)",
+                   "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(), "kernel": "k_sweep<float,float>",
+                     "peak_source": peak_kind, "sweep_ms_per_step": r["sweep_ms"] / max(r["nprof"], 1),
+                     "ib_ms_per_step": r["ib_ms"] / max(r["nprof"], 1)},
+        "e2e": {"value": r["ncell"] * r["e2e_steps"] * world / r["e2e_s"] / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"])},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

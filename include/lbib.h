@@ -1,0 +1,172 @@
+/*
+ * lbib.h -- C ABI of the GB300 lattice-Boltzmann / dynamic immersed-boundary
+ * library (liblbib.so).
+ *
+ * Method: Coclite, Ranaldo, Pascazio, de Tullio, "A Lattice Boltzmann
+ * dynamic-Immersed Boundary scheme for the transport of deformable inertial
+ * capsules in low-Re flows" (arXiv 2207.06029).  A D3Q19 BGK lattice with the
+ * Guo forcing term (Sec. 2.1, Eqs. e_i, evoleq, eqfunc, forcing) and Zou-He
+ * velocity walls is coupled to immersed bodies through moving-least-squares
+ * interpolation and spreading (Sec. 2.2, Eqs. uLag, l2norm, intKernel,
+ * bodyforce).  Membranes feel spring, bending and volume forces plus the
+ * probe-based hydrodynamic stresses and move by the Verlet update; rigid
+ * bodies follow the Newton-Euler update (Sec. 2.3, Eqs. strainPot..
+ * angularVelRig).
+ *
+ * Units: lattice units, dx = dt = 1, reference density 1.  Node (x, y, z)
+ * sits at position (x, y, z); the linear cell index is
+ * idx = x + nx * (y + ny * z).
+ *
+ * Ownership: the library owns all device state of a context.  Every array
+ * argument is owned by the caller and is only read or written during the
+ * call (inputs are copied).  Pointers flagged "on_device" are CUDA device
+ * pointers (e.g. torch tensor data); otherwise they are host pointers.
+ *
+ * Errors: every call returns LBIB_OK (0) or a negative code and never aborts
+ * or traps the device.  lbib_last_error() gives a message.  Errors raised on
+ * the device (a body support reaching a wall) surface at the next call that
+ * synchronises (lbib_sync, lbib_get_*); after any error the context is
+ * sticky: further lbib_step calls return the same code.
+ *
+ * Calls on one context are not thread-safe; different contexts are
+ * independent.  All device work of a context runs on its stream.
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBIB_OK = 0,
+    LBIB_EINVAL = -1,      /* invalid argument or parameter */
+    LBIB_ENOMEM = -2,      /* device or host allocation failed */
+    LBIB_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+    LBIB_EDIVERGED = -4,   /* reserved: non-finite state detected */
+    LBIB_EBODY_WALL = -5,  /* an MLS support (marker or probe) reached a wall node */
+    LBIB_ETIMEOUT = -6     /* reserved: a bounded device wait expired */
+};
+
+/* Storage precision of the populations.  FP64 stores and computes in
+ * double; FP32 stores and computes in float; FP16_DEV / BF16_DEV store the
+ * deviations f_i - w_i in half / bfloat16 and compute in float. */
+typedef enum { LBIB_FP64 = 0, LBIB_FP32 = 1, LBIB_FP16_DEV = 2, LBIB_BF16_DEV = 3 } lbib_prec;
+
+/* Boundary kind per axis: PERIODIC wraps; WALL makes the first and last
+ * nodes of the axis Zou-He velocity-wall nodes (Sec. 2.1). */
+typedef enum { LBIB_PERIODIC = 0, LBIB_WALL = 1 } lbib_bc;
+
+typedef struct {
+    int nx, ny, nz;          /* lattice nodes per axis; >= 3 on walled axes */
+    double tau;              /* BGK relaxation time, > 0.5; nu = (tau - 1/2)/3 (Sec. 2.1) */
+    double body_force[3];    /* uniform fluid body force g_ext (not applied on wall nodes) */
+    int bc[3];               /* lbib_bc per axis */
+    double wall_u[6][3];     /* wall velocity per face: -x, +x, -y, +y, -z, +z */
+    int precision;           /* lbib_prec */
+    void *stream;            /* cudaStream_t to run on, or NULL for a library-owned stream */
+    /* optional device allocator (e.g. a PyTorch caching allocator); both NULL
+     * means cudaMalloc / cudaFree */
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *alloc_user;
+} lbib_params;
+
+typedef struct {
+    int rigid;               /* 1: rigid body (Newton-Euler); 0: membrane (Verlet) */
+    double ks0;              /* membrane: global stiffness k_s0 (Ca = rho nu u_ref / k_s0, Sec. 2.3) */
+    double Eb;               /* membrane: bending ratio Eb = k_b / (k_s,l r^2) */
+    double kv;               /* membrane: volume-penalty constant k_v (Eq. volFor) */
+    double thickness;        /* membrane thickness T (springs and mass), lattice units */
+    double density_ratio;    /* rho_s / rho_f: membrane mass or rigid-body density */
+    double ref_radius;       /* r in the bending constant */
+    double gravity[3];       /* rigid: gravity acceleration (adds (rho_s - rho_f) V g) */
+    double u0[3], omega0[3]; /* rigid: initial linear and angular velocity */
+    int bend_variant;        /* 0: k_b [1 - cos(theta - theta0)]; 1: k_b/2 (theta - theta0)^2 */
+} lbib_body_params;
+
+typedef struct {
+    double xc[3];            /* rigid: centre of mass; membrane: mean of the vertices */
+    double u[3];             /* rigid: velocity; membrane: mean marker boundary velocity */
+    double omega[3];         /* rigid: angular velocity; membrane: 0 */
+    double q[4];             /* rigid: orientation quaternion (w, x, y, z); membrane: (1,0,0,0) */
+    double volume, area;     /* enclosed volume and surface area of the current mesh */
+} lbib_body_state;
+
+/* Creates a context: allocates the two population buffers, the force field
+ * and its tile flags, and sets the fluid at rest (f = f^eq(1, 0)).
+ * out receives the context; returns LBIB_EINVAL for bad sizes, tau <= 1/2,
+ * an unknown precision or bc; LBIB_ENOMEM / LBIB_ECUDA otherwise. */
+int lbib_create(const lbib_params *p, void **out);
+
+/* Sets the fluid to equilibrium f = f^eq(rho(x), u(x)) (Eq. eqfunc).
+ * rho[ncell], u[3*ncell] (x, y, z per cell), host or device doubles. */
+int lbib_set_fields(void *ctx, const double *rho, const double *u, int on_device);
+
+/* Sets the post-collision populations directly: f[ncell*19], 19 values per
+ * cell in the order of Eq. (e_i).  Host or device doubles. */
+int lbib_set_populations(void *ctx, const double *f, int on_device);
+
+/* Adds an immersed body given its vertices (the Lagrangian markers,
+ * verts[3*nv]) and outward, counter-clockwise triangles (tris[3*nt]) of a
+ * closed manifold mesh (Sec. 2.2, Fig. IB).  The rest state (spring
+ * constants, rest lengths and dihedral angles, volume, mass, inertia) is
+ * computed here in FP64.  Host arrays.  body_id receives the body index.
+ * LBIB_EINVAL for an open or inverted mesh or bad parameters. */
+int lbib_add_body(void *ctx, const double *verts, int nv, const int *tris, int nt,
+                  const lbib_body_params *bp, int *body_id);
+
+/* Advances nsteps time steps, asynchronously on the context stream.  One
+ * step: MLS interpolation at markers and hydrodynamic probes, structure
+ * forces and update, spreading of the IB force (Eq. bodyforce), then the
+ * fused stream + wall + collide sweep (Eq. evoleq).  Returns the sticky
+ * error if one is recorded. */
+int lbib_step(void *ctx, int nsteps);
+
+/* Waits for the context stream and reports device-side errors. */
+int lbib_sync(void *ctx);
+
+/* Density and velocity u = (sum f e + f_lb/2)/rho of the last collision
+ * (Sec. 2.1): rho[ncell], u[3*ncell]; either may be NULL.  Synchronises. */
+int lbib_get_fields(void *ctx, double *rho, double *u, int on_device);
+
+/* Post-collision populations, f[ncell*19] doubles.  Synchronises. */
+int lbib_get_populations(void *ctx, double *f, int on_device);
+
+/* Marker positions after the last step (X), the boundary velocity U_b
+ * imposed in that step (V) and the Lagrangian IB force F_l (F), each
+ * [3*nv] host doubles; any may be NULL.  Synchronises. */
+int lbib_get_markers(void *ctx, int body, double *X, double *V, double *F);
+
+/* Body summary after the last step.  Synchronises. */
+int lbib_get_body(void *ctx, int body, lbib_body_state *out);
+
+/* Number of steps taken and number of kernels launched so far. */
+int lbib_counters(void *ctx, long long *steps, long long *launches);
+
+/* Enables (1) or disables (0) CUDA-event timing of the kernels of each
+ * step, recorded on the context stream. */
+int lbib_profile(void *ctx, int enable);
+
+/* Timing since profiling was enabled or last read: total milliseconds of
+ * the collide-stream sweeps and of the IB kernels, and the number of steps
+ * timed.  Synchronises and resets the accumulators. */
+int lbib_get_profile(void *ctx, double *sweep_ms, double *ib_ms, long long *nsteps);
+
+/* Bytes of device memory held by the context. */
+int lbib_device_bytes(void *ctx, size_t *bytes);
+
+/* Releases all device and host memory of the context (NULL is a no-op). */
+void lbib_destroy(void *ctx);
+
+/* Message of the last error of ctx (or of the last failed lbib_create when
+ * ctx is NULL).  Valid until the next call on the context. */
+const char *lbib_last_error(const void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBIB_H */

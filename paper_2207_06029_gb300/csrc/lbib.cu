@@ -1,0 +1,808 @@
+// liblbib C ABI (include/lbib.h): context, device memory, body set-up and
+// the per-step launch sequence.  Host-side rest-state computations (mesh
+// hinges, spring and bending constants, mass properties) are FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/lbib.h"
+#include "lbib_device.cuh"
+#include "lbib_kernels.h"
+
+using namespace lbib;
+
+namespace {
+
+std::string g_create_error;
+
+struct DevBody {
+    int nv = 0, nt = 0, nh = 0, rigid = 0;
+    lbib_body_params p{};
+    double *X[3] = {nullptr, nullptr, nullptr};  // rotating buffers: prev, cur, next
+    int cur = 1;
+    double *U = nullptr, *Ub = nullptr, *Fl = nullptr, *phi = nullptr, *tri_geo = nullptr, *probe = nullptr;
+    int *node = nullptr, *tri = nullptr, *vh_ptr = nullptr, *vh_list = nullptr, *vt_ptr = nullptr,
+        *vt_list = nullptr;
+    int4 *hinge = nullptr;
+    double *ks = nullptr, *l0 = nullptr, *kb = nullptr, *theta0 = nullptr, *Xbody = nullptr, *rstate = nullptr;
+    double V0 = 0, A0 = 0, mv = 0, origin[3] = {0, 0, 0};
+};
+
+struct Ctx {
+    lbib_params p{};
+    Lattice L{};
+    int prec = 1;
+    size_t elem = 4, relem = 4;
+    void *fA = nullptr, *fB = nullptr, *force = nullptr, *fields = nullptr;
+    uint32_t *stamp = nullptr;
+    int ntiles = 0;
+    int *d_err = nullptr;
+    int *h_err = nullptr;
+    double *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<DevBody> bodies;
+    uint32_t stamp_step = 0;
+    long long steps = 0, launches = 0;
+    int err = 0;
+    std::string msg;
+    size_t bytes = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
+    bool profile = false;
+    std::vector<cudaEvent_t> events;  // triples: begin, after IB, after sweep
+    size_t nev = 0;
+};
+
+int fail(Ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->msg = buf;
+    return code;
+}
+
+int cuda_fail(Ctx *c, cudaError_t e, const char *what) {
+    c->err = LBIB_ECUDA;
+    return fail(c, LBIB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dev_alloc(Ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *ptr = nullptr;
+    if (c->p.alloc) {
+        ptr = c->p.alloc(bytes, c->p.alloc_user);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) {
+        c->allocs.push_back({ptr, bytes});
+        c->bytes += bytes;
+    }
+    return ptr;
+}
+
+void dev_free_all(Ctx *c) {
+    for (auto &a : c->allocs) {
+        if (c->p.free)
+            c->p.free(a.first, c->p.alloc_user);
+        else
+            cudaFree(a.first);
+    }
+    c->allocs.clear();
+    c->bytes = 0;
+}
+
+template <typename T>
+T *upload(Ctx *c, const std::vector<T> &v, int *rc) {
+    T *d = (T *)dev_alloc(c, v.size() * sizeof(T));
+    if (!d) {
+        *rc = LBIB_ENOMEM;
+        return nullptr;
+    }
+    if (!v.empty()) {
+        cudaError_t e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            *rc = LBIB_ECUDA;
+            return nullptr;
+        }
+    }
+    return d;
+}
+
+// Largest squared distance d2 for which sqrt(d2)/r_w <= 1 holds in IEEE
+// double arithmetic, i.e. the MLS support cut-off of Eq. (intKernel)
+// expressed on the squared distance (bisection on the bit patterns).
+double mls_dist2_cut() {
+    double lo = 1.0, hi = 4.0;
+    uint64_t a, b;
+    std::memcpy(&a, &lo, 8);
+    std::memcpy(&b, &hi, 8);
+    while (b - a > 1) {
+        uint64_t m = a + (b - a) / 2;
+        double d;
+        std::memcpy(&d, &m, 8);
+        if (std::sqrt(d) / 1.3 <= 1.0)
+            a = m;
+        else
+            b = m;
+    }
+    double out;
+    std::memcpy(&out, &a, 8);
+    return out;
+}
+
+Ctx *as_ctx(void *h) { return static_cast<Ctx *>(h); }
+
+// ---- host geometry (FP64) ----
+inline void v_sub(const double *a, const double *b, double *o) {
+    for (int i = 0; i < 3; ++i) o[i] = a[i] - b[i];
+}
+inline void v_cross(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+inline double v_dot(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+double tri_area(const double *X, const int *t) {
+    double e1[3], e2[3], N[3];
+    v_sub(X + 3 * t[1], X + 3 * t[0], e1);
+    v_sub(X + 3 * t[2], X + 3 * t[0], e2);
+    v_cross(e1, e2, N);
+    return 0.5 * std::sqrt(v_dot(N, N));
+}
+
+// signed dihedral angle between the outward normals of T1 = (a,b,c) and
+// T2 = (b,a,d), positive on convex hinges
+double dihedral(const double *xa, const double *xb, const double *xc, const double *xd) {
+    double e[3], ac[3], ad[3], N1[3], N2[3], c12[3];
+    v_sub(xb, xa, e);
+    v_sub(xc, xa, ac);
+    v_sub(xd, xa, ad);
+    v_cross(e, ac, N1);
+    v_cross(ad, e, N2);
+    const double l1 = std::sqrt(v_dot(N1, N1)), l2 = std::sqrt(v_dot(N2, N2)), le = std::sqrt(v_dot(e, e));
+    double n1[3], n2[3];
+    for (int k = 0; k < 3; ++k) {
+        n1[k] = N1[k] / l1;
+        n2[k] = N2[k] / l2;
+    }
+    v_cross(n1, n2, c12);
+    return std::atan2(v_dot(c12, e) / le, v_dot(n1, n2));
+}
+
+// volume, volume centroid and inertia (about the centroid, unit density) of
+// the solid bounded by a closed outward triangulation, by tetrahedra from
+// the origin
+void mass_props(const double *X, int nt, const int *tri, double *V, double *cen, double *I) {
+    double vol = 0, c[3] = {0, 0, 0}, C[9] = {0};
+    for (int t = 0; t < nt; ++t) {
+        const double *a = X + 3 * tri[3 * t], *b = X + 3 * tri[3 * t + 1], *d = X + 3 * tri[3 * t + 2];
+        double bd[3];
+        v_cross(b, d, bd);
+        const double v = v_dot(a, bd) / 6.0;
+        vol += v;
+        double s[3];
+        for (int k = 0; k < 3; ++k) {
+            s[k] = a[k] + b[k] + d[k];
+            c[k] += v * s[k] / 4.0;
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                C[3 * i + j] += v / 20.0 * (a[i] * a[j] + b[i] * b[j] + d[i] * d[j] + s[i] * s[j]);
+    }
+    for (int k = 0; k < 3; ++k) c[k] /= vol;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) C[3 * i + j] -= vol * c[i] * c[j];
+    const double tr = C[0] + C[4] + C[8];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) I[3 * i + j] = (i == j ? tr : 0.0) - C[3 * i + j];
+    *V = vol;
+    for (int k = 0; k < 3; ++k) cen[k] = c[k];
+}
+
+BodyView make_view(Ctx *c, DevBody &b) {
+    BodyView v{};
+    v.nv = b.nv;
+    v.nt = b.nt;
+    v.rigid = b.rigid;
+    const int prev = (b.cur + 2) % 3, next = (b.cur + 1) % 3;
+    v.X = b.X[b.cur];
+    v.Xprev = b.X[prev];
+    v.Xnew = b.X[next];
+    v.U = b.U;
+    v.Ub = b.Ub;
+    v.Fl = b.Fl;
+    v.phi = b.phi;
+    v.node = b.node;
+    v.tri = b.tri;
+    v.tri_geo = b.tri_geo;
+    v.probe = b.probe;
+    v.vh_ptr = b.vh_ptr;
+    v.vh_list = b.vh_list;
+    v.vt_ptr = b.vt_ptr;
+    v.vt_list = b.vt_list;
+    v.hinge = b.hinge;
+    v.ks = b.ks;
+    v.l0 = b.l0;
+    v.kb = b.kb;
+    v.theta0 = b.theta0;
+    v.V0 = b.V0;
+    v.mv = b.mv;
+    v.kv = b.p.kv;
+    for (int a = 0; a < 3; ++a) v.origin[a] = b.origin[a];
+    v.bend_variant = b.p.bend_variant;
+    v.Xbody = b.Xbody;
+    v.rstate = b.rstate;
+    (void)c;
+    return v;
+}
+
+int check_device_error(Ctx *c) {
+    if (*c->h_err != 0 && c->err == 0) {
+        c->err = *c->h_err;
+        if (c->err == LBIB_EBODY_WALL)
+            fail(c, c->err, "an MLS support (marker or probe) reached a wall node");
+        else
+            fail(c, c->err, "device error %d (singular MLS moment matrix)", c->err);
+    }
+    return c->err;
+}
+
+int sync_ctx(Ctx *c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    return check_device_error(c);
+}
+
+double *get_scratch(Ctx *c, size_t bytes) {
+    if (c->scratch_bytes >= bytes) return c->scratch;
+    c->scratch = (double *)dev_alloc(c, bytes);
+    c->scratch_bytes = c->scratch ? bytes : 0;
+    return c->scratch;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbib_last_error(const void *h) {
+    if (!h) return g_create_error.c_str();
+    return static_cast<const Ctx *>(h)->msg.c_str();
+}
+
+int lbib_create(const lbib_params *p, void **out) {
+    if (!p || !out) {
+        g_create_error = "null argument";
+        return LBIB_EINVAL;
+    }
+    *out = nullptr;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || (p->bc[a] != LBIB_PERIODIC && p->bc[a] != LBIB_WALL)) {
+            g_create_error = "lattice size must be >= 1 and bc PERIODIC or WALL";
+            return LBIB_EINVAL;
+        }
+        if (p->bc[a] == LBIB_WALL && n[a] < 3) {
+            g_create_error = "a walled axis needs at least 3 nodes";
+            return LBIB_EINVAL;
+        }
+    }
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) {
+        g_create_error = "tau must be > 0.5";
+        return LBIB_EINVAL;
+    }
+    if (p->precision < LBIB_FP64 || p->precision > LBIB_BF16_DEV) {
+        g_create_error = "unknown precision";
+        return LBIB_EINVAL;
+    }
+    if ((p->alloc == nullptr) != (p->free == nullptr)) {
+        g_create_error = "alloc and free must be given together";
+        return LBIB_EINVAL;
+    }
+    const long long ncell = (long long)n[0] * n[1] * n[2];
+    if (ncell > (1LL << 30)) {
+        g_create_error = "lattice too large (more than 2^30 nodes)";
+        return LBIB_EINVAL;
+    }
+    Ctx *c = new Ctx();
+    c->p = *p;
+    c->prec = p->precision;
+    c->elem = c->prec == LBIB_FP64 ? 8 : c->prec == LBIB_FP32 ? 4 : 2;
+    c->relem = c->prec == LBIB_FP64 ? 8 : 4;
+    Lattice &L = c->L;
+    L.nx = n[0];
+    L.ny = n[1];
+    L.nz = n[2];
+    L.ntx = (n[0] + kTile - 1) / kTile;
+    L.nty = (n[1] + kTile - 1) / kTile;
+    L.ntz = (n[2] + kTile - 1) / kTile;
+    L.ncell = (int)ncell;
+    L.stride = (ncell + 63) / 64 * 64;
+    for (int a = 0; a < 3; ++a) {
+        L.bc[a] = p->bc[a];
+        L.gext[a] = p->body_force[a];
+    }
+    L.tau = p->tau;
+    for (int f = 0; f < 6; ++f)
+        for (int a = 0; a < 3; ++a) L.wall_u[f][a] = p->wall_u[f][a];
+    L.dist2_cut = mls_dist2_cut();
+    c->ntiles = L.ntx * L.nty * L.ntz;
+
+    cudaError_t e;
+    if (p->stream) {
+        c->stream = (cudaStream_t)p->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            delete c;
+            return LBIB_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    const size_t pop_bytes = (size_t)Q * L.stride * c->elem;
+    c->fA = dev_alloc(c, pop_bytes);
+    c->fB = dev_alloc(c, pop_bytes);
+    c->force = dev_alloc(c, 3 * (size_t)L.stride * c->relem);
+    c->fields = dev_alloc(c, 4 * (size_t)L.stride * c->relem);
+    c->stamp = (uint32_t *)dev_alloc(c, sizeof(uint32_t) * (size_t)c->ntiles);
+    c->d_err = (int *)dev_alloc(c, sizeof(int));
+    if (!c->fA || !c->fB || !c->force || !c->fields || !c->stamp || !c->d_err) {
+        g_create_error = "device allocation failed";
+        lbib_destroy(c);
+        return LBIB_ENOMEM;
+    }
+    if (cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "pinned host allocation failed";
+        c->h_err = nullptr;
+        lbib_destroy(c);
+        return LBIB_ENOMEM;
+    }
+    *c->h_err = 0;
+    e = cudaMemsetAsync(c->force, 0, 3 * (size_t)L.stride * c->relem, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cudaMemset: ") + cudaGetErrorString(e);
+        lbib_destroy(c);
+        return LBIB_ECUDA;
+    }
+    // fluid at rest
+    std::vector<double> rho((size_t)ncell, 1.0), u(3 * (size_t)ncell, 0.0);
+    int rc = lbib_set_fields(c, rho.data(), u.data(), 0);
+    if (rc) {
+        g_create_error = c->msg;
+        lbib_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LBIB_OK;
+}
+
+void lbib_destroy(void *h) {
+    if (!h) return;
+    Ctx *c = as_ctx(h);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto ev : c->events) cudaEventDestroy(ev);
+    dev_free_all(c);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int lbib_set_fields(void *h, const double *rho, const double *u, int on_device) {
+    Ctx *c = as_ctx(h);
+    if (!c || !rho || !u) return LBIB_EINVAL;
+    const size_t n = (size_t)c->L.ncell;
+    const double *drho = rho, *du = u;
+    if (!on_device) {
+        double *tmp = get_scratch(c, 4 * n * sizeof(double));
+        if (!tmp) return fail(c, LBIB_ENOMEM, "scratch allocation failed");
+        cudaError_t e = cudaMemcpyAsync(tmp, rho, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_fields copy");
+        drho = tmp;
+        du = tmp + n;
+    }
+    cudaError_t e = launch_init_equilibrium(c->prec, c->fA, c->L, drho, du, c->fields, c->stream);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    if (!on_device) {
+        e = cudaStreamSynchronize(c->stream);  // the host buffers may be freed after return
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_fields sync");
+    }
+    return LBIB_OK;
+}
+
+int lbib_set_populations(void *h, const double *f, int on_device) {
+    Ctx *c = as_ctx(h);
+    if (!c || !f) return LBIB_EINVAL;
+    const size_t n = (size_t)c->L.ncell * Q;
+    const double *df = f;
+    if (!on_device) {
+        double *tmp = get_scratch(c, n * sizeof(double));
+        if (!tmp) return fail(c, LBIB_ENOMEM, "scratch allocation failed");
+        cudaError_t e = cudaMemcpyAsync(tmp, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_populations copy");
+        df = tmp;
+    }
+    cudaError_t e = launch_aos_to_pop(c->prec, df, c->L, c->fA, c->stream);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "populations kernel");
+    if (!on_device) {
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_populations sync");
+    }
+    return LBIB_OK;
+}
+
+int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt, const lbib_body_params *bp,
+                  int *body_id) {
+    Ctx *c = as_ctx(h);
+    if (!c || !verts || !tris || !bp) return LBIB_EINVAL;
+    if (c->err) return c->err;
+    if (nv < 4 || nt < 4) return fail(c, LBIB_EINVAL, "a body needs at least 4 vertices and 4 triangles");
+    for (int a = 0; a < 3; ++a) {
+        const int na = a == 0 ? c->L.nx : a == 1 ? c->L.ny : c->L.nz;
+        if (c->L.bc[a] == kWall && na < 5)
+            return fail(c, LBIB_EINVAL, "bodies need at least 5 nodes along walled axes");
+    }
+    for (int i = 0; i < 3 * nt; ++i)
+        if (tris[i] < 0 || tris[i] >= nv) return fail(c, LBIB_EINVAL, "triangle index out of range");
+    for (int i = 0; i < 3 * nv; ++i)
+        if (!std::isfinite(verts[i])) return fail(c, LBIB_EINVAL, "non-finite vertex");
+    if (bp->rigid) {
+        if (!(bp->density_ratio > 0)) return fail(c, LBIB_EINVAL, "rigid body needs density_ratio > 0");
+    } else {
+        if (!(bp->thickness > 0) || !(bp->density_ratio > 0) || bp->ks0 < 0 || bp->Eb < 0 || bp->kv < 0 ||
+            (bp->Eb > 0 && !(bp->ref_radius > 0)))
+            return fail(c, LBIB_EINVAL, "invalid membrane parameters");
+    }
+    DevBody b;
+    b.nv = nv;
+    b.nt = nt;
+    b.rigid = bp->rigid ? 1 : 0;
+    b.p = *bp;
+    // hinges: one per undirected edge a<b, T1 holds a->b, T2 holds b->a
+    std::unordered_map<unsigned long long, std::pair<int, int>> dir;  // (a,b) -> (triangle, third vertex)
+    dir.reserve((size_t)3 * nt * 2);
+    for (int t = 0; t < nt; ++t)
+        for (int s = 0; s < 3; ++s) {
+            const int a = tris[3 * t + s], bb = tris[3 * t + (s + 1) % 3], cc = tris[3 * t + (s + 2) % 3];
+            const unsigned long long key = (unsigned long long)a * (unsigned long long)nv + (unsigned long long)bb;
+            if (!dir.emplace(key, std::make_pair(t, cc)).second)
+                return fail(c, LBIB_EINVAL, "mesh has a repeated directed edge (not an oriented manifold)");
+        }
+    std::vector<int4> hinge;
+    std::vector<int> htri;
+    for (int t = 0; t < nt; ++t)
+        for (int s = 0; s < 3; ++s) {
+            const int a = tris[3 * t + s], bb = tris[3 * t + (s + 1) % 3];
+            const unsigned long long rkey = (unsigned long long)bb * nv + (unsigned long long)a;
+            auto it = dir.find(rkey);
+            if (it == dir.end()) return fail(c, LBIB_EINVAL, "mesh is not closed (edge without a twin)");
+            if (a < bb) {
+                hinge.push_back(make_int4(a, bb, tris[3 * t + (s + 2) % 3], it->second.second));
+                htri.push_back(t);
+                htri.push_back(it->second.first);
+            }
+        }
+    const int nh = (int)hinge.size();
+    b.nh = nh;
+    std::vector<double> ks(nh), l0(nh), kb(nh), th0(nh);
+    for (int h2 = 0; h2 < nh; ++h2) {
+        const int4 H = hinge[h2];
+        double r[3];
+        v_sub(verts + 3 * H.x, verts + 3 * H.y, r);
+        const double l = std::sqrt(v_dot(r, r));
+        const double A1 = tri_area(verts, tris + 3 * htri[2 * h2]), A2 = tri_area(verts, tris + 3 * htri[2 * h2 + 1]);
+        l0[h2] = l;
+        ks[h2] = bp->ks0 * bp->thickness * (A1 + A2) / (l * l);  // Van Gelder, rest values
+        kb[h2] = bp->Eb * ks[h2] * bp->ref_radius * bp->ref_radius;
+        th0[h2] = dihedral(verts + 3 * H.x, verts + 3 * H.y, verts + 3 * H.z, verts + 3 * H.w);
+    }
+    double V0 = 0.0, A0 = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        double cr[3];
+        v_cross(verts + 3 * tris[3 * t + 1], verts + 3 * tris[3 * t + 2], cr);
+        V0 += v_dot(verts + 3 * tris[3 * t], cr) / 6.0;
+        A0 += tri_area(verts, tris + 3 * t);
+    }
+    if (!(V0 > 0.0)) return fail(c, LBIB_EINVAL, "mesh encloses no positive volume (inward orientation?)");
+    b.V0 = V0;
+    b.A0 = A0;
+    b.mv = bp->density_ratio * bp->thickness * A0 / nv;
+    for (int v = 0; v < nv; ++v)
+        for (int a = 0; a < 3; ++a) b.origin[a] += verts[3 * v + a] / nv;
+    // vertex -> (hinge, role) and vertex -> (triangle, corner) lists
+    std::vector<std::vector<int>> vh(nv), vt(nv);
+    for (int h2 = 0; h2 < nh; ++h2) {
+        vh[hinge[h2].x].push_back(4 * h2 + 0);
+        vh[hinge[h2].y].push_back(4 * h2 + 1);
+        vh[hinge[h2].z].push_back(4 * h2 + 2);
+        vh[hinge[h2].w].push_back(4 * h2 + 3);
+    }
+    for (int t = 0; t < nt; ++t)
+        for (int q = 0; q < 3; ++q) vt[tris[3 * t + q]].push_back(3 * t + q);
+    std::vector<int> vh_ptr(nv + 1, 0), vt_ptr(nv + 1, 0), vh_list, vt_list;
+    for (int v = 0; v < nv; ++v) {
+        vh_ptr[v + 1] = vh_ptr[v] + (int)vh[v].size();
+        vt_ptr[v + 1] = vt_ptr[v] + (int)vt[v].size();
+        vh_list.insert(vh_list.end(), vh[v].begin(), vh[v].end());
+        vt_list.insert(vt_list.end(), vt[v].begin(), vt[v].end());
+    }
+    int rc = 0;
+    std::vector<double> X(verts, verts + 3 * (size_t)nv);
+    std::vector<int> T(tris, tris + 3 * (size_t)nt);
+    for (int k = 0; k < 3; ++k) b.X[k] = upload(c, X, &rc);  // x(t-dt) = x(t) at start
+    b.U = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
+    b.Ub = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
+    b.Fl = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
+    b.phi = (double *)dev_alloc(c, sizeof(double) * 27 * (size_t)nv);
+    b.node = (int *)dev_alloc(c, sizeof(int) * 27 * (size_t)nv);
+    b.tri = upload(c, T, &rc);
+    b.tri_geo = (double *)dev_alloc(c, sizeof(double) * 8 * (size_t)nt);
+    b.probe = (double *)dev_alloc(c, sizeof(double) * 8 * (size_t)nt);
+    b.vh_ptr = upload(c, vh_ptr, &rc);
+    b.vh_list = upload(c, vh_list, &rc);
+    b.vt_ptr = upload(c, vt_ptr, &rc);
+    b.vt_list = upload(c, vt_list, &rc);
+    b.hinge = upload(c, hinge, &rc);
+    b.ks = upload(c, ks, &rc);
+    b.l0 = upload(c, l0, &rc);
+    b.kb = upload(c, kb, &rc);
+    b.theta0 = upload(c, th0, &rc);
+    if (b.rigid) {
+        double V, cen[3], I[9];
+        mass_props(verts, nt, tris, &V, cen, I);
+        std::vector<double> Xb(3 * (size_t)nv), st(RigidState::SIZE, 0.0);
+        for (int v = 0; v < nv; ++v)
+            for (int a = 0; a < 3; ++a) Xb[3 * v + a] = verts[3 * v + a] - cen[a];
+        const double rs = bp->density_ratio;
+        for (int a = 0; a < 3; ++a) {
+            st[RigidState::XC + a] = cen[a];
+            st[RigidState::XC_OLD + a] = cen[a];
+            st[RigidState::U + a] = st[RigidState::UP + a] = bp->u0[a];
+            st[RigidState::W + a] = st[RigidState::WP + a] = bp->omega0[a];
+            st[RigidState::GRAV + a] = bp->gravity[a];
+        }
+        st[RigidState::Q4] = 1.0;
+        st[RigidState::ROT] = st[RigidState::ROT + 4] = st[RigidState::ROT + 8] = 1.0;
+        for (int k = 0; k < 9; ++k) st[RigidState::IB + k] = rs * I[k];
+        st[RigidState::MASS] = rs * V;
+        st[RigidState::VOL] = V;
+        st[RigidState::DENS] = rs;
+        b.Xbody = upload(c, Xb, &rc);
+        b.rstate = upload(c, st, &rc);
+    }
+    if (rc || !b.phi || !b.node || !b.tri_geo || !b.probe) {
+        c->err = rc ? rc : LBIB_ENOMEM;
+        return fail(c, c->err, "body allocation or upload failed");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);  // host vectors are released on return
+    if (e != cudaSuccess) return cuda_fail(c, e, "add_body upload");
+    c->bodies.push_back(b);
+    if (body_id) *body_id = (int)c->bodies.size() - 1;
+    return LBIB_OK;
+}
+
+int lbib_step(void *h, int nsteps) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (c->err) return c->err;
+    if (nsteps < 0) return fail(c, LBIB_EINVAL, "nsteps < 0");
+    for (int it = 0; it < nsteps; ++it) {
+        if (++c->stamp_step == 0) {  // flag wrap-around: clear the tile flags
+            cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
+            c->stamp_step = 1;
+        }
+        cudaEvent_t *ev = nullptr;
+        if (c->profile) {
+            if (c->nev + 3 > c->events.size())
+                for (int k = 0; k < 3; ++k) {
+                    cudaEvent_t x;
+                    if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
+                    c->events.push_back(x);
+                }
+            ev = &c->events[c->nev];
+            c->nev += 3;
+            cudaEventRecord(ev[0], c->stream);
+        }
+        for (auto &b : c->bodies) {
+            const BodyView v = make_view(c, b);
+            cudaError_t e = launch_mls(c->prec, c->fA, c->L, v, c->d_err, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernel");
+            if (b.rigid) {
+                e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, c->stream);
+                c->launches += 3;
+            } else {
+                e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, c->stream);
+                c->launches += 2;
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
+        }
+        if (ev) cudaEventRecord(ev[1], c->stream);
+        cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L,
+                                     it == nsteps - 1 ? c->fields : nullptr, c->stream);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
+        if (ev) cudaEventRecord(ev[2], c->stream);
+        std::swap(c->fA, c->fB);
+        for (auto &b : c->bodies) b.cur = (b.cur + 1) % 3;
+        c->steps++;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "error word copy");
+    return LBIB_OK;
+}
+
+int lbib_sync(void *h) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    return sync_ctx(c);
+}
+
+int lbib_get_fields(void *h, double *rho, double *u, int on_device) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    int rc = sync_ctx(c);
+    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    const size_t n = (size_t)c->L.ncell;
+    double *drho = rho, *du = u;
+    if (!on_device) {
+        double *tmp = get_scratch(c, 4 * n * sizeof(double));
+        if (!tmp) return fail(c, LBIB_ENOMEM, "scratch allocation failed");
+        drho = rho ? tmp : nullptr;
+        du = u ? tmp + n : nullptr;
+    }
+    cudaError_t e = launch_fields_out(c->prec, c->fields, c->L, drho, du, c->stream);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "fields kernel");
+    if (!on_device) {
+        if (rho) e = cudaMemcpyAsync(rho, drho, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "fields copy");
+    }
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fields sync");
+    return rc;
+}
+
+int lbib_get_populations(void *h, double *f, int on_device) {
+    Ctx *c = as_ctx(h);
+    if (!c || !f) return LBIB_EINVAL;
+    int rc = sync_ctx(c);
+    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    const size_t n = (size_t)c->L.ncell * Q;
+    double *df = f;
+    if (!on_device) {
+        df = get_scratch(c, n * sizeof(double));
+        if (!df) return fail(c, LBIB_ENOMEM, "scratch allocation failed");
+    }
+    cudaError_t e = launch_pop_to_aos(c->prec, c->fA, c->L, df, c->stream);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "populations kernel");
+    if (!on_device) {
+        e = cudaMemcpyAsync(f, df, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "populations copy");
+    }
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "populations sync");
+    return rc;
+}
+
+int lbib_get_markers(void *h, int body, double *X, double *V, double *F) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
+    int rc = sync_ctx(c);
+    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    DevBody &b = c->bodies[body];
+    const size_t bytes = 3 * (size_t)b.nv * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (X) e = cudaMemcpy(X, b.X[b.cur], bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && V) e = cudaMemcpy(V, b.Ub, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && F) e = cudaMemcpy(F, b.Fl, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "markers copy");
+    return rc;
+}
+
+int lbib_get_body(void *h, int body, lbib_body_state *out) {
+    Ctx *c = as_ctx(h);
+    if (!c || !out) return LBIB_EINVAL;
+    if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
+    DevBody &b = c->bodies[body];
+    std::vector<double> X(3 * (size_t)b.nv), Ub(3 * (size_t)b.nv);
+    int rc = lbib_get_markers(h, body, X.data(), Ub.data(), nullptr);
+    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    std::memset(out, 0, sizeof(*out));
+    if (b.rigid) {
+        double st[RigidState::SIZE];
+        cudaError_t e = cudaMemcpy(st, b.rstate, sizeof(st), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "body state copy");
+        for (int a = 0; a < 3; ++a) {
+            out->xc[a] = st[RigidState::XC + a];
+            out->u[a] = st[RigidState::U + a];
+            out->omega[a] = st[RigidState::W + a];
+        }
+        for (int k = 0; k < 4; ++k) out->q[k] = st[RigidState::Q4 + k];
+    } else {
+        for (int v = 0; v < b.nv; ++v)
+            for (int a = 0; a < 3; ++a) {
+                out->xc[a] += X[3 * v + a] / b.nv;
+                out->u[a] += Ub[3 * v + a] / b.nv;
+            }
+        out->q[0] = 1.0;
+    }
+    std::vector<int> T(3 * (size_t)b.nt);
+    cudaError_t e = cudaMemcpy(T.data(), b.tri, T.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "triangles copy");
+    double V = 0, A = 0;
+    for (int t = 0; t < b.nt; ++t) {
+        double cr[3];
+        v_cross(&X[3 * T[3 * t + 1]], &X[3 * T[3 * t + 2]], cr);
+        V += v_dot(&X[3 * T[3 * t]], cr) / 6.0;
+        A += tri_area(X.data(), &T[3 * t]);
+    }
+    out->volume = V;
+    out->area = A;
+    return rc;
+}
+
+int lbib_counters(void *h, long long *steps, long long *launches) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (steps) *steps = c->steps;
+    if (launches) *launches = c->launches;
+    return LBIB_OK;
+}
+
+int lbib_profile(void *h, int enable) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    c->profile = enable != 0;
+    return LBIB_OK;
+}
+
+int lbib_get_profile(void *h, double *sweep_ms, double *ib_ms, long long *nsteps) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+    double sw = 0.0, ib = 0.0;
+    for (size_t k = 0; k + 2 < c->nev + 1 && k < c->nev; k += 3) {
+        float a = 0.f, b2 = 0.f;
+        cudaEventElapsedTime(&a, c->events[k], c->events[k + 1]);
+        cudaEventElapsedTime(&b2, c->events[k + 1], c->events[k + 2]);
+        ib += a;
+        sw += b2;
+    }
+    if (sweep_ms) *sweep_ms = sw;
+    if (ib_ms) *ib_ms = ib;
+    if (nsteps) *nsteps = (long long)(c->nev / 3);
+    c->nev = 0;
+    return LBIB_OK;
+}
+
+int lbib_device_bytes(void *h, size_t *bytes) {
+    Ctx *c = as_ctx(h);
+    if (!c || !bytes) return LBIB_EINVAL;
+    *bytes = c->bytes;
+    return LBIB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Device-side definitions shared by the kernels of liblbib: the D3Q19
+// molecule, storage conversions and the views of lattice and body state
+// that kernels receive by value.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbib {
+
+constexpr int Q = 19;
+constexpr int kPeriodic = 0;
+constexpr int kWall = 1;
+constexpr int kTile = 8;  // edge of the cubic tiles that carry an IB-force flag
+
+// D3Q19 velocities, columns of the matrix of Eq. (e_i), Sec. 2.1.
+__host__ __device__ constexpr int ex(int i) {
+    return (i == 1 || i == 7 || i == 8 || i == 9 || i == 10) ? 1
+           : (i == 2 || i == 11 || i == 12 || i == 13 || i == 14) ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int ey(int i) {
+    return (i == 3 || i == 7 || i == 11 || i == 15 || i == 16) ? 1
+           : (i == 4 || i == 8 || i == 12 || i == 17 || i == 18) ? -1
+                                                                 : 0;
+}
+__host__ __device__ constexpr int ez(int i) {
+    return (i == 5 || i == 9 || i == 13 || i == 15 || i == 17) ? 1
+           : (i == 6 || i == 10 || i == 14 || i == 16 || i == 18) ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int ecomp(int i, int a) { return a == 0 ? ex(i) : a == 1 ? ey(i) : ez(i); }
+// opposite direction: e_opp(i) = -e_i
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : i <= 6 ? (i % 2 ? i + 1 : i - 1) : i == 7 ? 12 : i == 8 ? 11 : i == 9 ? 14 : i == 10 ? 13
+         : i == 11 ? 8 : i == 12 ? 7 : i == 13 ? 10 : i == 14 ? 9 : i == 15 ? 18 : i == 16 ? 17 : i == 17 ? 16 : 15;
+}
+// weights: 1/3, 1/18 (axis), 1/36 (diagonals), stated after Eq. (eqfunc)
+template <typename R>
+__host__ __device__ constexpr R wq(int i) {
+    return i == 0 ? R(1) / R(3) : i <= 6 ? R(1) / R(18) : R(1) / R(36);
+}
+
+constexpr bool lattice_is_consistent() {
+    for (int i = 0; i < Q; ++i) {
+        int o = opp(i);
+        if (ex(o) != -ex(i) || ey(o) != -ey(i) || ez(o) != -ez(i)) return false;
+        int n2 = ex(i) * ex(i) + ey(i) * ey(i) + ez(i) * ez(i);
+        if ((i == 0) != (n2 == 0) || (i >= 1 && i <= 6) != (n2 == 1)) return false;
+    }
+    return true;
+}
+static_assert(lattice_is_consistent(), "D3Q19 table");
+
+// ---- population storage: S is the stored type, arithmetic is float or double ----
+// Populations are stored as deviations g_i = f_i - w_i from the resting
+// equilibrium; half and bfloat16 storage scale them by kHalfScale to stay
+// clear of subnormals.
+constexpr float kHalfScale = 256.0f;
+
+template <typename S, typename R>
+struct Pop;
+template <>
+struct Pop<double, double> {
+    __device__ static double ld(const double *p) { return __ldg(p); }
+    __device__ static void st(double *p, double v) { __stcs(p, v); }
+};
+template <>
+struct Pop<float, float> {
+    __device__ static float ld(const float *p) { return __ldg(p); }
+    __device__ static void st(float *p, float v) { __stcs(p, v); }
+};
+template <>
+struct Pop<__half, float> {
+    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)) * (1.0f / kHalfScale); }
+    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
+};
+template <>
+struct Pop<__nv_bfloat16, float> {
+    __device__ static float ld(const __nv_bfloat16 *p) {
+        return __bfloat162float(__ldg(p)) * (1.0f / kHalfScale);
+    }
+    __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v * kHalfScale); }
+};
+
+// ---- views passed by value to kernels ----
+struct Lattice {
+    int nx, ny, nz;
+    int ntx, nty, ntz;      // tiles per axis
+    int ncell;              // nx*ny*nz
+    long long stride;       // elements between population planes (ncell padded)
+    int bc[3];
+    double tau;
+    double gext[3];
+    double wall_u[6][3];
+    double dist2_cut;       // largest |X - x_k|^2 whose MLS weight is non-zero
+};
+
+struct BodyView {
+    int nv, nt, rigid;
+    const double *X;        // [3nv] positions of level n
+    const double *Xprev;    // [3nv] positions of level n-1
+    double *Xnew;           // [3nv] positions of level n+1 (written)
+    double *U;              // [3nv] interpolated fluid velocity
+    double *Ub;             // [3nv] boundary velocity imposed by the IB force
+    double *Fl;             // [3nv] Lagrangian IB force
+    double *phi;            // [27nv] MLS transfer weights of level n
+    int *node;              // [27nv] support node indices
+    const int *tri;         // [3nt]
+    double *tri_geo;        // [8nt] unit normal (3), area, centroid (3), volume term
+    double *probe;          // [8nt] per side: pressure p, traction tau.n (3)
+    // membrane topology (CSR over vertices)
+    const int *vh_ptr;      // [nv+1]
+    const int *vh_list;     // hinge*4 + role
+    const int *vt_ptr;      // [nv+1]
+    const int *vt_list;     // triangle*3 + corner
+    const int4 *hinge;      // (a, b, c, d)
+    const double *ks, *l0, *kb, *theta0;
+    double V0, mv, kv;
+    double origin[3];       // reference point of the enclosed-volume sum
+    int bend_variant;
+    // rigid body
+    const double *Xbody;    // [3nv] rest coordinates about the centre
+    double *rstate;         // rigid state block, see RigidState
+};
+
+// Layout of the rigid-body state block (doubles).
+struct RigidState {
+    enum {
+        XC = 0, Q4 = 3, U = 7, UP = 10, W = 13, WP = 16, XC_OLD = 19, ROT = 22, IB = 31, MASS = 40,
+        VOL = 41, DENS = 42, GRAV = 43, SIZE = 46
+    };
+};
+
+}  // namespace lbib

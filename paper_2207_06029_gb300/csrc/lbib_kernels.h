@@ -1,0 +1,28 @@
+// Host-side launchers of the liblbib kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbib_device.cuh"
+
+namespace lbib {
+
+// sweep.cu
+cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
+                         uint32_t step, const Lattice &L, void *fields, cudaStream_t s);
+cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
+                                    void *fields, cudaStream_t s);
+cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s);
+cudaError_t launch_aos_to_pop(int prec, const double *in, const Lattice &L, void *fout, cudaStream_t s);
+cudaError_t launch_fields_out(int prec, const void *fields, const Lattice &L, double *rho, double *u,
+                              cudaStream_t s);
+
+// ib.cu
+cudaError_t launch_mls(int prec, const void *fin, const Lattice &L, const BodyView &B, int *err, cudaStream_t s);
+cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
+                            uint32_t step, cudaStream_t s);
+cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
+                         uint32_t step, cudaStream_t s);
+
+}  // namespace lbib

@@ -1,0 +1,337 @@
+// Fused stream + wall + collide sweep over the whole lattice (Sec. 2.1,
+// Eq. evoleq with the equilibrium of Eq. eqfunc and the Guo term of
+// Eq. forcing), plus the kernels that initialise and export populations and
+// macroscopic fields.
+//
+// Design: one thread per node, pull streaming f_i(x) = f*_i(x - e_i) from
+// structure-of-arrays planes (x fastest, so every population load and store
+// of a warp is one contiguous 128-byte run except at the x-wrap), read-only
+// loads through the non-coherent path and evict-first stores.  The IB force
+// lives in a dense field that is read (and zeroed) only inside tiles flagged
+// for the current step, so untouched tiles cost one cached 4-byte flag read.
+#include "lbib_device.cuh"
+#include "lbib_kernels.h"
+
+namespace lbib {
+
+__host__ __device__ constexpr unsigned dirmask(int a, int sgn) {
+    unsigned m = 0;
+    for (int i = 0; i < Q; ++i)
+        if (ecomp(i, a) * sgn > 0) m |= 1u << i;
+    return m;
+}
+
+// Zou-He known-velocity wall on a face node with inward normal s*e_A
+// (s = +1 on the index-0 face).  In deviation form, with
+// sum_{e_A=0} w + 2 sum_{s e_A<0} w = 1:
+//   rho = (1 + sum0 g + 2 sumout g) / (1 - s uw_A)
+//   N_b = 1/2 sum_{e_A=0} g e_b - rho uw_b / 3
+//   g_i = g_opp + 6 w_i rho (e_i . uw) - sum_{b != A} e_ib N_b   (s e_iA > 0)
+template <int A, typename R>
+__device__ __forceinline__ void zouhe_face(R (&g)[Q], int s, const double *uwd) {
+    const R uw[3] = {R(uwd[0]), R(uwd[1]), R(uwd[2])};
+    R sum0 = R(0), sumout = R(0), t[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int ea = ecomp(i, A);
+        if (ea == 0) {
+            sum0 += g[i];
+            if (ex(i)) t[0] += R(ex(i)) * g[i];
+            if (ey(i)) t[1] += R(ey(i)) * g[i];
+            if (ez(i)) t[2] += R(ez(i)) * g[i];
+        } else if (s * ea < 0) {
+            sumout += g[i];
+        }
+    }
+    const R rho = (R(1) + sum0 + R(2) * sumout) / (R(1) - R(s) * uw[A]);
+    R N[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) N[b] = (b == A) ? R(0) : R(0.5) * t[b] - rho * uw[b] / R(3);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int ea = ecomp(i, A);
+        if (ea != 0 && s * ea > 0) {
+            const R eu = R(ex(i)) * uw[0] + R(ey(i)) * uw[1] + R(ez(i)) * uw[2];
+            R corr = R(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                if (b != A && ecomp(i, b) != 0) corr += R(ecomp(i, b)) * N[b];
+            g[i] = g[opp(i)] + R(6) * wq<R>(i) * rho * eu - corr;
+        }
+    }
+}
+
+// Edge and corner nodes: unknown populations (incoming through any of the
+// node's walls) bounce back with the moving-wall momentum term at the mean
+// wall velocity and rho0 = 1; buried links (opposite also unknown) take
+// the equilibrium f^eq(1, uw).
+template <typename R>
+__device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const double *uwd) {
+    const R uw[3] = {R(uwd[0]), R(uwd[1]), R(uwd[2])};
+    const R uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (!((unknown >> i) & 1u)) continue;
+        const R eu = R(ex(i)) * uw[0] + R(ey(i)) * uw[1] + R(ez(i)) * uw[2];
+        if (!((unknown >> opp(i)) & 1u))
+            g[i] = g[opp(i)] + R(6) * wq<R>(i) * eu;
+        else
+            g[i] = wq<R>(i) * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu);
+    }
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
+                                               R *__restrict__ force, const uint32_t *__restrict__ stamp,
+                                               uint32_t step, Lattice L, R *__restrict__ fields) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= L.ncell) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int x = idx % nx;
+    const int yz = idx / nx;
+    const int y = yz % ny;
+    const int z = yz / ny;
+    const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
+    // neighbour coordinates; on walled axes an outside source is clamped to
+    // the node itself (its value is unused: the wall rule overwrites it)
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    if (xm < 0) xm = px ? nx - 1 : 0;
+    if (xp >= nx) xp = px ? 0 : nx - 1;
+    if (ym < 0) ym = py ? ny - 1 : 0;
+    if (yp >= ny) yp = py ? 0 : ny - 1;
+    if (zm < 0) zm = pz ? nz - 1 : 0;
+    if (zp >= nz) zp = pz ? 0 : nz - 1;
+    const int nxy = nx * ny;
+    const int oy_m = ym * nx, oy_0 = y * nx, oy_p = yp * nx;
+    const int oz_m = zm * nxy, oz_0 = z * nxy, oz_p = zp * nxy;
+    const long long st = L.stride;
+
+    // pull: f_i(x) = f*_i(x - e_i)
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
+        const int sy = ey(i) > 0 ? oy_m : ey(i) < 0 ? oy_p : oy_0;
+        const int sz = ez(i) > 0 ? oz_m : ez(i) < 0 ? oz_p : oz_0;
+        g[i] = Pop<S, R>::ld(fin + (long long)i * st + (sx + sy + sz));
+    }
+
+    // walls (faces -x,+x,-y,+y,-z,+z; the index-0 face has inward normal +)
+    int nf = 0, fa = 0, fs = 0, face = 0;
+    unsigned unknown = 0;
+    double uwsum[3] = {0.0, 0.0, 0.0};
+    const int c[3] = {x, y, z}, n[3] = {nx, ny, nz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (L.bc[a] != kWall) continue;
+        int s = 0;
+        if (c[a] == 0)
+            s = 1;
+        else if (c[a] == n[a] - 1)
+            s = -1;
+        if (!s) continue;
+        ++nf;
+        fa = a;
+        fs = s;
+        face = 2 * a + (s < 0);
+        unknown |= (a == 0 ? (s > 0 ? dirmask(0, 1) : dirmask(0, -1))
+                           : a == 1 ? (s > 0 ? dirmask(1, 1) : dirmask(1, -1))
+                                    : (s > 0 ? dirmask(2, 1) : dirmask(2, -1)));
+    }
+    if (nf == 1) {
+        if (fa == 0)
+            zouhe_face<0>(g, fs, L.wall_u[face]);
+        else if (fa == 1)
+            zouhe_face<1>(g, fs, L.wall_u[face]);
+        else
+            zouhe_face<2>(g, fs, L.wall_u[face]);
+    } else if (nf > 1) {
+        for (int a = 0; a < 3; ++a) {
+            if (L.bc[a] != kWall) continue;
+            int s = c[a] == 0 ? 1 : (c[a] == n[a] - 1 ? -1 : 0);
+            if (!s) continue;
+            const int fc = 2 * a + (s < 0);
+            for (int b = 0; b < 3; ++b) uwsum[b] += L.wall_u[fc][b] / nf;
+        }
+        wall_corner(g, unknown, uwsum);
+    }
+
+    // moments of the streamed populations
+    R dr = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        dr += g[i];
+        if (ex(i) > 0) jx += g[i];
+        if (ex(i) < 0) jx -= g[i];
+        if (ey(i) > 0) jy += g[i];
+        if (ey(i) < 0) jy -= g[i];
+        if (ez(i) > 0) jz += g[i];
+        if (ez(i) < 0) jz -= g[i];
+    }
+    const R rho = R(1) + dr;
+
+    // body force f_lb = g_ext + f_ib (none on wall nodes); consume the IB
+    // force of flagged tiles
+    R F0 = R(0), F1 = R(0), F2 = R(0);
+    if (nf == 0) {
+        F0 = R(L.gext[0]);
+        F1 = R(L.gext[1]);
+        F2 = R(L.gext[2]);
+    }
+    const int tile = (x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3));
+    if (__ldg(stamp + tile) == step) {
+        const R fx = force[idx], fy = force[st + idx], fz = force[2 * st + idx];
+        force[idx] = R(0);
+        force[st + idx] = R(0);
+        force[2 * st + idx] = R(0);
+        if (nf == 0) {
+            F0 += fx;
+            F1 += fy;
+            F2 += fz;
+        }
+    }
+
+    // BGK collision with the Guo term, u = (sum f e + f_lb/2)/rho
+    const R inv = R(1) / rho;
+    const R ux = (jx + R(0.5) * F0) * inv, uy = (jy + R(0.5) * F1) * inv, uz = (jz + R(0.5) * F2) * inv;
+    const R omega = R(1.0 / L.tau), cF = R(1.0 - 0.5 / L.tau);
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * F0 + uy * F1 + uz * F2;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R eu = R(ex(i)) * ux + R(ey(i)) * uy + R(ez(i)) * uz;
+        const R eF = R(ex(i)) * F0 + R(ey(i)) * F1 + R(ez(i)) * F2;
+        const R w = wq<R>(i);
+        const R dfeq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
+        const R Fi = cF * w * (R(3) * (eF - uF) + R(9) * eu * eF);
+        const R gn = g[i] - omega * (g[i] - dfeq) + Fi;
+        Pop<S, R>::st(fout + (long long)i * st + idx, gn);
+    }
+    if (fields) {
+        fields[idx] = rho;
+        fields[st + idx] = ux;
+        fields[2 * st + idx] = uy;
+        fields[3 * st + idx] = uz;
+    }
+}
+
+// f = f^eq(rho, u) from double fields (Eq. eqfunc), stored as deviations.
+template <typename S, typename R>
+__global__ void k_init_equilibrium(S *__restrict__ fout, Lattice L, const double *__restrict__ rho,
+                                   const double *__restrict__ u, R *__restrict__ fields) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= L.ncell) return;
+    const double r = rho[idx], ux = u[3 * idx], uy = u[3 * idx + 1], uz = u[3 * idx + 2];
+    const double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double eu = ex(i) * ux + ey(i) * uy + ez(i) * uz;
+        const double w = wq<double>(i);
+        const double g = w * (r - 1.0) + w * r * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+        Pop<S, R>::st(fout + (long long)i * L.stride + idx, R(g));
+    }
+    fields[idx] = R(r);
+    fields[L.stride + idx] = R(ux);
+    fields[2 * L.stride + idx] = R(uy);
+    fields[3 * L.stride + idx] = R(uz);
+}
+
+template <typename S, typename R>
+__global__ void k_pop_to_aos(const S *__restrict__ fin, Lattice L, double *__restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= L.ncell) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        out[(long long)idx * Q + i] = wq<double>(i) + (double)Pop<S, R>::ld(fin + (long long)i * L.stride + idx);
+}
+
+template <typename S, typename R>
+__global__ void k_aos_to_pop(const double *__restrict__ in, Lattice L, S *__restrict__ fout) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= L.ncell) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        Pop<S, R>::st(fout + (long long)i * L.stride + idx, R(in[(long long)idx * Q + i] - wq<double>(i)));
+}
+
+template <typename R>
+__global__ void k_fields_out(const R *__restrict__ fields, Lattice L, double *__restrict__ rho,
+                             double *__restrict__ u) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= L.ncell) return;
+    if (rho) rho[idx] = (double)fields[idx];
+    if (u) {
+        u[3 * idx] = (double)fields[L.stride + idx];
+        u[3 * idx + 1] = (double)fields[2 * L.stride + idx];
+        u[3 * idx + 2] = (double)fields[3 * L.stride + idx];
+    }
+}
+
+// ---- host-side launchers (one per storage precision) ----
+static inline unsigned grid_for(int n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename S, typename R>
+static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, uint32_t step,
+                           const Lattice &L, void *fields, cudaStream_t s) {
+    k_sweep<S, R><<<grid_for(L.ncell, 256), 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
+                                                         (R *)fields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
+                         uint32_t step, const Lattice &L, void *fields, cudaStream_t s) {
+    switch (prec) {
+        case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, s);
+        case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, s);
+        case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, s);
+        default: return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, s);
+    }
+}
+
+cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
+                                    void *fields, cudaStream_t s) {
+    const unsigned g = grid_for(L.ncell, 256);
+    switch (prec) {
+        case 0: k_init_equilibrium<double, double><<<g, 256, 0, s>>>((double *)fout, L, rho, u, (double *)fields); break;
+        case 1: k_init_equilibrium<float, float><<<g, 256, 0, s>>>((float *)fout, L, rho, u, (float *)fields); break;
+        case 2: k_init_equilibrium<__half, float><<<g, 256, 0, s>>>((__half *)fout, L, rho, u, (float *)fields); break;
+        default:
+            k_init_equilibrium<__nv_bfloat16, float><<<g, 256, 0, s>>>((__nv_bfloat16 *)fout, L, rho, u,
+                                                                      (float *)fields);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s) {
+    const unsigned g = grid_for(L.ncell, 256);
+    switch (prec) {
+        case 0: k_pop_to_aos<double, double><<<g, 256, 0, s>>>((const double *)fin, L, out); break;
+        case 1: k_pop_to_aos<float, float><<<g, 256, 0, s>>>((const float *)fin, L, out); break;
+        case 2: k_pop_to_aos<__half, float><<<g, 256, 0, s>>>((const __half *)fin, L, out); break;
+        default: k_pop_to_aos<__nv_bfloat16, float><<<g, 256, 0, s>>>((const __nv_bfloat16 *)fin, L, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_pop(int prec, const double *in, const Lattice &L, void *fout, cudaStream_t s) {
+    const unsigned g = grid_for(L.ncell, 256);
+    switch (prec) {
+        case 0: k_aos_to_pop<double, double><<<g, 256, 0, s>>>(in, L, (double *)fout); break;
+        case 1: k_aos_to_pop<float, float><<<g, 256, 0, s>>>(in, L, (float *)fout); break;
+        case 2: k_aos_to_pop<__half, float><<<g, 256, 0, s>>>(in, L, (__half *)fout); break;
+        default: k_aos_to_pop<__nv_bfloat16, float><<<g, 256, 0, s>>>(in, L, (__nv_bfloat16 *)fout);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_out(int prec, const void *fields, const Lattice &L, double *rho, double *u,
+                              cudaStream_t s) {
+    const unsigned g = grid_for(L.ncell, 256);
+    if (prec == 0)
+        k_fields_out<double><<<g, 256, 0, s>>>((const double *)fields, L, rho, u);
+    else
+        k_fields_out<float><<<g, 256, 0, s>>>((const float *)fields, L, rho, u);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

@@ -1,0 +1,310 @@
+"""ctypes binding of liblbib (C ABI in include/lbib.h), with the same names.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  If the library is missing, importing a function raises
+``RuntimeError`` (there is no CPU fallback).  Arrays may be numpy arrays
+(host) or torch CUDA tensors (device, passed with ``on_device=1``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbib.so")
+
+LBIB_OK, LBIB_EINVAL, LBIB_ENOMEM, LBIB_ECUDA, LBIB_EDIVERGED, LBIB_EBODY_WALL, LBIB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBIB_FP64, LBIB_FP32, LBIB_FP16_DEV, LBIB_BF16_DEV = 0, 1, 2, 3
+LBIB_PERIODIC, LBIB_WALL = 0, 1
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class lbib_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("tau", C.c_double), ("body_force", C.c_double * 3),
+                ("bc", C.c_int * 3), ("wall_u", (C.c_double * 3) * 6),
+                ("precision", C.c_int), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class lbib_body_params(C.Structure):
+    _fields_ = [("rigid", C.c_int), ("ks0", C.c_double), ("Eb", C.c_double), ("kv", C.c_double),
+                ("thickness", C.c_double), ("density_ratio", C.c_double), ("ref_radius", C.c_double),
+                ("gravity", C.c_double * 3), ("u0", C.c_double * 3), ("omega0", C.c_double * 3),
+                ("bend_variant", C.c_int)]
+
+
+class lbib_body_state(C.Structure):
+    _fields_ = [("xc", C.c_double * 3), ("u", C.c_double * 3), ("omega", C.c_double * 3),
+                ("q", C.c_double * 4), ("volume", C.c_double), ("area", C.c_double)]
+
+
+class LbibError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbib error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
+           "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
+           "lbib_profile", "lbib_get_profile", "lbib_device_bytes", "lbib_destroy", "lbib_last_error"]
+
+
+def load():
+    """Loads liblbib.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblbib.so not found at {LIB_PATH}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.lbib_create.argtypes = [C.POINTER(lbib_params), C.POINTER(C.c_void_p)]
+        L.lbib_set_fields.argtypes = [vp, vp, vp, C.c_int]
+        L.lbib_set_populations.argtypes = [vp, vp, C.c_int]
+        L.lbib_add_body.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.POINTER(lbib_body_params), ip]
+        L.lbib_step.argtypes = [vp, C.c_int]
+        L.lbib_sync.argtypes = [vp]
+        L.lbib_get_fields.argtypes = [vp, vp, vp, C.c_int]
+        L.lbib_get_populations.argtypes = [vp, vp, C.c_int]
+        L.lbib_get_markers.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.lbib_get_body.argtypes = [vp, C.c_int, C.POINTER(lbib_body_state)]
+        L.lbib_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.lbib_profile.argtypes = [vp, C.c_int]
+        L.lbib_get_profile.argtypes = [vp, dp, dp, C.POINTER(C.c_longlong)]
+        L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.lbib_destroy.argtypes = [vp]
+        L.lbib_destroy.restype = None
+        L.lbib_last_error.argtypes = [vp]
+        L.lbib_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("lbib_destroy", "lbib_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(ctx, rc):
+    if rc != LBIB_OK:
+        msg = load().lbib_last_error(ctx)
+        raise LbibError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    """Host numpy array or CUDA tensor -> (pointer, on_device)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+    return a.ctypes.data_as(C.c_void_p), 0
+
+
+# ---- thin wrappers with the ABI names ------------------------------------------------
+
+def lbib_create(params: lbib_params):
+    h = C.c_void_p()
+    rc = load().lbib_create(C.byref(params), C.byref(h))
+    _check(None, rc)
+    return h
+
+
+def lbib_set_fields(ctx, rho, u):
+    pr, dev = _ptr(rho)
+    pu, _ = _ptr(u)
+    return _check(ctx, load().lbib_set_fields(ctx, pr, pu, dev))
+
+
+def lbib_set_populations(ctx, f):
+    pf, dev = _ptr(f)
+    return _check(ctx, load().lbib_set_populations(ctx, pf, dev))
+
+
+def lbib_add_body(ctx, verts, tris, bp: lbib_body_params):
+    verts = _host(verts, np.float64)
+    tris = _host(tris, np.int32)
+    bid = C.c_int(-1)
+    _check(ctx, load().lbib_add_body(ctx, verts.ctypes.data_as(C.c_void_p), verts.shape[0],
+                                     tris.ctypes.data_as(C.c_void_p), tris.shape[0], C.byref(bp), C.byref(bid)))
+    return bid.value
+
+
+def lbib_step(ctx, nsteps):
+    return _check(ctx, load().lbib_step(ctx, int(nsteps)))
+
+
+def lbib_sync(ctx):
+    return _check(ctx, load().lbib_sync(ctx))
+
+
+def lbib_get_fields(ctx, rho, u):
+    pr, dev = _ptr(rho)
+    pu, dev2 = _ptr(u)
+    return _check(ctx, load().lbib_get_fields(ctx, pr, pu, max(dev, dev2)))
+
+
+def lbib_get_populations(ctx, f):
+    pf, dev = _ptr(f)
+    return _check(ctx, load().lbib_get_populations(ctx, pf, dev))
+
+
+def lbib_get_markers(ctx, body, X=None, V=None, F=None):
+    return _check(ctx, load().lbib_get_markers(ctx, int(body), _ptr(X)[0], _ptr(V)[0], _ptr(F)[0]))
+
+
+def lbib_get_body(ctx, body):
+    st = lbib_body_state()
+    _check(ctx, load().lbib_get_body(ctx, int(body), C.byref(st)))
+    return st
+
+
+def lbib_counters(ctx):
+    s, l = C.c_longlong(), C.c_longlong()
+    _check(ctx, load().lbib_counters(ctx, C.byref(s), C.byref(l)))
+    return s.value, l.value
+
+
+def lbib_profile(ctx, enable):
+    return _check(ctx, load().lbib_profile(ctx, int(enable)))
+
+
+def lbib_get_profile(ctx):
+    a, b, n = C.c_double(), C.c_double(), C.c_longlong()
+    _check(ctx, load().lbib_get_profile(ctx, C.byref(a), C.byref(b), C.byref(n)))
+    return a.value, b.value, n.value
+
+
+def lbib_device_bytes(ctx):
+    n = C.c_size_t()
+    _check(ctx, load().lbib_device_bytes(ctx, C.byref(n)))
+    return n.value
+
+
+def lbib_destroy(ctx):
+    load().lbib_destroy(ctx)
+
+
+def lbib_last_error(ctx):
+    m = load().lbib_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---- convenience object used by tests and the benchmark ------------------------------
+
+def make_params(n, tau, *, bc=(0, 0, 0), wall_u=None, body_force=(0, 0, 0), precision=LBIB_FP32, stream=None):
+    p = lbib_params()
+    p.nx, p.ny, p.nz = (int(v) for v in n)
+    p.tau = float(tau)
+    for a in range(3):
+        p.body_force[a] = float(body_force[a])
+        p.bc[a] = int(bc[a])
+    w = np.zeros((6, 3)) if wall_u is None else np.asarray(wall_u, np.float64).reshape(6, 3)
+    for f in range(6):
+        for a in range(3):
+            p.wall_u[f][a] = float(w[f, a])
+    p.precision = int(precision)
+    p.stream = stream
+    return p
+
+
+def make_body_params(*, rigid=False, ks0=0.0, Eb=0.0, kv=0.0, thickness=1.0, density_ratio=1.0, ref_radius=1.0,
+                     gravity=(0, 0, 0), u0=(0, 0, 0), omega0=(0, 0, 0), bend_variant=0):
+    bp = lbib_body_params()
+    bp.rigid = int(rigid)
+    bp.ks0, bp.Eb, bp.kv = float(ks0), float(Eb), float(kv)
+    bp.thickness, bp.density_ratio, bp.ref_radius = float(thickness), float(density_ratio), float(ref_radius)
+    for a in range(3):
+        bp.gravity[a] = float(gravity[a])
+        bp.u0[a] = float(u0[a])
+        bp.omega0[a] = float(omega0[a])
+    bp.bend_variant = int(bend_variant)
+    return bp
+
+
+class Context:
+    """One lattice with its bodies on the GPU."""
+
+    def __init__(self, n, tau, *, bc=(0, 0, 0), wall_u=None, body_force=(0, 0, 0), precision=LBIB_FP32,
+                 stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.h = lbib_create(make_params(n, tau, bc=bc, wall_u=wall_u, body_force=body_force,
+                                         precision=precision, stream=stream))
+        self.nv = []
+
+    @classmethod
+    def from_case(cls, case, precision=None, stream=None):
+        ctx = cls(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, body_force=case.gext,
+                  precision=case.precision if precision is None else precision, stream=stream)
+        rho, u = case.initial_fields()
+        ctx.set_fields(rho, u)
+        for b in case.bodies:
+            ctx.add_body(b.verts, b.tris, **b.kwargs())
+        return ctx
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbib_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, rho, u):
+        lbib_set_fields(self.h, _host(rho, np.float64), _host(u, np.float64).reshape(-1))
+
+    def set_populations(self, f):
+        lbib_set_populations(self.h, _host(f, np.float64).reshape(-1))
+
+    def add_body(self, verts, tris, **kw):
+        bid = lbib_add_body(self.h, verts, tris, make_body_params(**kw))
+        self.nv.append(int(np.asarray(verts).shape[0]))
+        return bid
+
+    def step(self, n=1):
+        lbib_step(self.h, n)
+
+    def sync(self):
+        lbib_sync(self.h)
+
+    def fields(self):
+        rho = np.zeros(self.ncell)
+        u = np.zeros(3 * self.ncell)
+        lbib_get_fields(self.h, rho, u)
+        return rho, u.reshape(self.ncell, 3)
+
+    def populations(self):
+        f = np.zeros(19 * self.ncell)
+        lbib_get_populations(self.h, f)
+        return f.reshape(self.ncell, 19)
+
+    def markers(self, body=0):
+        nv = self.nv[body]
+        X, V, F = (np.zeros((nv, 3)) for _ in range(3))
+        lbib_get_markers(self.h, body, X, V, F)
+        return X, V, F
+
+    def body(self, body=0):
+        st = lbib_get_body(self.h, body)
+        return {"xc": np.array(st.xc), "u": np.array(st.u), "omega": np.array(st.omega), "q": np.array(st.q),
+                "volume": st.volume, "area": st.area}
+
+    def counters(self):
+        return lbib_counters(self.h)

@@ -1,0 +1,65 @@
+"""C-ABI checks that need no GPU: the library builds, loads, and exports
+every function that include/lbib.h declares; the Python binding uses the
+same names; a missing library is a loud error, never a fallback."""
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbib.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbib_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2207_06029_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_path_calls():
+    names = _declared()
+    for required in ["lbib_create", "lbib_add_body", "lbib_step", "lbib_get_fields", "lbib_get_markers",
+                     "lbib_destroy", "lbib_last_error", "lbib_sync"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lbib_[a-z_]+)\b", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_uses_the_same_names(libpath):
+    from paper_2207_06029_gb300 import lbib
+    L = lbib.load()
+    for name in _declared():
+        assert hasattr(L, name)
+        assert hasattr(lbib, name), f"binding lacks {name}"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    code = ("import paper_2207_06029_gb300.lbib as m; m.LIB_PATH = '/nonexistent/liblbib.so'\n"
+            "try:\n    m.load()\nexcept RuntimeError as e:\n    print('RAISED', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert "RAISED" in r.stdout and "no CPU fallback" in r.stdout
+
+
+def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
+    """Argument validation happens before any CUDA call."""
+    from paper_2207_06029_gb300 import lbib
+    for kw in [dict(n=(8, 8, 8), tau=0.5), dict(n=(0, 8, 8), tau=0.8), dict(n=(8, 8, 2), tau=0.8, bc=(0, 0, 1))]:
+        p = lbib.make_params(kw["n"], kw["tau"], bc=kw.get("bc", (0, 0, 0)))
+        with pytest.raises(lbib.LbibError) as ei:
+            lbib.lbib_create(p)
+        assert ei.value.code == lbib.LBIB_EINVAL
+    p = lbib.make_params((8, 8, 8), 0.8, precision=7)
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_create(p)

@@ -1,0 +1,221 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances: the FP64 build agrees with the oracle to 1e-12 relative
+(populations, fields, markers); the FP32 build to 1e-5 relative on the
+velocity field and 1e-4 lattice units on marker positions.  Relative means
+max |gpu - oracle| / max |oracle| over the array.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_06029_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_06029_gb300 import build, lbib as L
+    build.build()
+    L.load()
+    return L
+
+
+def run_gpu(L, case, steps, precision=None):
+    ctx = L.Context.from_case(case, precision=precision)
+    ctx.step(steps)
+    out = {"f": ctx.populations() if case.ncell <= 4_000_000 else None, "fields": ctx.fields(),
+           "markers": [ctx.markers(b) for b in range(len(case.bodies))],
+           "bodies": [ctx.body(b) for b in range(len(case.bodies))]}
+    ctx.close()
+    return out
+
+
+def run_oracle(case, steps):
+    s = oracle.Sim(case.n, case.tau, gext=case.gext, bc=case.bc, wall_u=case.wall_u.ravel())
+    s.set_fields(*case.initial_fields())
+    for b in case.bodies:
+        s.add_body(b.verts, b.tris, **b.kwargs())
+    rc = s.step(steps)
+    assert rc == 0
+    out = {"f": s.populations() if case.ncell <= 4_000_000 else None, "fields": s.fields(),
+           "markers": [s.markers(b) for b in range(len(case.bodies))],
+           "bodies": [s.body(b) for b in range(len(case.bodies))]}
+    s.close()
+    return out
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def check_fp64(g, o, tol=1e-12):
+    if o["f"] is not None:
+        assert rel(g["f"], o["f"]) < tol
+    assert rel(g["fields"][0], o["fields"][0]) < tol
+    assert rel(g["fields"][1], o["fields"][1]) < tol
+    for (Xg, Vg, Fg), (Xo, Vo, Fo) in zip(g["markers"], o["markers"]):
+        assert rel(Xg, Xo) < tol
+        assert np.abs(Vg - Vo).max() < tol * max(np.abs(Vo).max(), 1e-3)
+        assert np.abs(Fg - Fo).max() < tol * max(np.abs(Fo).max(), 1e-3) * 10
+
+
+# ---------------------------------------------------------------------------------------
+# FP64: the fluid alone
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [(3, 4, 5), (33, 17, 9)])
+def test_fp64_periodic_random_state(lbib, n):
+    """Tiny and ragged periodic lattices from a random populated state, with a
+    uniform body force (pull streaming and wrap at every face)."""
+    case = W.case_empty(n=n, tau=0.73, gext=(1e-5, -2e-5, 3e-6), seed=1)
+    rng = np.random.default_rng(2)
+    e, w = oracle.lattice()
+    f0 = w[None, :] * (1.0 + 0.02 * rng.standard_normal((case.ncell, 19)))
+    ctx = lbib.Context(case.n, case.tau, body_force=case.gext, precision=lbib.LBIB_FP64)
+    ctx.set_populations(f0)
+    ctx.step(7)
+    fg = ctx.populations()
+    rg, ug = ctx.fields()
+    ctx.close()
+    s = oracle.Sim(case.n, case.tau, gext=case.gext)
+    s.set_populations(f0.ravel())
+    assert s.step(7) == 0
+    assert rel(fg, s.populations()) < 1e-12
+    ro, uo = s.fields()
+    assert rel(rg, ro) < 1e-12 and rel(ug, uo) < 1e-12
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1), (0, 1, 1), (1, 0, 0)])
+def test_fp64_moving_walls_edges_corners(lbib, bc):
+    """Walled boxes with tangentially moving walls: Zou-He faces plus the
+    edge and corner rule."""
+    n = (7, 6, 9)
+    rng = np.random.default_rng(3)
+    wall_u = 0.02 * rng.standard_normal((6, 3))
+    for f in range(6):
+        wall_u[f, f // 2] = 0.0  # tangential wall motion
+    case = W.case_empty(n=n, tau=0.9, bc=bc, wall_u=wall_u, seed=4, amplitude=5e-3)
+    g = run_gpu(lbib, case, 25, precision=lbib.LBIB_FP64)
+    o = run_oracle(case, 25)
+    check_fp64(g, o)
+
+
+# ---------------------------------------------------------------------------------------
+# FP64: immersed bodies
+# ---------------------------------------------------------------------------------------
+
+def test_fp64_couette_rigid_sphere_full(lbib):
+    """32^3 Couette cell, z walls at -+0.01, rigid neutrally buoyant sphere of
+    radius 4 (642 markers), tau 1, 200 steps, FP64."""
+    case = W.case_couette_sphere()
+    g = run_gpu(lbib, case, case.steps)
+    o = run_oracle(case, case.steps)
+    check_fp64(g, o)
+    bg, bo = g["bodies"][0], o["bodies"][0]
+    assert np.abs(bg["omega"] - bo["omega"]).max() < 1e-12 * np.abs(bo["omega"]).max()
+    assert np.abs(bg["xc"] - bo["xc"]).max() < 1e-12 * 16
+
+
+@pytest.mark.parametrize("bend_variant", [0, 1])
+def test_fp64_capsule_in_shear(lbib, bend_variant):
+    """Deformable capsule (springs, bending, volume, probes, Verlet) in a 24^3
+    Couette cell, 40 steps, FP64."""
+    case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.05,
+                                kv=1.0, precision=W.PREC_FP64)
+    case.bodies[0].bend_variant = bend_variant
+    case.bodies[0].verts = W.perturb(case.bodies[0].verts, 0.02, seed=11)
+    g = run_gpu(lbib, case, 40)
+    o = run_oracle(case, 40)
+    check_fp64(g, o)
+
+
+def test_fp64_two_bodies_and_gravity_periodic(lbib):
+    """Two bodies in one periodic lattice: a settling rigid sphere and a
+    capsule (shared force field, several spreads per step)."""
+    n = (26, 22, 30)
+    v1, f1 = W.icosphere(2, 3.0, (7.2, 10.9, 20.1))
+    v2, f2 = W.icosphere(2, 3.5, (18.4, 11.3, 9.7))
+    case = W.Case("two_bodies", n, 0.7, (0, 0, 0), np.zeros((6, 3)), precision=W.PREC_FP64, steps=30,
+                  bodies=[W.Body(v1, f1, rigid=True, density_ratio=1.3, ref_radius=3.0, gravity=(0, 0, -2e-5)),
+                          W.Body(v2, f2, ks0=5e-3, Eb=0.02, kv=1.0, density_ratio=2.0, ref_radius=3.5)])
+    g = run_gpu(lbib, case, 30)
+    o = run_oracle(case, 30)
+    check_fp64(g, o)
+
+
+# ---------------------------------------------------------------------------------------
+# FP32 at the benchmark sizes
+# ---------------------------------------------------------------------------------------
+
+def check_fp32(g, o, pos_tol=1e-4, vel_tol=1e-5):
+    ug, uo = g["fields"][1], o["fields"][1]
+    assert rel(ug, uo) < vel_tol
+    assert np.abs(g["fields"][0] - o["fields"][0]).max() < 1e-6
+    for (Xg, _, _), (Xo, _, _) in zip(g["markers"], o["markers"]):
+        assert np.abs(Xg - Xo).max() < pos_tol
+
+
+@pytest.mark.parametrize("Ca", [0.01, 0.05, 0.2])
+def test_fp32_capsule_96_full_size(lbib, Ca):
+    """96^3 capsule in shear (radius 10, 2562 markers, 5120 triangles),
+    tau 0.8, shear rate 1e-4, FP32 storage and arithmetic, 60 steps."""
+    case = W.case_capsule_shear(Ca=Ca, kv=1.0)
+    g = run_gpu(lbib, case, 60)
+    o = run_oracle(case, 60)
+    check_fp32(g, o)
+
+
+def test_fp32_settling_box_full_size(lbib):
+    """160x160x480 walled box, rigid sphere radius 8 (10242 markers), tau 0.7,
+    FP32, 3 steps; fields and markers."""
+    case = W.case_settling()
+    g = run_gpu(lbib, case, 3)
+    o = run_oracle(case, 3)
+    check_fp32(g, o)
+
+
+# ---------------------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------------------
+
+def test_zero_steps_and_empty_lattice(lbib):
+    case = W.case_empty(n=(5, 4, 3), precision=W.PREC_FP64, seed=7)
+    ctx = lbib.Context.from_case(case)
+    ctx.step(0)
+    rho, u = ctx.fields()
+    r0, u0 = case.initial_fields()
+    assert np.abs(rho - r0).max() < 1e-15 and np.abs(u - u0).max() < 1e-15
+    ctx.close()
+
+
+def test_support_reaching_wall_reports_error(lbib):
+    n = 16
+    v, f = W.icosphere(1, 2.0, (8.0, 8.0, 3.2))
+    ctx = lbib.Context((n, n, n), 0.8, bc=(0, 0, 1), precision=lbib.LBIB_FP64)
+    ctx.add_body(v, f, rigid=True, ref_radius=2.0)
+    ctx.step(1)
+    with pytest.raises(lbib.LbibError) as ei:
+        ctx.sync()
+    assert ei.value.code == lbib.LBIB_EBODY_WALL
+    with pytest.raises(lbib.LbibError):
+        ctx.step(1)  # sticky
+    ctx.close()
+
+
+def test_invalid_bodies_rejected(lbib):
+    ctx = lbib.Context((16, 16, 16), 0.8, precision=lbib.LBIB_FP32)
+    v, f = W.icosphere(1, 3.0, (8, 8, 8))
+    with pytest.raises(lbib.LbibError):
+        ctx.add_body(v, f[:-1])  # open mesh
+    with pytest.raises(lbib.LbibError):
+        ctx.add_body(v, f[:, ::-1].copy())  # inward orientation
+    with pytest.raises(lbib.LbibError):
+        ctx.add_body(v, f, density_ratio=0.0)
+    ctx.close()
