@@ -151,10 +151,18 @@ int lbib_counters(void *ctx, long long *steps, long long *launches);
  * step, recorded on the context stream. */
 int lbib_profile(void *ctx, int enable);
 
-/* Timing since profiling was enabled or last read: total milliseconds of
- * the collide-stream sweeps and of the IB kernels, and the number of steps
- * timed.  Synchronises and resets the accumulators. */
-int lbib_get_profile(void *ctx, double *sweep_ms, double *ib_ms, long long *nsteps);
+/* Timing since profiling was enabled or last read: ms[0] total
+ * milliseconds of the MLS stage (support-region moments, interpolation and
+ * probes), ms[1] of the structure update and spreading, ms[2] of the
+ * collide-stream sweeps; nsteps receives the number of steps timed.
+ * Synchronises and resets the accumulators. */
+int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
+
+/* When the sweep also writes the macroscopic fields read by
+ * lbib_get_fields: fields_every = 0 (default) on the last step of each
+ * lbib_step call, k > 0 on every k-th step, < 0 never (lbib_get_fields then
+ * returns the fields of the last step that wrote them). */
+int lbib_set_output(void *ctx, int fields_every);
 
 /* Bytes of device memory held by the context. */
 int lbib_device_bytes(void *ctx, size_t *bytes);

@@ -4,22 +4,90 @@
 // Eqs. strainFor, bendFor, volFor, newtonSoft, verletPos, verletVel;
 // Sec. 2.2, Eq. bodyforce) and the rigid-body Newton-Euler update
 // (Eqs. linearVelRig, angularVelRig).
+//
+// Per step and body: k_moments streams the populations once for every node
+// of the body's support region (predictor density and velocity), k_mls
+// fits at every marker and probe from those node moments, and one
+// structure kernel updates the markers and spreads the IB force.
 #include "lbib_device.cuh"
 #include "lbib_kernels.h"
 
 namespace lbib {
 
-constexpr int kPts = 32;         // MLS points per block
+constexpr int kPts = 32;          // MLS points per block
 constexpr int kMlsThreads = 128;  // 4 warps, 8 points each
 constexpr double kAlpha = 0.3;    // Eq. (intKernel)
 constexpr double kRw = 1.3;       // support size r_w (Sec. 2.2)
 constexpr double kProbe = 1.2;    // probe length (Sec. 2.3)
+constexpr int kBoxLo = 3, kBoxHi = 4;  // node margins that cover marker and probe supports
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ---------------------------------------------------------------------------
+// Predictor moments on the support region: for every node of the box,
+// pull the 19 populations (f_i(x) = f*_i(x - e_i)) and store
+// rho - 1 and u* = (sum f e + g_ext/2)/rho.  Grid-stride over the box
+// recorded on the device by the previous step's update.
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Lattice L, const int *__restrict__ box,
+                                                 int *__restrict__ box_next, R *__restrict__ mom) {
+    const int n[3] = {L.nx, L.ny, L.nz};
+    int lo[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        long long l = box[a], h = box[3 + a];
+        if (L.bc[a] == kWall) {
+            l = l < 0 ? 0 : l;
+            h = h > n[a] - 1 ? n[a] - 1 : h;
+        } else if (h - l + 1 > n[a]) {
+            l = 0;
+            h = n[a] - 1;
+        }
+        lo[a] = (int)l;
+        ext[a] = h < l ? 0 : (int)(h - l + 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 6) box_next[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+    const int total = ext[0] * ext[1] * ext[2];
+    const int nxy = L.nx * L.ny;
+    const long long st = L.stride;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
+        int cm[3], cp[3];
+        for (int a = 0; a < 3; ++a) {
+            if (L.bc[a] == kPeriodic) c[a] = ((c[a] % n[a]) + n[a]) % n[a];
+            int vm = c[a] - 1, vp = c[a] + 1;
+            if (vm < 0) vm = L.bc[a] == kPeriodic ? n[a] - 1 : 0;
+            if (vp >= n[a]) vp = L.bc[a] == kPeriodic ? 0 : n[a] - 1;
+            cm[a] = vm;
+            cp[a] = vp;
+        }
+        R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int sx = ex(i) > 0 ? cm[0] : ex(i) < 0 ? cp[0] : c[0];
+            const int sy = ey(i) > 0 ? cm[1] : ey(i) < 0 ? cp[1] : c[1];
+            const int sz = ez(i) > 0 ? cm[2] : ez(i) < 0 ? cp[2] : c[2];
+            const R gi = Pop<S, R>::ld(fin + (long long)i * st + (sx + L.nx * sy + nxy * sz));
+            drho += gi;
+            if (ex(i) > 0) jx += gi;
+            if (ex(i) < 0) jx -= gi;
+            if (ey(i) > 0) jy += gi;
+            if (ey(i) < 0) jy -= gi;
+            if (ez(i) > 0) jz += gi;
+            if (ez(i) < 0) jz -= gi;
+        }
+        const int node = c[0] + L.nx * c[1] + nxy * c[2];
+        const R rho = R(1) + drho;
+        mom[node] = drho;
+        mom[st + node] = (jx + R(0.5 * L.gext[0])) / rho;
+        mom[2 * st + node] = (jy + R(0.5 * L.gext[1])) / rho;
+        mom[3 * st + node] = (jz + R(0.5 * L.gext[2])) / rho;
+    }
 }
 
 template <typename R>
@@ -29,6 +97,7 @@ struct MlsSmem {
     R rho[kPts][27];
     R u[kPts][27][3];
     R nrm[kPts][3];
+    double vol[kPts];
     double A[kPts][10];
     double Ai[kPts][16];
 };
@@ -40,30 +109,30 @@ __device__ bool spd_inverse4(const double *a, double *inv) {
     M[0][0] = a[0]; M[0][1] = M[1][0] = a[1]; M[0][2] = M[2][0] = a[2]; M[0][3] = M[3][0] = a[3];
     M[1][1] = a[4]; M[1][2] = M[2][1] = a[5]; M[1][3] = M[3][1] = a[6];
     M[2][2] = a[7]; M[2][3] = M[3][2] = a[8]; M[3][3] = a[9];
-    double L[4][4] = {{0}}, Li[4][4] = {{0}};
+    double Lw[4][4] = {{0}}, Li[4][4] = {{0}};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         double s = M[j][j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        for (int k = 0; k < j; ++k) s -= Lw[j][k] * Lw[j][k];
         if (!(s > 0.0)) return false;
-        L[j][j] = sqrt(s);
+        Lw[j][j] = sqrt(s);
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
             double t = M[i][j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-            L[i][j] = t / L[j][j];
+            for (int k = 0; k < j; ++k) t -= Lw[i][k] * Lw[j][k];
+            Lw[i][j] = t / Lw[j][j];
         }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        Li[i][i] = 1.0 / L[i][i];
+        Li[i][i] = 1.0 / Lw[i][i];
 #pragma unroll
         for (int j = 0; j < i; ++j) {
             double t = 0.0;
 #pragma unroll
-            for (int k = j; k < i; ++k) t += L[i][k] * Li[k][j];
+            for (int k = j; k < i; ++k) t += Lw[i][k] * Li[k][j];
             Li[i][j] = -t * Li[i][i];
         }
     }
@@ -101,14 +170,14 @@ __device__ __forceinline__ void tri_geometry(const double *X, const int *t, cons
 // One warp per point, 32 points per block.  Points 0..nv-1 are the markers;
 // point nv + 2t + side is the probe of triangle t on the outer (side 0) or
 // inner (side 1) face.
-//  phase 1: support block, weights, streamed moments at the 27 nodes and the
-//           moment matrix A (warp reduction);
+//  phase 1: support block, weights (the r_k <= 1 decision bit-exact in
+//           FP64), node moments, moment matrix A (warp reduction);
 //  phase 2: warp 0 inverts the 32 matrices in FP64, one lane each;
 //  phase 3: shape functions psi_k = W_k A^-1 p_k; markers interpolate U and
 //           keep phi = psi[0] for spreading; probes fit rho and u and store
 //           pressure and traction.
-template <typename S, typename R>
-__global__ void __launch_bounds__(kMlsThreads) k_mls(const S *__restrict__ fin, Lattice L, BodyView B,
+template <typename R>
+__global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, Lattice L, BodyView B,
                                                      int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlsSmem<R> &sm = *reinterpret_cast<MlsSmem<R> *>(smem_raw);
@@ -118,6 +187,8 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const S *__restrict__ fin, 
     const long long st = L.stride;
     const int nxy = L.nx * L.ny;
     const int n[3] = {L.nx, L.ny, L.nz};
+    if (threadIdx.x < kPts) sm.vol[threadIdx.x] = 0.0;
+    __syncthreads();
 
     // ---------------- phase 1 ----------------
     for (int j = 0; j < kPts / 4; ++j) {
@@ -150,6 +221,7 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const S *__restrict__ fin, 
                     tg[5] = cen[1];
                     tg[6] = cen[2];
                     tg[7] = vol6;
+                    sm.vol[lp] = vol6;
                 }
             }
         }
@@ -164,15 +236,16 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const S *__restrict__ fin, 
             }
         }
         if (bad && lane == 0) atomicCAS(err, 0, -5);
-        R W = R(0), dk[3] = {R(0), R(0), R(0)}, drho = R(0), uk[3] = {R(0), R(0), R(0)};
+        R W = R(0), dk[3] = {R(0), R(0), R(0)};
         if (lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-            int c[3];
+            int cw[3];
             double dx[3];
             for (int a = 0; a < 3; ++a) {
-                c[a] = base[a] + dd[a];
-                dx[a] = (double)c[a] - P[a];
+                const int c = base[a] + dd[a];
+                dx[a] = (double)c - P[a];
                 dk[a] = R(dx[a]);
+                cw[a] = L.bc[a] == kPeriodic ? ((c % n[a]) + n[a]) % n[a] : c;
             }
             // |x_k - X|^2 rounded exactly as the plain sum of squares, so the
             // cut-off r_k <= 1 of Eq. (intKernel) is decided bit for bit
@@ -182,46 +255,14 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const S *__restrict__ fin, 
                 const R r = sqrt(R(dist2)) / R(kRw);
                 W = exp(-(r / R(kAlpha)) * (r / R(kAlpha)));
             }
-            // node coordinates (periodic wrap) and its streamed populations
-            int cw[3], cm[3], cp[3];
-            for (int a = 0; a < 3; ++a) {
-                int v = c[a];
-                if (L.bc[a] == kPeriodic) v = ((v % n[a]) + n[a]) % n[a];
-                cw[a] = v;
-                int vm = v - 1, vp = v + 1;
-                if (vm < 0) vm = L.bc[a] == kPeriodic ? n[a] - 1 : 0;
-                if (vp >= n[a]) vp = L.bc[a] == kPeriodic ? 0 : n[a] - 1;
-                cm[a] = vm;
-                cp[a] = vp;
-            }
             const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
             if (p < B.nv) B.node[27 * p + lane] = node;
-            R jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int sx = ex(i) > 0 ? cm[0] : ex(i) < 0 ? cp[0] : cw[0];
-                const int sy = ey(i) > 0 ? cm[1] : ey(i) < 0 ? cp[1] : cw[1];
-                const int sz = ez(i) > 0 ? cm[2] : ez(i) < 0 ? cp[2] : cw[2];
-                const R gi = Pop<S, R>::ld(fin + (long long)i * st + (sx + L.nx * sy + nxy * sz));
-                drho += gi;
-                if (ex(i) > 0) jx += gi;
-                if (ex(i) < 0) jx -= gi;
-                if (ey(i) > 0) jy += gi;
-                if (ey(i) < 0) jy -= gi;
-                if (ez(i) > 0) jz += gi;
-                if (ez(i) < 0) jz -= gi;
-            }
-            // predictor velocity u* = (sum f e + g_ext/2)/rho (support nodes are not wall nodes)
-            const R rho = R(1) + drho;
-            uk[0] = (jx + R(0.5 * L.gext[0])) / rho;
-            uk[1] = (jy + R(0.5 * L.gext[1])) / rho;
-            uk[2] = (jz + R(0.5 * L.gext[2])) / rho;
             sm.W[lp][lane] = W;
-            sm.rho[lp][lane] = drho;
-            for (int a = 0; a < 3; ++a) {
-                sm.d[lp][lane][a] = dk[a];
-                sm.u[lp][lane][a] = uk[a];
-            }
+            sm.rho[lp][lane] = mom[node];
+            sm.u[lp][lane][0] = mom[st + node];
+            sm.u[lp][lane][1] = mom[2 * st + node];
+            sm.u[lp][lane][2] = mom[3 * st + node];
+            for (int a = 0; a < 3; ++a) sm.d[lp][lane][a] = dk[a];
         }
         // moment matrix A = sum W p p^T, p = (1, x_k - X)
         R a10[10] = {W, W * dk[0], W * dk[1], W * dk[2], W * dk[0] * dk[0], W * dk[0] * dk[1],
@@ -236,6 +277,11 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const S *__restrict__ fin, 
     // ---------------- phase 2: FP64 solves, one lane per point ----------------
     if (warp == 0 && p0 + lane < npts) {
         if (!spd_inverse4(sm.A[lane], sm.Ai[lane])) atomicCAS(err, 0, -1);
+    }
+    if (threadIdx.x == 32 && B.vol_part) {  // fixed-order partial of the enclosed volume
+        double s = 0.0;
+        for (int k = 0; k < kPts; ++k) s += sm.vol[k];
+        B.vol_part[blockIdx.x] = s;
     }
     __syncthreads();
 
@@ -311,57 +357,59 @@ __device__ __forceinline__ void tri_hydro(const BodyView &B, int t, double *F) {
     for (int a = 0; a < 3; ++a) F[a] = (-(pp[0] - pm[0]) * tg[a] + (pp[1 + a] - pm[1 + a])) * A;
 }
 
-// Adds c phi_k F to the force field at the 27 support nodes of marker v and
-// flags the tiles they touch for this step.
+// Lanes 0..26 of a warp add c phi_k F to the force field at the support
+// nodes of marker v; the lanes of the 8 block corners flag their tiles.
 template <typename R>
-__device__ __forceinline__ void spread_marker(const Lattice &L, const BodyView &B, int v, double c,
-                                              const double *Fl, R *__restrict__ force, uint32_t *stamp,
-                                              uint32_t step) {
+__device__ __forceinline__ void spread_warp(const Lattice &L, const BodyView &B, int v, int lane, double c,
+                                            const double *Fl, R *__restrict__ force, uint32_t *stamp,
+                                            uint32_t step) {
+    if (lane >= 27) return;
     const long long st = L.stride;
-    for (int k = 0; k < 27; ++k) {
-        const int node = B.node[27 * v + k];
-        const double w = c * B.phi[27 * v + k];
-        atomicAdd(force + node, R(w * Fl[0]));
-        atomicAdd(force + st + node, R(w * Fl[1]));
-        atomicAdd(force + 2 * st + node, R(w * Fl[2]));
-        if (k == 0 || k == 2 || k == 6 || k == 8 || k == 18 || k == 20 || k == 24 || k == 26) {
-            const int x = node % L.nx, yz = node / L.nx, y = yz % L.ny, z = yz / L.ny;
-            stamp[(x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3))] = step;
-        }
+    const int node = B.node[27 * v + lane];
+    const double w = c * B.phi[27 * v + lane];
+    atomicAdd(force + node, R(w * Fl[0]));
+    atomicAdd(force + st + node, R(w * Fl[1]));
+    atomicAdd(force + 2 * st + node, R(w * Fl[2]));
+    if (lane == 0 || lane == 2 || lane == 6 || lane == 8 || lane == 18 || lane == 20 || lane == 24 || lane == 26) {
+        const int x = node % L.nx, yz = node / L.nx, y = yz % L.ny, z = yz / L.ny;
+        stamp[(x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3))] = step;
     }
 }
 
-// Deterministic block sum of the per-triangle volume terms: V = sum/6.
-__device__ double block_volume(const BodyView &B) {
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int t = threadIdx.x; t < B.nt; t += blockDim.x) s += B.tri_geo[8 * t + 7];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
+// Grows the node box of level n+1 by one marker position.
+__device__ __forceinline__ void box_add(int *box, const double *x) {
+    for (int a = 0; a < 3; ++a) {
+        const int c = (int)floor(x[a]);
+        atomicMin(box + a, c - kBoxLo);
+        atomicMax(box + 3 + a, c + kBoxHi);
     }
-    const double V = red[0] / 6.0;
-    __syncthreads();
-    return V;
 }
 
-// Membrane vertex update, one thread per vertex: spring (Eq. strainFor),
+// Membrane vertex update, one warp per vertex: spring (Eq. strainFor),
 // bending (gradient of k_b[1 - cos(theta - theta0)], reading of Eq. bendFor),
 // volume penalty (restoring reading of Eq. volFor) and element hydrodynamic
-// forces shared 1/3 per vertex (Eq. newtonSoft); Verlet positions
-// (Eqs. verletPos, verletVel); boundary velocity U_b = U + F/m_v dt; the
-// Lagrangian force F_l = U_b - U spread with c_l = A_l (Eq. bodyforce).
+// forces shared 1/3 per vertex (Eq. newtonSoft), with the lanes sharing the
+// incident hinges and triangles; Verlet positions (Eqs. verletPos,
+// verletVel); boundary velocity U_b = U + F/m_v dt; the Lagrangian force
+// F_l = U_b - U spread with c_l = A_l (Eq. bodyforce).
 template <typename R>
 __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
                                                   uint32_t *__restrict__ stamp, uint32_t step) {
-    const double V = block_volume(B);
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double sV;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int i = lane; i < B.nvol_part; i += 32) s += B.vol_part[i];
+        s = warp_sum(s);
+        if (lane == 0) sV = s / 6.0;
+    }
+    __syncthreads();
+    const double V = sV;
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (v >= B.nv) return;
     const double *X = B.X;
     R F[3] = {R(0), R(0), R(0)};
-    for (int q = B.vh_ptr[v]; q < B.vh_ptr[v + 1]; ++q) {
+    for (int q = B.vh_ptr[v] + lane; q < B.vh_ptr[v + 1]; q += 32) {
         const int code = B.vh_list[q];
         const int h = code >> 2, role = code & 3;
         const int4 H = B.hinge[h];
@@ -397,7 +445,7 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         const R h1 = l1 / le, h2 = l2 / le;
         const R tc = (ac[0] * e[0] + ac[1] * e[1] + ac[2] * e[2]) / le2;
         const R td = (ad[0] * e[0] + ad[1] * e[1] + ad[2] * e[2]) / le2;
-        R c1, c2;  // gradient = c1 n1/h1 + c2 n2/h2
+        R c1, c2;  // dtheta/dx = c1 n1/h1 + c2 n2/h2
         if (role == 0) {
             c1 = R(1) - tc;
             c2 = R(1) - td;
@@ -416,7 +464,7 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
     // element terms: volume penalty and hydrodynamic force, 1/3 per vertex
     const R cv = R(B.kv * (1.0 - V / B.V0));
     double Al = 0.0;
-    for (int q = B.vt_ptr[v]; q < B.vt_ptr[v + 1]; ++q) {
+    for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32) {
         const int t = B.vt_list[q] / 3;
         const double *tg = B.tri_geo + 8 * t;
         Al += tg[3] / 3.0;
@@ -424,21 +472,29 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         tri_hydro(B, t, Fh);
         for (int a = 0; a < 3; ++a) F[a] += cv * R(tg[a]) * R(tg[3]) / R(3) + R(Fh[a] / 3.0);
     }
+    for (int a = 0; a < 3; ++a) F[a] = warp_sum(F[a]);
+    Al = warp_sum(Al);
     // Newton (Eq. newtonSoft) and Verlet (Eqs. verletPos, verletVel), dt = 1
-    double acc[3], U[3], Ub[3], Fl[3];
+    double Fl[3];
     for (int a = 0; a < 3; ++a) {
-        acc[a] = (double)F[a] / B.mv;
-        U[a] = B.U[3 * v + a];
-        const double x = X[3 * v + a], xp = B.Xprev[3 * v + a];
-        const double xt = x + U[a] + 0.5 * acc[a];
-        const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
-        B.Xnew[3 * v + a] = x + ubdf + 0.5 * acc[a];
-        Ub[a] = U[a] + acc[a];
-        Fl[a] = Ub[a] - U[a];
-        B.Ub[3 * v + a] = Ub[a];
-        B.Fl[3 * v + a] = Fl[a];
+        const double acc = (double)F[a] / B.mv;
+        const double U = B.U[3 * v + a];
+        const double Ub = U + acc;
+        Fl[a] = Ub - U;
+        if (lane == 0) {
+            const double x = X[3 * v + a], xp = B.Xprev[3 * v + a];
+            const double xt = x + U + 0.5 * acc;
+            const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
+            B.Xnew[3 * v + a] = x + ubdf + 0.5 * acc;
+            B.Ub[3 * v + a] = Ub;
+            B.Fl[3 * v + a] = Fl[a];
+        }
     }
-    spread_marker<R>(L, B, v, Al, Fl, force, stamp, step);
+    if (lane == 0) {
+        double xn[3] = {B.Xnew[3 * v], B.Xnew[3 * v + 1], B.Xnew[3 * v + 2]};
+        box_add(B.bbox_next, xn);
+    }
+    spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
 }
 
 // Rigid body, one block: total force and moment of the element stresses,
@@ -549,60 +605,76 @@ __global__ void __launch_bounds__(256) k_rigid_update(BodyView B) {
     }
 }
 
-// Rigid markers, one thread each: boundary velocity u + w x (X - x_c) of
+// Rigid markers, one warp each: boundary velocity u + w x (X - x_c) of
 // level n, IB force and spreading, then the markers of level n+1.
 template <typename R>
 __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
                                                        uint32_t *__restrict__ stamp, uint32_t step) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (v >= B.nv) return;
     const double *S = B.rstate;
     const double *un = S + RigidState::U, *wn = S + RigidState::W, *xo = S + RigidState::XC_OLD;
     const double *xc = S + RigidState::XC, *Rn = S + RigidState::ROT;
+    double Al = 0.0;
+    for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32) Al += B.tri_geo[8 * (B.vt_list[q] / 3) + 3] / 3.0;
+    Al = warp_sum(Al);
     const double r[3] = {B.X[3 * v] - xo[0], B.X[3 * v + 1] - xo[1], B.X[3 * v + 2] - xo[2]};
     const double wxr[3] = {wn[1] * r[2] - wn[2] * r[1], wn[2] * r[0] - wn[0] * r[2], wn[0] * r[1] - wn[1] * r[0]};
     double Fl[3];
-    double Al = 0.0;
-    for (int q = B.vt_ptr[v]; q < B.vt_ptr[v + 1]; ++q) Al += B.tri_geo[8 * (B.vt_list[q] / 3) + 3] / 3.0;
     for (int a = 0; a < 3; ++a) {
         const double ub = un[a] + wxr[a];
         Fl[a] = ub - B.U[3 * v + a];
-        B.Ub[3 * v + a] = ub;
-        B.Fl[3 * v + a] = Fl[a];
+        if (lane == 0) {
+            B.Ub[3 * v + a] = ub;
+            B.Fl[3 * v + a] = Fl[a];
+        }
     }
-    const double *xb = B.Xbody + 3 * v;
-    for (int a = 0; a < 3; ++a)
-        B.Xnew[3 * v + a] = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
-    spread_marker<R>(L, B, v, Al, Fl, force, stamp, step);
+    if (lane == 0) {
+        const double *xb = B.Xbody + 3 * v;
+        double xn[3];
+        for (int a = 0; a < 3; ++a) {
+            xn[a] = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
+            B.Xnew[3 * v + a] = xn[a];
+        }
+        box_add(B.bbox_next, xn);
+    }
+    spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
 }
 
 // ---- launchers ----
+int mls_blocks(const BodyView &B) { return (B.nv + 2 * B.nt + kPts - 1) / kPts; }
+
 template <typename S, typename R>
-static cudaError_t mls_t(const void *fin, const Lattice &L, const BodyView &B, int *err, cudaStream_t s) {
-    const int npts = B.nv + 2 * B.nt;
+static cudaError_t ib_front_t(const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm, int *err,
+                              cudaStream_t s) {
+    k_moments<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, L, B.bbox, B.bbox_next, (R *)mom);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const size_t smem = sizeof(MlsSmem<R>);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_mls<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_mls<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_mls<S, R><<<(npts + kPts - 1) / kPts, kMlsThreads, smem, s>>>((const S *)fin, L, B, err);
+    k_mls<R><<<mls_blocks(B), kMlsThreads, smem, s>>>((const R *)mom, L, B, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mls(int prec, const void *fin, const Lattice &L, const BodyView &B, int *err, cudaStream_t s) {
+cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm,
+                            int *err, cudaStream_t s) {
     switch (prec) {
-        case 0: return mls_t<double, double>(fin, L, B, err, s);
-        case 1: return mls_t<float, float>(fin, L, B, err, s);
-        case 2: return mls_t<__half, float>(fin, L, B, err, s);
-        default: return mls_t<__nv_bfloat16, float>(fin, L, B, err, s);
+        case 0: return ib_front_t<double, double>(fin, L, B, mom, nsm, err, s);
+        case 1: return ib_front_t<float, float>(fin, L, B, mom, nsm, err, s);
+        case 2: return ib_front_t<__half, float>(fin, L, B, mom, nsm, err, s);
+        default: return ib_front_t<__nv_bfloat16, float>(fin, L, B, mom, nsm, err, s);
     }
 }
 
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
                             uint32_t step, cudaStream_t s) {
-    const unsigned g = (unsigned)((B.nv + 255) / 256);
+    const unsigned g = (unsigned)((B.nv + 7) / 8);  // 8 warps (vertices) per block
     if (prec == 0)
         k_membrane<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
     else
@@ -615,7 +687,7 @@ cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *fo
     k_rigid_update<<<1, 256, 0, s>>>(B);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const unsigned g = (unsigned)((B.nv + 255) / 256);
+    const unsigned g = (unsigned)((B.nv + 7) / 8);
     if (prec == 0)
         k_rigid_markers<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
     else

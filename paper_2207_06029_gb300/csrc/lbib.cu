@@ -32,6 +32,10 @@ struct DevBody {
         *vt_list = nullptr;
     int4 *hinge = nullptr;
     double *ks = nullptr, *l0 = nullptr, *kb = nullptr, *theta0 = nullptr, *Xbody = nullptr, *rstate = nullptr;
+    int *bbox[2] = {nullptr, nullptr};  // support-region node boxes, current and next
+    int bcur = 0;
+    double *vol_part = nullptr;
+    int nvol_part = 0;
     double V0 = 0, A0 = 0, mv = 0, origin[3] = {0, 0, 0};
 };
 
@@ -40,7 +44,9 @@ struct Ctx {
     Lattice L{};
     int prec = 1;
     size_t elem = 4, relem = 4;
-    void *fA = nullptr, *fB = nullptr, *force = nullptr, *fields = nullptr;
+    void *fA = nullptr, *fB = nullptr, *force = nullptr, *fields = nullptr, *mom = nullptr;
+    int nsm = 1;
+    int fields_every = 0;  // <0 never, 0 last step of each lbib_step call, k>0 every k-th step
     uint32_t *stamp = nullptr;
     int ntiles = 0;
     int *d_err = nullptr;
@@ -57,7 +63,7 @@ struct Ctx {
     size_t bytes = 0;
     std::vector<std::pair<void *, size_t>> allocs;
     bool profile = false;
-    std::vector<cudaEvent_t> events;  // triples: begin, after IB, after sweep
+    std::vector<cudaEvent_t> events;  // per step: begin, after MLS, after structure, after sweep
     size_t nev = 0;
 };
 
@@ -245,6 +251,10 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.bend_variant = b.p.bend_variant;
     v.Xbody = b.Xbody;
     v.rstate = b.rstate;
+    v.bbox = b.bbox[b.bcur];
+    v.bbox_next = b.bbox[1 - b.bcur];
+    v.vol_part = b.vol_part;
+    v.nvol_part = b.nvol_part;
     (void)c;
     return v;
 }
@@ -298,6 +308,10 @@ int lbib_create(const lbib_params *p, void **out) {
             g_create_error = "a walled axis needs at least 3 nodes";
             return LBIB_EINVAL;
         }
+    }
+    if (n[1] > 65535 || n[2] > 65535) {
+        g_create_error = "ny and nz must be at most 65535";
+        return LBIB_EINVAL;
     }
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) {
         g_create_error = "tau must be > 0.5";
@@ -357,9 +371,18 @@ int lbib_create(const lbib_params *p, void **out) {
     c->fB = dev_alloc(c, pop_bytes);
     c->force = dev_alloc(c, 3 * (size_t)L.stride * c->relem);
     c->fields = dev_alloc(c, 4 * (size_t)L.stride * c->relem);
+    c->mom = dev_alloc(c, 4 * (size_t)L.stride * c->relem);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c->nsm < 1) {
+            cudaGetLastError();
+            c->nsm = 1;
+        }
+    }
     c->stamp = (uint32_t *)dev_alloc(c, sizeof(uint32_t) * (size_t)c->ntiles);
     c->d_err = (int *)dev_alloc(c, sizeof(int));
-    if (!c->fA || !c->fB || !c->force || !c->fields || !c->stamp || !c->d_err) {
+    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err) {
         g_create_error = "device allocation failed";
         lbib_destroy(c);
         return LBIB_ENOMEM;
@@ -589,6 +612,25 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         b.Xbody = upload(c, Xb, &rc);
         b.rstate = upload(c, st, &rc);
     }
+    {
+        // node box of the supports of the initial markers (kept current by the
+        // update kernels from then on)
+        std::vector<int> box = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000,
+                                (int)0x80000000};
+        for (int v = 0; v < nv; ++v)
+            for (int a = 0; a < 3; ++a) {
+                const int cc = (int)std::floor(verts[3 * v + a]);
+                box[a] = std::min(box[a], cc - 3);
+                box[3 + a] = std::max(box[3 + a], cc + 4);
+            }
+        b.bbox[0] = upload(c, box, &rc);
+        b.bbox[1] = upload(c, box, &rc);
+        BodyView tmp{};
+        tmp.nv = nv;
+        tmp.nt = nt;
+        b.nvol_part = mls_blocks(tmp);
+        b.vol_part = upload(c, std::vector<double>((size_t)b.nvol_part, 0.0), &rc);
+    }
     if (rc || !b.phi || !b.node || !b.tri_geo || !b.probe) {
         c->err = rc ? rc : LBIB_ENOMEM;
         return fail(c, c->err, "body allocation or upload failed");
@@ -612,37 +654,50 @@ int lbib_step(void *h, int nsteps) {
         }
         cudaEvent_t *ev = nullptr;
         if (c->profile) {
-            if (c->nev + 3 > c->events.size())
-                for (int k = 0; k < 3; ++k) {
+            if (c->nev + 4 > c->events.size())
+                for (int k = 0; k < 4; ++k) {
                     cudaEvent_t x;
                     if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
                     c->events.push_back(x);
                 }
             ev = &c->events[c->nev];
-            c->nev += 3;
+            c->nev += 4;
             cudaEventRecord(ev[0], c->stream);
         }
+        // IB front: support-region moments + MLS at markers and probes
         for (auto &b : c->bodies) {
             const BodyView v = make_view(c, b);
-            cudaError_t e = launch_mls(c->prec, c->fA, c->L, v, c->d_err, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernel");
+            cudaError_t e = launch_ib_front(c->prec, c->fA, c->L, v, c->mom, c->nsm, c->d_err, c->stream);
+            c->launches += 2;
+            if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernels");
+        }
+        if (ev) cudaEventRecord(ev[1], c->stream);
+        // structure update and spreading
+        for (auto &b : c->bodies) {
+            const BodyView v = make_view(c, b);
+            cudaError_t e;
             if (b.rigid) {
                 e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, c->stream);
-                c->launches += 3;
+                c->launches += 2;
             } else {
                 e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, c->stream);
-                c->launches += 2;
+                c->launches += 1;
             }
             if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
         }
-        if (ev) cudaEventRecord(ev[1], c->stream);
+        if (ev) cudaEventRecord(ev[2], c->stream);
+        const bool store = c->fields_every == 0 ? (it == nsteps - 1)
+                                                : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
         cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L,
-                                     it == nsteps - 1 ? c->fields : nullptr, c->stream);
+                                     store ? c->fields : nullptr, c->stream);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
-        if (ev) cudaEventRecord(ev[2], c->stream);
+        if (ev) cudaEventRecord(ev[3], c->stream);
         std::swap(c->fA, c->fB);
-        for (auto &b : c->bodies) b.cur = (b.cur + 1) % 3;
+        for (auto &b : c->bodies) {
+            b.cur = (b.cur + 1) % 3;
+            b.bcur ^= 1;
+        }
         c->steps++;
     }
     cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -778,23 +833,28 @@ int lbib_profile(void *h, int enable) {
     return LBIB_OK;
 }
 
-int lbib_get_profile(void *h, double *sweep_ms, double *ib_ms, long long *nsteps) {
+int lbib_get_profile(void *h, double *ms, long long *nsteps) {
     Ctx *c = as_ctx(h);
-    if (!c) return LBIB_EINVAL;
+    if (!c || !ms) return LBIB_EINVAL;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
-    double sw = 0.0, ib = 0.0;
-    for (size_t k = 0; k + 2 < c->nev + 1 && k < c->nev; k += 3) {
-        float a = 0.f, b2 = 0.f;
-        cudaEventElapsedTime(&a, c->events[k], c->events[k + 1]);
-        cudaEventElapsedTime(&b2, c->events[k + 1], c->events[k + 2]);
-        ib += a;
-        sw += b2;
-    }
-    if (sweep_ms) *sweep_ms = sw;
-    if (ib_ms) *ib_ms = ib;
-    if (nsteps) *nsteps = (long long)(c->nev / 3);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (size_t k = 0; k + 4 <= c->nev; k += 4)
+        for (int j = 0; j < 3; ++j) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, c->events[k + j], c->events[k + j + 1]);
+            acc[j] += t;
+        }
+    for (int j = 0; j < 3; ++j) ms[j] = acc[j];
+    if (nsteps) *nsteps = (long long)(c->nev / 4);
     c->nev = 0;
+    return LBIB_OK;
+}
+
+int lbib_set_output(void *h, int fields_every) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    c->fields_every = fields_every;
     return LBIB_OK;
 }
 

@@ -124,6 +124,11 @@ struct BodyView {
     // rigid body
     const double *Xbody;    // [3nv] rest coordinates about the centre
     double *rstate;         // rigid state block, see RigidState
+    // support region: node box of level n (read) and of level n+1 (built)
+    const int *bbox;        // [6]: lo xyz, hi xyz (inclusive node coordinates)
+    int *bbox_next;         // [6], reset by the moments kernel, filled by the update kernel
+    double *vol_part;       // [one per MLS block] partial sums of the volume terms
+    int nvol_part;
 };
 
 // Layout of the rigid-body state block (doubles).

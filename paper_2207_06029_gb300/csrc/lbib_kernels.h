@@ -19,7 +19,9 @@ cudaError_t launch_fields_out(int prec, const void *fields, const Lattice &L, do
                               cudaStream_t s);
 
 // ib.cu
-cudaError_t launch_mls(int prec, const void *fin, const Lattice &L, const BodyView &B, int *err, cudaStream_t s);
+int mls_blocks(const BodyView &B);
+cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm,
+                            int *err, cudaStream_t s);
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
                             uint32_t step, cudaStream_t s);
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,

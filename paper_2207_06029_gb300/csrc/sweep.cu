@@ -84,13 +84,12 @@ template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
                                                R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                                uint32_t step, Lattice L, R *__restrict__ fields) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= L.ncell) return;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int x = idx % nx;
-    const int yz = idx / nx;
-    const int y = yz % ny;
-    const int z = yz / ny;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const int idx = x + nx * (y + ny * z);
     const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
     // neighbour coordinates; on walled axes an outside source is clamped to
     // the node itself (its value is unused: the wall rule overwrites it)
@@ -270,11 +269,24 @@ __global__ void k_fields_out(const R *__restrict__ fields, Lattice L, double *__
 // ---- host-side launchers (one per storage precision) ----
 static inline unsigned grid_for(int n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Block of whole x-rows: bx = nx rounded up to a warp (at most 256), by rows
+// so that a block holds about 256 threads; one z-plane per grid layer.
+static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
+    int bx = (L.nx + 31) / 32 * 32;
+    if (bx > 256) bx = 256;
+    int by = 256 / bx;
+    if (by < 1) by = 1;
+    if (by > L.ny) by = L.ny;
+    block = dim3(bx, by, 1);
+    grid = dim3((L.nx + bx - 1) / bx, (L.ny + by - 1) / by, L.nz);
+}
+
 template <typename S, typename R>
 static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, uint32_t step,
                            const Lattice &L, void *fields, cudaStream_t s) {
-    k_sweep<S, R><<<grid_for(L.ncell, 256), 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
-                                                         (R *)fields);
+    dim3 grid, block;
+    sweep_shape(L, grid, block);
+    k_sweep<S, R><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L, (R *)fields);
     return cudaGetLastError();
 }
 

@@ -127,7 +127,9 @@ def test_fp64_couette_rigid_sphere_full(lbib):
 def test_fp64_capsule_in_shear(lbib, bend_variant):
     """Deformable capsule (springs, bending, volume, probes, Verlet) in a 24^3
     Couette cell, 40 steps, FP64."""
-    case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.05,
+    # Eb = 0.01 keeps the explicit update stable at this resolution (0.05
+    # diverges in the oracle as well)
+    case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01,
                                 kv=1.0, precision=W.PREC_FP64)
     case.bodies[0].bend_variant = bend_variant
     case.bodies[0].verts = W.perturb(case.bodies[0].verts, 0.02, seed=11)
