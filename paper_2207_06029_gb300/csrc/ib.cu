@@ -84,22 +84,28 @@ __global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Latt
         const int node = c[0] + L.nx * c[1] + nxy * c[2];
         const R rho = R(1) + drho;
         mom[node] = drho;
-        mom[st + node] = (jx + R(0.5 * L.gext[0])) / rho;
-        mom[2 * st + node] = (jy + R(0.5 * L.gext[1])) / rho;
-        mom[3 * st + node] = (jz + R(0.5 * L.gext[2])) / rho;
+        mom[st + node] = (jx + R(0.5) * pick<R>(L.gext_d[0], L.gext_f[0])) / rho;
+        mom[2 * st + node] = (jy + R(0.5) * pick<R>(L.gext_d[1], L.gext_f[1])) / rho;
+        mom[3 * st + node] = (jz + R(0.5) * pick<R>(L.gext_d[2], L.gext_f[2])) / rho;
     }
 }
 
 template <typename R>
 struct MlsSmem {
+    // per point, filled in phase 0 (one lane per point)
+    double P[kPts][3];
+    double frac[kPts][3];  // P - base, exact
+    int base[kPts][3];
+    R fracR[kPts][3];
+    R nrm[kPts][3];
+    double vol[kPts];
+    // per point and support node
     R W[kPts][27];
     R d[kPts][27][3];
     R rho[kPts][27];
     R u[kPts][27][3];
-    R nrm[kPts][3];
-    double vol[kPts];
-    double A[kPts][10];
-    double Ai[kPts][16];
+    R A[kPts][10];
+    R Ai[kPts][16];
 };
 
 // Inverse of a symmetric positive definite 4x4 matrix given by its upper
@@ -148,31 +154,21 @@ __device__ bool spd_inverse4(const double *a, double *inv) {
     return true;
 }
 
-// Triangle geometry in arithmetic R from double positions: unit normal,
-// area, centroid (double) and the volume term (x_0 - o) . (e1 x e2).
-template <typename R>
-__device__ __forceinline__ void tri_geometry(const double *X, const int *t, const double *o, R *n, R &area,
-                                             double *cen, double &vol6) {
-    const int i0 = t[0], i1 = t[1], i2 = t[2];
-    const double x0[3] = {X[3 * i0], X[3 * i0 + 1], X[3 * i0 + 2]};
-    const R e1[3] = {R(X[3 * i1] - x0[0]), R(X[3 * i1 + 1] - x0[1]), R(X[3 * i1 + 2] - x0[2])};
-    const R e2[3] = {R(X[3 * i2] - x0[0]), R(X[3 * i2 + 1] - x0[1]), R(X[3 * i2 + 2] - x0[2])};
-    const R N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const R nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-    area = R(0.5) * nn;
-    for (int a = 0; a < 3; ++a) {
-        n[a] = N[a] / nn;
-        cen[a] = x0[a] + (double)((e1[a] + e2[a]) / R(3));
-    }
-    vol6 = (x0[0] - o[0]) * (double)N[0] + (x0[1] - o[1]) * (double)N[1] + (x0[2] - o[2]) * (double)N[2];
+// Squared distance with the products and sums rounded one by one in the
+// order (x^2 + y^2) + z^2, as a plain sum of squares is.
+__device__ __forceinline__ double dist2_exact(double a, double b, double c) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
 }
 
-// One warp per point, 32 points per block.  Points 0..nv-1 are the markers;
-// point nv + 2t + side is the probe of triangle t on the outer (side 0) or
-// inner (side 1) face.
-//  phase 1: support block, weights (the r_k <= 1 decision bit-exact in
-//           FP64), node moments, moment matrix A (warp reduction);
-//  phase 2: warp 0 inverts the 32 matrices in FP64, one lane each;
+// MLS at markers and probes, one warp per point, 32 points per block.
+// Points 0..nv-1 are the markers; point nv + 2t + side is the probe of
+// triangle t on the outer (side 0) or inner (side 1) face.
+//  phase 0: one lane per point: position (probes: triangle geometry), the
+//           nearest node base = floor(X + 1/2) and the exact offset X - base;
+//  phase 1: one warp per point, one lane per support node: weight
+//           W = exp(-(r/alpha)^2) for r <= 1 (the cut-off decided exactly as
+//           in FP64), node moments, moment matrix A (warp reduction);
+//  phase 2: one lane per point: FP64 Cholesky inverse of A;
 //  phase 3: shape functions psi_k = W_k A^-1 p_k; markers interpolate U and
 //           keep phi = psi[0] for spreading; probes fit rho and u and store
 //           pressure and traction.
@@ -187,72 +183,101 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     const long long st = L.stride;
     const int nxy = L.nx * L.ny;
     const int n[3] = {L.nx, L.ny, L.nz};
-    if (threadIdx.x < kPts) sm.vol[threadIdx.x] = 0.0;
+
+    // ---------------- phase 0: one lane per point ----------------
+    if (warp == 0) {
+        const int p = p0 + lane;
+        sm.vol[lane] = 0.0;
+        if (p < npts) {
+            double P[3];
+            if (p < B.nv) {
+                P[0] = B.X[3 * p];
+                P[1] = B.X[3 * p + 1];
+                P[2] = B.X[3 * p + 2];
+            } else {
+                const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
+                const int *tv = B.tri + 3 * t;
+                const double *X = B.X;
+                const double x0[3] = {X[3 * tv[0]], X[3 * tv[0] + 1], X[3 * tv[0] + 2]};
+                const R e1[3] = {R(X[3 * tv[1]] - x0[0]), R(X[3 * tv[1] + 1] - x0[1]), R(X[3 * tv[1] + 2] - x0[2])};
+                const R e2[3] = {R(X[3 * tv[2]] - x0[0]), R(X[3 * tv[2] + 1] - x0[1]), R(X[3 * tv[2] + 2] - x0[2])};
+                const R N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                e1[0] * e2[1] - e1[1] * e2[0]};
+                const R nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+                R nr[3];
+                double cen[3];
+                for (int a = 0; a < 3; ++a) {
+                    nr[a] = N[a] / nn;
+                    cen[a] = x0[a] + (double)((e1[a] + e2[a]) / R(3));
+                    sm.nrm[lane][a] = nr[a];
+                }
+                const double sg = side ? -kProbe : kProbe;
+                for (int a = 0; a < 3; ++a) P[a] = cen[a] + sg * (double)nr[a];
+                if (side == 0) {
+                    R *tg = (R *)B.tri_geo + 8 * t;
+                    for (int a = 0; a < 3; ++a) {
+                        tg[a] = nr[a];
+                        tg[4 + a] = R(cen[a] - B.origin[a]);
+                    }
+                    tg[3] = R(0.5) * nn;
+                    const double v6 = (x0[0] - B.origin[0]) * (double)N[0] + (x0[1] - B.origin[1]) * (double)N[1] +
+                                      (x0[2] - B.origin[2]) * (double)N[2];
+                    B.tri_vol[t] = v6;
+                    sm.vol[lane] = v6;
+                }
+            }
+            bool bad = false;
+            for (int a = 0; a < 3; ++a) {
+                int b = (int)floor(P[a] + 0.5);
+                if (L.bc[a] == kWall && (b - 1 < 1 || b + 1 > n[a] - 2)) {
+                    bad = true;
+                    b = b < 2 ? 2 : (b > n[a] - 3 ? n[a] - 3 : b);
+                }
+                sm.base[lane][a] = b;
+                sm.P[lane][a] = P[a];
+                sm.frac[lane][a] = P[a] - (double)b;
+                sm.fracR[lane][a] = R(sm.frac[lane][a]);
+            }
+            if (bad) atomicCAS(err, 0, -5);
+        }
+    }
     __syncthreads();
 
-    // ---------------- phase 1 ----------------
+    // ---------------- phase 1: one warp per point, one lane per node ----------------
     for (int j = 0; j < kPts / 4; ++j) {
         const int lp = warp * (kPts / 4) + j;
         const int p = p0 + lp;
         if (p >= npts) break;
-        double P[3];
-        if (p < B.nv) {
-            P[0] = B.X[3 * p];
-            P[1] = B.X[3 * p + 1];
-            P[2] = B.X[3 * p + 2];
-        } else {
-            const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
-            R nr[3], area;
-            double cen[3], vol6;
-            tri_geometry<R>(B.X, B.tri + 3 * t, B.origin, nr, area, cen, vol6);
-            const double sg = side ? -kProbe : kProbe;
-            for (int a = 0; a < 3; ++a) P[a] = cen[a] + sg * (double)nr[a];
-            if (lane == 0) {
-                sm.nrm[lp][0] = nr[0];
-                sm.nrm[lp][1] = nr[1];
-                sm.nrm[lp][2] = nr[2];
-                if (side == 0) {
-                    double *tg = B.tri_geo + 8 * t;
-                    tg[0] = nr[0];
-                    tg[1] = nr[1];
-                    tg[2] = nr[2];
-                    tg[3] = area;
-                    tg[4] = cen[0];
-                    tg[5] = cen[1];
-                    tg[6] = cen[2];
-                    tg[7] = vol6;
-                    sm.vol[lp] = vol6;
-                }
-            }
-        }
-        // nearest node and wall check (supports stay off wall nodes)
-        int base[3];
-        bool bad = false;
-        for (int a = 0; a < 3; ++a) {
-            base[a] = (int)floor(P[a] + 0.5);
-            if (L.bc[a] == kWall && (base[a] - 1 < 1 || base[a] + 1 > n[a] - 2)) {
-                bad = true;
-                base[a] = base[a] < 2 ? 2 : (base[a] > n[a] - 3 ? n[a] - 3 : base[a]);
-            }
-        }
-        if (bad && lane == 0) atomicCAS(err, 0, -5);
         R W = R(0), dk[3] = {R(0), R(0), R(0)};
         if (lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
             int cw[3];
-            double dx[3];
             for (int a = 0; a < 3; ++a) {
-                const int c = base[a] + dd[a];
-                dx[a] = (double)c - P[a];
-                dk[a] = R(dx[a]);
-                cw[a] = L.bc[a] == kPeriodic ? ((c % n[a]) + n[a]) % n[a] : c;
+                // x_k - X = dd - (X - base), one rounding like (base + dd) - X
+                dk[a] = R(dd[a]) - sm.fracR[lp][a];
+                const int cc = sm.base[lp][a] + dd[a];
+                cw[a] = L.bc[a] == kPeriodic ? ((cc % n[a]) + n[a]) % n[a] : cc;
             }
-            // |x_k - X|^2 rounded exactly as the plain sum of squares, so the
-            // cut-off r_k <= 1 of Eq. (intKernel) is decided bit for bit
-            const double dist2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])),
-                                           __dmul_rn(dx[2], dx[2]));
-            if (dist2 <= L.dist2_cut) {
-                const R r = sqrt(R(dist2)) / R(kRw);
+            // support cut-off r_k <= 1 of Eq. (intKernel), decided on the FP64
+            // squared distance; the FP32 path computes it in FP64 only near
+            // the cut-off, where its own rounding could flip the decision
+            bool inside;
+            R dist2;
+            if (sizeof(R) == 8) {
+                dist2 = R(dist2_exact(double(dk[0]), double(dk[1]), double(dk[2])));
+                inside = double(dist2) <= L.dist2_cut;
+            } else {
+                dist2 = dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2];
+                if (fabsf(float(dist2) - L.dist2_cut_f) > 1e-4f) {
+                    inside = float(dist2) < L.dist2_cut_f;
+                } else {
+                    const double e0 = (double)dd[0] - sm.frac[lp][0], e1 = (double)dd[1] - sm.frac[lp][1],
+                                 e2 = (double)dd[2] - sm.frac[lp][2];
+                    inside = dist2_exact(e0, e1, e2) <= L.dist2_cut;
+                }
+            }
+            if (inside) {
+                const R r = sqrt(dist2) / R(kRw);
                 W = exp(-(r / R(kAlpha)) * (r / R(kAlpha)));
             }
             const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
@@ -269,14 +294,16 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                      W * dk[0] * dk[2], W * dk[1] * dk[1], W * dk[1] * dk[2], W * dk[2] * dk[2]};
 #pragma unroll
         for (int q = 0; q < 10; ++q) a10[q] = warp_sum(a10[q]);
-        if (lane == 0)
-            for (int q = 0; q < 10; ++q) sm.A[lp][q] = (double)a10[q];
+        if (lane < 10) sm.A[lp][lane] = a10[lane];
     }
     __syncthreads();
 
     // ---------------- phase 2: FP64 solves, one lane per point ----------------
     if (warp == 0 && p0 + lane < npts) {
-        if (!spd_inverse4(sm.A[lane], sm.Ai[lane])) atomicCAS(err, 0, -1);
+        double a[10], inv[16];
+        for (int q = 0; q < 10; ++q) a[q] = (double)sm.A[lane][q];
+        if (!spd_inverse4(a, inv)) atomicCAS(err, 0, -1);
+        for (int q = 0; q < 16; ++q) sm.Ai[lane][q] = R(inv[q]);
     }
     if (threadIdx.x == 32 && B.vol_part) {  // fixed-order partial of the enclosed volume
         double s = 0.0;
@@ -286,7 +313,7 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     __syncthreads();
 
     // ---------------- phase 3 ----------------
-    const R nu = R((L.tau - 0.5) / 3.0);
+    const R nu = pick<R>(L.nu_d, L.nu_f);
     for (int j = 0; j < kPts / 4; ++j) {
         const int lp = warp * (kPts / 4) + j;
         const int p = p0 + lp;
@@ -302,21 +329,17 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
             u1 = sm.u[lp][lane][1];
             u2 = sm.u[lp][lane][2];
         }
-        const double *Ai = sm.Ai[lp];
+        const R *Ai = sm.Ai[lp];
         if (p < B.nv) {
-            const R phi = W * (R(Ai[0]) + R(Ai[1]) * d0 + R(Ai[2]) * d1 + R(Ai[3]) * d2);
-            if (lane < 27) B.phi[27 * p + lane] = (double)phi;
+            const R phi = W * (Ai[0] + Ai[1] * d0 + Ai[2] * d1 + Ai[3] * d2);
+            if (lane < 27) ((R *)B.phi)[27 * p + lane] = phi;
             const R U0 = warp_sum(phi * u0), U1 = warp_sum(phi * u1), U2 = warp_sum(phi * u2);
-            if (lane == 0) {
-                B.U[3 * p] = U0;
-                B.U[3 * p + 1] = U1;
-                B.U[3 * p + 2] = U2;
-            }
+            if (lane < 3) B.U[3 * p + lane] = (double)(lane == 0 ? U0 : lane == 1 ? U1 : U2);
         } else {
             R psi[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                psi[i] = W * (R(Ai[4 * i]) + R(Ai[4 * i + 1]) * d0 + R(Ai[4 * i + 2]) * d1 + R(Ai[4 * i + 3]) * d2);
+                psi[i] = W * (Ai[4 * i] + Ai[4 * i + 1] * d0 + Ai[4 * i + 2] * d1 + Ai[4 * i + 3] * d2);
             R fit[16];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -329,20 +352,16 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                 const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
                 const R rho = R(1) + fit[0];
                 // grad u: du_j/dx_m = fit[4 + 4j + 1 + m]
-                R tn[3];
+                R *pr = (R *)B.probe + 8 * t + 4 * side;
+                pr[0] = fit[0] / R(3);  // p - c_s^2 rho0
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
                     R acc = R(0);
 #pragma unroll
                     for (int m = 0; m < 3; ++m)
                         acc += rho * nu * (fit[4 + 4 * jj + 1 + m] + fit[4 + 4 * m + 1 + jj]) * sm.nrm[lp][m];
-                    tn[jj] = acc;
+                    pr[1 + jj] = acc;
                 }
-                double *pr = B.probe + 8 * t + 4 * side;
-                pr[0] = (1.0 + (double)fit[0]) / 3.0;
-                pr[1] = tn[0];
-                pr[2] = tn[1];
-                pr[3] = tn[2];
             }
         }
     }
@@ -350,39 +369,37 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
 
 // Hydrodynamic force on triangle t from its two probes (Eqs. hydroForP,
 // hydroForNu): F = [-(p+ - p-) n + (tau+ - tau-) . n] A.
-__device__ __forceinline__ void tri_hydro(const BodyView &B, int t, double *F) {
-    const double *tg = B.tri_geo + 8 * t;
-    const double *pp = B.probe + 8 * t, *pm = pp + 4;
-    const double A = tg[3];
+template <typename R>
+__device__ __forceinline__ void tri_hydro(const BodyView &B, int t, R *F) {
+    const R *tg = (const R *)B.tri_geo + 8 * t;
+    const R *pp = (const R *)B.probe + 8 * t, *pm = pp + 4;
+    const R A = tg[3];
     for (int a = 0; a < 3; ++a) F[a] = (-(pp[0] - pm[0]) * tg[a] + (pp[1 + a] - pm[1 + a])) * A;
 }
 
 // Lanes 0..26 of a warp add c phi_k F to the force field at the support
 // nodes of marker v; the lanes of the 8 block corners flag their tiles.
 template <typename R>
-__device__ __forceinline__ void spread_warp(const Lattice &L, const BodyView &B, int v, int lane, double c,
-                                            const double *Fl, R *__restrict__ force, uint32_t *stamp,
-                                            uint32_t step) {
+__device__ __forceinline__ void spread_warp(const Lattice &L, const BodyView &B, int v, int lane, R c, const R *Fl,
+                                            R *__restrict__ force, uint32_t *stamp, uint32_t step) {
     if (lane >= 27) return;
     const long long st = L.stride;
     const int node = B.node[27 * v + lane];
-    const double w = c * B.phi[27 * v + lane];
-    atomicAdd(force + node, R(w * Fl[0]));
-    atomicAdd(force + st + node, R(w * Fl[1]));
-    atomicAdd(force + 2 * st + node, R(w * Fl[2]));
+    const R w = c * ((const R *)B.phi)[27 * v + lane];
+    atomicAdd(force + node, w * Fl[0]);
+    atomicAdd(force + st + node, w * Fl[1]);
+    atomicAdd(force + 2 * st + node, w * Fl[2]);
     if (lane == 0 || lane == 2 || lane == 6 || lane == 8 || lane == 18 || lane == 20 || lane == 24 || lane == 26) {
         const int x = node % L.nx, yz = node / L.nx, y = yz % L.ny, z = yz / L.ny;
         stamp[(x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3))] = step;
     }
 }
 
-// Grows the node box of level n+1 by one marker position.
-__device__ __forceinline__ void box_add(int *box, const double *x) {
-    for (int a = 0; a < 3; ++a) {
-        const int c = (int)floor(x[a]);
-        atomicMin(box + a, c - kBoxLo);
-        atomicMax(box + 3 + a, c + kBoxHi);
-    }
+// Grows component a of the node box of level n+1 by one marker position.
+__device__ __forceinline__ void box_add(int *box, int a, double x) {
+    const int c = (int)floor(x);
+    atomicMin(box + a, c - kBoxLo);
+    atomicMax(box + 3 + a, c + kBoxHi);
 }
 
 // Membrane vertex update, one warp per vertex: spring (Eq. strainFor),
@@ -390,41 +407,43 @@ __device__ __forceinline__ void box_add(int *box, const double *x) {
 // volume penalty (restoring reading of Eq. volFor) and element hydrodynamic
 // forces shared 1/3 per vertex (Eq. newtonSoft), with the lanes sharing the
 // incident hinges and triangles; Verlet positions (Eqs. verletPos,
-// verletVel); boundary velocity U_b = U + F/m_v dt; the Lagrangian force
-// F_l = U_b - U spread with c_l = A_l (Eq. bodyforce).
+// verletVel) in FP64, one lane per component; boundary velocity
+// U_b = U + F/m_v dt; the Lagrangian force F_l = U_b - U spread with
+// c_l = A_l (Eq. bodyforce).
 template <typename R>
 __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
                                                   uint32_t *__restrict__ stamp, uint32_t step) {
-    __shared__ double sV;
+    __shared__ R s_cv;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
         double s = 0.0;
         for (int i = lane; i < B.nvol_part; i += 32) s += B.vol_part[i];
         s = warp_sum(s);
-        if (lane == 0) sV = s / 6.0;
+        if (lane == 0) s_cv = R(B.kv * (1.0 - (s / 6.0) / B.V0));
     }
     __syncthreads();
-    const double V = sV;
+    const R cv = s_cv;
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (v >= B.nv) return;
-    const double *X = B.X;
+    const R *Xr = (const R *)B.Xrel;
+    const R *ks = (const R *)B.ks, *l0 = (const R *)B.l0, *kb = (const R *)B.kb, *th0 = (const R *)B.theta0;
     R F[3] = {R(0), R(0), R(0)};
     for (int q = B.vh_ptr[v] + lane; q < B.vh_ptr[v + 1]; q += 32) {
         const int code = B.vh_list[q];
         const int h = code >> 2, role = code & 3;
         const int4 H = B.hinge[h];
-        const double xa[3] = {X[3 * H.x], X[3 * H.x + 1], X[3 * H.x + 2]};
         R e[3], ac[3], ad[3];
         for (int a = 0; a < 3; ++a) {
-            e[a] = R(X[3 * H.y + a] - xa[a]);
-            ac[a] = R(X[3 * H.z + a] - xa[a]);
-            ad[a] = R(X[3 * H.w + a] - xa[a]);
+            const R xa = Xr[3 * H.x + a];
+            e[a] = Xr[3 * H.y + a] - xa;
+            ac[a] = Xr[3 * H.z + a] - xa;
+            ad[a] = Xr[3 * H.w + a] - xa;
         }
         const R le2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
         const R le = sqrt(le2);
         if (role < 2) {
             // F_a = -k (l - l0) (x_a - x_b)/l = k (l - l0) e / l, F_b = -F_a
-            const R c = R(B.ks[h]) * (le - R(B.l0[h])) / le;
+            const R c = ks[h] * (le - l0[h]) / le;
             const R sg = role == 0 ? R(1) : R(-1);
             for (int a = 0; a < 3; ++a) F[a] += sg * c * e[a];
         }
@@ -440,8 +459,8 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         const R cx[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
         const R theta = atan2((cx[0] * e[0] + cx[1] * e[1] + cx[2] * e[2]) / le,
                               n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
-        const R dth = theta - R(B.theta0[h]);
-        const R dE = B.bend_variant ? R(B.kb[h]) * dth : R(B.kb[h]) * sin(dth);
+        const R dth = theta - th0[h];
+        const R dE = B.bend_variant ? kb[h] * dth : kb[h] * sin(dth);
         const R h1 = l1 / le, h2 = l2 / le;
         const R tc = (ac[0] * e[0] + ac[1] * e[1] + ac[2] * e[2]) / le2;
         const R td = (ad[0] * e[0] + ad[1] * e[1] + ad[2] * e[2]) / le2;
@@ -462,38 +481,39 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         for (int a = 0; a < 3; ++a) F[a] -= dE * (c1 * n1[a] / h1 + c2 * n2[a] / h2);
     }
     // element terms: volume penalty and hydrodynamic force, 1/3 per vertex
-    const R cv = R(B.kv * (1.0 - V / B.V0));
-    double Al = 0.0;
+    R Al = R(0);
     for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32) {
         const int t = B.vt_list[q] / 3;
-        const double *tg = B.tri_geo + 8 * t;
-        Al += tg[3] / 3.0;
-        double Fh[3];
-        tri_hydro(B, t, Fh);
-        for (int a = 0; a < 3; ++a) F[a] += cv * R(tg[a]) * R(tg[3]) / R(3) + R(Fh[a] / 3.0);
+        const R *tg = (const R *)B.tri_geo + 8 * t;
+        Al += tg[3] / R(3);
+        R Fh[3];
+        tri_hydro<R>(B, t, Fh);
+        for (int a = 0; a < 3; ++a) F[a] += (cv * tg[a] * tg[3] + Fh[a]) / R(3);
     }
     for (int a = 0; a < 3; ++a) F[a] = warp_sum(F[a]);
     Al = warp_sum(Al);
-    // Newton (Eq. newtonSoft) and Verlet (Eqs. verletPos, verletVel), dt = 1
-    double Fl[3];
-    for (int a = 0; a < 3; ++a) {
-        const double acc = (double)F[a] / B.mv;
+    // Newton (Eq. newtonSoft) and Verlet (Eqs. verletPos, verletVel), dt = 1,
+    // lane a < 3 integrates component a in FP64
+    R fl = R(0);
+    if (lane < 3) {
+        const int a = lane;
+        const double acc = (double)(a == 0 ? F[0] : a == 1 ? F[1] : F[2]) / B.mv;
         const double U = B.U[3 * v + a];
         const double Ub = U + acc;
-        Fl[a] = Ub - U;
-        if (lane == 0) {
-            const double x = X[3 * v + a], xp = B.Xprev[3 * v + a];
-            const double xt = x + U + 0.5 * acc;
-            const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
-            B.Xnew[3 * v + a] = x + ubdf + 0.5 * acc;
-            B.Ub[3 * v + a] = Ub;
-            B.Fl[3 * v + a] = Fl[a];
-        }
+        const double Fla = Ub - U;
+        const double x = B.X[3 * v + a], xp = B.Xprev[3 * v + a];
+        const double xt = x + U + 0.5 * acc;
+        const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
+        const double xn = x + ubdf + 0.5 * acc;
+        B.Xnew[3 * v + a] = xn;
+        ((R *)B.Xrel_next)[3 * v + a] = R(xn - B.origin[a]);
+        B.Ub[3 * v + a] = Ub;
+        B.Fl[3 * v + a] = Fla;
+        box_add(B.bbox_next, a, xn);
+        fl = R(Fla);
     }
-    if (lane == 0) {
-        double xn[3] = {B.Xnew[3 * v], B.Xnew[3 * v + 1], B.Xnew[3 * v + 2]};
-        box_add(B.bbox_next, xn);
-    }
+    const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
+                     __shfl_sync(0xffffffffu, fl, 2)};
     spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
 }
 
@@ -501,16 +521,18 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
 // gravity minus buoyancy, F = m du/dt and M = I dw/dt with I in the world
 // frame, second-order backward velocities (Eqs. linearVelRig,
 // angularVelRig), centre and orientation advanced with the new velocities.
-__global__ void __launch_bounds__(256) k_rigid_update(BodyView B) {
-    __shared__ double red[6][256];
+template <typename R>
+__global__ void __launch_bounds__(1024) k_rigid_update(BodyView B) {
+    __shared__ double red[6][32];
     double *S = B.rstate;
-    const double xc[3] = {S[RigidState::XC], S[RigidState::XC + 1], S[RigidState::XC + 2]};
-    double f[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+    const R xc[3] = {R(S[RigidState::XC] - B.origin[0]), R(S[RigidState::XC + 1] - B.origin[1]),
+                     R(S[RigidState::XC + 2] - B.origin[2])};
+    R f[3] = {R(0), R(0), R(0)}, m[3] = {R(0), R(0), R(0)};
     for (int t = threadIdx.x; t < B.nt; t += blockDim.x) {
-        double Fh[3];
-        tri_hydro(B, t, Fh);
-        const double *tg = B.tri_geo + 8 * t;
-        const double r[3] = {tg[4] - xc[0], tg[5] - xc[1], tg[6] - xc[2]};
+        R Fh[3];
+        tri_hydro<R>(B, t, Fh);
+        const R *tg = (const R *)B.tri_geo + 8 * t;
+        const R r[3] = {tg[4] - xc[0], tg[5] - xc[1], tg[6] - xc[2]};
         f[0] += Fh[0];
         f[1] += Fh[1];
         f[2] += Fh[2];
@@ -518,42 +540,41 @@ __global__ void __launch_bounds__(256) k_rigid_update(BodyView B) {
         m[1] += r[2] * Fh[0] - r[0] * Fh[2];
         m[2] += r[0] * Fh[1] - r[1] * Fh[0];
     }
-    for (int a = 0; a < 3; ++a) {
-        red[a][threadIdx.x] = f[a];
-        red[3 + a][threadIdx.x] = m[a];
+    double acc6[6] = {(double)f[0], (double)f[1], (double)f[2], (double)m[0], (double)m[1], (double)m[2]};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < 6; ++q) {
+        const double w = warp_sum(acc6[q]);
+        if (lane == 0) red[q][warp] = w;
     }
     __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-            for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
+    if (warp != 0) return;
+    for (int q = 0; q < 6; ++q) acc6[q] = warp_sum(lane < (int)(blockDim.x >> 5) ? red[q][lane] : 0.0);
+    if (lane != 0) return;
     double F[3], M[3];
     for (int a = 0; a < 3; ++a) {
-        F[a] = red[a][0] + (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + a];
-        M[a] = red[3 + a][0];
+        F[a] = acc6[a] + (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + a];
+        M[a] = acc6[3 + a];
     }
     const double *q = S + RigidState::Q4;
     const double *Ib = S + RigidState::IB;
-    double R[9];
+    double Rm[9];
     {
         const double w = q[0], x = q[1], y = q[2], z = q[3];
-        R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-        R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-        R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+        Rm[0] = 1 - 2 * (y * y + z * z); Rm[1] = 2 * (x * y - w * z); Rm[2] = 2 * (x * z + w * y);
+        Rm[3] = 2 * (x * y + w * z); Rm[4] = 1 - 2 * (x * x + z * z); Rm[5] = 2 * (y * z - w * x);
+        Rm[6] = 2 * (x * z - w * y); Rm[7] = 2 * (y * z + w * x); Rm[8] = 1 - 2 * (x * x + y * y);
     }
     double T[9], Iw[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * Ib[3 * k + j];
+            for (int k = 0; k < 3; ++k) acc += Rm[3 * i + k] * Ib[3 * k + j];
             T[3 * i + j] = acc;
         }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += T[3 * i + k] * R[3 * j + k];
+            for (int k = 0; k < 3; ++k) acc += T[3 * i + k] * Rm[3 * j + k];
             Iw[3 * i + j] = acc;
         }
     const double det = Iw[0] * (Iw[4] * Iw[8] - Iw[5] * Iw[7]) - Iw[1] * (Iw[3] * Iw[8] - Iw[5] * Iw[6]) +
@@ -576,8 +597,9 @@ __global__ void __launch_bounds__(256) k_rigid_update(BodyView B) {
         wn[a] = 2.0 / 3.0 * (2.0 * S[RigidState::W + a] - 0.5 * S[RigidState::WP + a] + wdot);
     }
     for (int a = 0; a < 3; ++a) {
-        S[RigidState::XC_OLD + a] = xc[a];
-        S[RigidState::XC + a] = xc[a] + un[a];
+        const double x0 = S[RigidState::XC + a];
+        S[RigidState::XC_OLD + a] = x0;
+        S[RigidState::XC + a] = x0 + un[a];
         S[RigidState::UP + a] = S[RigidState::U + a];
         S[RigidState::U + a] = un[a];
         S[RigidState::WP + a] = S[RigidState::W + a];
@@ -614,31 +636,29 @@ __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R 
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (v >= B.nv) return;
     const double *S = B.rstate;
-    const double *un = S + RigidState::U, *wn = S + RigidState::W, *xo = S + RigidState::XC_OLD;
-    const double *xc = S + RigidState::XC, *Rn = S + RigidState::ROT;
-    double Al = 0.0;
-    for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32) Al += B.tri_geo[8 * (B.vt_list[q] / 3) + 3] / 3.0;
+    R Al = R(0);
+    for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32)
+        Al += ((const R *)B.tri_geo)[8 * (B.vt_list[q] / 3) + 3] / R(3);
     Al = warp_sum(Al);
-    const double r[3] = {B.X[3 * v] - xo[0], B.X[3 * v + 1] - xo[1], B.X[3 * v + 2] - xo[2]};
-    const double wxr[3] = {wn[1] * r[2] - wn[2] * r[1], wn[2] * r[0] - wn[0] * r[2], wn[0] * r[1] - wn[1] * r[0]};
-    double Fl[3];
-    for (int a = 0; a < 3; ++a) {
-        const double ub = un[a] + wxr[a];
-        Fl[a] = ub - B.U[3 * v + a];
-        if (lane == 0) {
-            B.Ub[3 * v + a] = ub;
-            B.Fl[3 * v + a] = Fl[a];
-        }
-    }
-    if (lane == 0) {
+    R fl = R(0);
+    if (lane < 3) {
+        const int a = lane, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        const double *un = S + RigidState::U, *wn = S + RigidState::W, *xo = S + RigidState::XC_OLD;
+        const double *xc = S + RigidState::XC, *Rn = S + RigidState::ROT;
+        const double r1 = B.X[3 * v + a1] - xo[a1], r2 = B.X[3 * v + a2] - xo[a2];
+        const double ub = un[a] + (wn[a1] * r2 - wn[a2] * r1);  // (w x r)_a
+        const double Fla = ub - B.U[3 * v + a];
+        B.Ub[3 * v + a] = ub;
+        B.Fl[3 * v + a] = Fla;
         const double *xb = B.Xbody + 3 * v;
-        double xn[3];
-        for (int a = 0; a < 3; ++a) {
-            xn[a] = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
-            B.Xnew[3 * v + a] = xn[a];
-        }
-        box_add(B.bbox_next, xn);
+        const double xn = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
+        B.Xnew[3 * v + a] = xn;
+        ((R *)B.Xrel_next)[3 * v + a] = R(xn - B.origin[a]);
+        box_add(B.bbox_next, a, xn);
+        fl = R(Fla);
     }
+    const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
+                     __shfl_sync(0xffffffffu, fl, 2)};
     spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
 }
 
@@ -684,7 +704,10 @@ cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void 
 
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
                          uint32_t step, cudaStream_t s) {
-    k_rigid_update<<<1, 256, 0, s>>>(B);
+    if (prec == 0)
+        k_rigid_update<double><<<1, 1024, 0, s>>>(B);
+    else
+        k_rigid_update<float><<<1, 1024, 0, s>>>(B);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)((B.nv + 7) / 8);

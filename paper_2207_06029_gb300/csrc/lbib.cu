@@ -27,11 +27,14 @@ struct DevBody {
     lbib_body_params p{};
     double *X[3] = {nullptr, nullptr, nullptr};  // rotating buffers: prev, cur, next
     int cur = 1;
-    double *U = nullptr, *Ub = nullptr, *Fl = nullptr, *phi = nullptr, *tri_geo = nullptr, *probe = nullptr;
+    double *U = nullptr, *Ub = nullptr, *Fl = nullptr, *tri_vol = nullptr;
+    void *phi = nullptr, *tri_geo = nullptr, *probe = nullptr;  // arithmetic precision R
+    void *Xrel[2] = {nullptr, nullptr};                          // R: X - origin, current and next
     int *node = nullptr, *tri = nullptr, *vh_ptr = nullptr, *vh_list = nullptr, *vt_ptr = nullptr,
         *vt_list = nullptr;
     int4 *hinge = nullptr;
-    double *ks = nullptr, *l0 = nullptr, *kb = nullptr, *theta0 = nullptr, *Xbody = nullptr, *rstate = nullptr;
+    void *ks = nullptr, *l0 = nullptr, *kb = nullptr, *theta0 = nullptr;  // R per hinge
+    double *Xbody = nullptr, *rstate = nullptr;
     int *bbox[2] = {nullptr, nullptr};  // support-region node boxes, current and next
     int bcur = 0;
     double *vol_part = nullptr;
@@ -124,6 +127,13 @@ T *upload(Ctx *c, const std::vector<T> &v, int *rc) {
         }
     }
     return d;
+}
+
+// Uploads doubles in the arithmetic precision of the context.
+void *upload_r(Ctx *c, const std::vector<double> &v, int *rc) {
+    if (c->relem == 8) return upload(c, v, rc);
+    std::vector<float> f(v.begin(), v.end());
+    return upload(c, f, rc);
 }
 
 // Largest squared distance d2 for which sqrt(d2)/r_w <= 1 holds in IEEE
@@ -234,7 +244,10 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.node = b.node;
     v.tri = b.tri;
     v.tri_geo = b.tri_geo;
+    v.tri_vol = b.tri_vol;
     v.probe = b.probe;
+    v.Xrel = b.Xrel[b.bcur];
+    v.Xrel_next = b.Xrel[1 - b.bcur];
     v.vh_ptr = b.vh_ptr;
     v.vh_list = b.vh_list;
     v.vt_ptr = b.vt_ptr;
@@ -352,6 +365,35 @@ int lbib_create(const lbib_params *p, void **out) {
     for (int f = 0; f < 6; ++f)
         for (int a = 0; a < 3; ++a) L.wall_u[f][a] = p->wall_u[f][a];
     L.dist2_cut = mls_dist2_cut();
+    L.dist2_cut_f = (float)L.dist2_cut;
+    L.omega_d = 1.0 / p->tau;
+    L.cF_d = 1.0 - 0.5 / p->tau;
+    L.nu_d = (p->tau - 0.5) / 3.0;
+    L.omega_f = (float)L.omega_d;
+    L.cF_f = (float)L.cF_d;
+    L.nu_f = (float)L.nu_d;
+    for (int a = 0; a < 3; ++a) {
+        L.gext_d[a] = p->body_force[a];
+        L.gext_f[a] = (float)p->body_force[a];
+    }
+    // wall velocity per combination of faces: the face's own velocity on a
+    // face node, the mean of the faces' velocities on edges and corners
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+            for (int cx = 0; cx < 3; ++cx) {
+                const int code[3] = {cx, cy, cz};
+                int faces[3], nf = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (code[a]) faces[nf++] = 2 * a + (code[a] == 2);
+                double uw[3] = {0.0, 0.0, 0.0};
+                for (int j = 0; j < nf; ++j)
+                    for (int a = 0; a < 3; ++a) uw[a] += p->wall_u[faces[j]][a] / nf;
+                const int wc = wall_code(cx, cy, cz);
+                for (int a = 0; a < 3; ++a) {
+                    L.uw_d[wc][a] = uw[a];
+                    L.uw_f[wc][a] = (float)uw[a];
+                }
+            }
     c->ntiles = L.ntx * L.nty * L.ntz;
 
     cudaError_t e;
@@ -575,20 +617,28 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     b.U = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
     b.Ub = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
     b.Fl = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
-    b.phi = (double *)dev_alloc(c, sizeof(double) * 27 * (size_t)nv);
+    b.phi = dev_alloc(c, c->relem * 27 * (size_t)nv);
     b.node = (int *)dev_alloc(c, sizeof(int) * 27 * (size_t)nv);
     b.tri = upload(c, T, &rc);
-    b.tri_geo = (double *)dev_alloc(c, sizeof(double) * 8 * (size_t)nt);
-    b.probe = (double *)dev_alloc(c, sizeof(double) * 8 * (size_t)nt);
+    b.tri_geo = dev_alloc(c, c->relem * 8 * (size_t)nt);
+    b.tri_vol = (double *)dev_alloc(c, sizeof(double) * (size_t)nt);
+    b.probe = dev_alloc(c, c->relem * 8 * (size_t)nt);
     b.vh_ptr = upload(c, vh_ptr, &rc);
     b.vh_list = upload(c, vh_list, &rc);
     b.vt_ptr = upload(c, vt_ptr, &rc);
     b.vt_list = upload(c, vt_list, &rc);
     b.hinge = upload(c, hinge, &rc);
-    b.ks = upload(c, ks, &rc);
-    b.l0 = upload(c, l0, &rc);
-    b.kb = upload(c, kb, &rc);
-    b.theta0 = upload(c, th0, &rc);
+    b.ks = upload_r(c, ks, &rc);
+    b.l0 = upload_r(c, l0, &rc);
+    b.kb = upload_r(c, kb, &rc);
+    b.theta0 = upload_r(c, th0, &rc);
+    {
+        std::vector<double> xr(3 * (size_t)nv);
+        for (int v = 0; v < nv; ++v)
+            for (int a = 0; a < 3; ++a) xr[3 * v + a] = verts[3 * v + a] - b.origin[a];
+        b.Xrel[0] = upload_r(c, xr, &rc);
+        b.Xrel[1] = upload_r(c, xr, &rc);
+    }
     if (b.rigid) {
         double V, cen[3], I[9];
         mass_props(verts, nt, tris, &V, cen, I);
@@ -631,7 +681,7 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         b.nvol_part = mls_blocks(tmp);
         b.vol_part = upload(c, std::vector<double>((size_t)b.nvol_part, 0.0), &rc);
     }
-    if (rc || !b.phi || !b.node || !b.tri_geo || !b.probe) {
+    if (rc || !b.phi || !b.node || !b.tri_geo || !b.tri_vol || !b.probe) {
         c->err = rc ? rc : LBIB_ENOMEM;
         return fail(c, c->err, "body allocation or upload failed");
     }

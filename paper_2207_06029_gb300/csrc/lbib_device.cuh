@@ -86,6 +86,8 @@ struct Pop<__nv_bfloat16, float> {
 };
 
 // ---- views passed by value to kernels ----
+// Scalar parameters exist in both precisions so that the FP32 kernels never
+// touch the (slow) FP64 pipe for them; pick<R>() selects the copy.
 struct Lattice {
     int nx, ny, nz;
     int ntx, nty, ntz;      // tiles per axis
@@ -96,30 +98,47 @@ struct Lattice {
     double gext[3];
     double wall_u[6][3];
     double dist2_cut;       // largest |X - x_k|^2 whose MLS weight is non-zero
+    // derived, double and float copies
+    double omega_d, cF_d, nu_d, gext_d[3], uw_d[27][3];
+    float omega_f, cF_f, nu_f, gext_f[3], uw_f[27][3], dist2_cut_f;
 };
+
+template <typename R>
+__device__ __forceinline__ R pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// Wall velocity table index of a node: per axis 0 (interior), 1 (index-0
+// face), 2 (last face); entry = mean velocity of the faces present.
+__host__ __device__ constexpr int wall_code(int cx, int cy, int cz) { return cx + 3 * cy + 9 * cz; }
 
 struct BodyView {
     int nv, nt, rigid;
     const double *X;        // [3nv] positions of level n
     const double *Xprev;    // [3nv] positions of level n-1
     double *Xnew;           // [3nv] positions of level n+1 (written)
+    const void *Xrel;       // [3nv] R: X - origin of level n
+    void *Xrel_next;        // [3nv] R: X - origin of level n+1 (written)
     double *U;              // [3nv] interpolated fluid velocity
     double *Ub;             // [3nv] boundary velocity imposed by the IB force
     double *Fl;             // [3nv] Lagrangian IB force
-    double *phi;            // [27nv] MLS transfer weights of level n
+    void *phi;              // [27nv] R: MLS transfer weights of level n
     int *node;              // [27nv] support node indices
     const int *tri;         // [3nt]
-    double *tri_geo;        // [8nt] unit normal (3), area, centroid (3), volume term
-    double *probe;          // [8nt] per side: pressure p, traction tau.n (3)
+    void *tri_geo;          // [8nt] R: unit normal (3), area, centroid - origin (3), unused
+    double *tri_vol;        // [nt] volume terms (x_0 - o) . (e1 x e2)
+    void *probe;            // [8nt] R per side: pressure - 1/3, traction tau.n (3)
     // membrane topology (CSR over vertices)
     const int *vh_ptr;      // [nv+1]
     const int *vh_list;     // hinge*4 + role
     const int *vt_ptr;      // [nv+1]
     const int *vt_list;     // triangle*3 + corner
     const int4 *hinge;      // (a, b, c, d)
-    const double *ks, *l0, *kb, *theta0;
+    const void *ks, *l0, *kb, *theta0;  // R per hinge
     double V0, mv, kv;
-    double origin[3];       // reference point of the enclosed-volume sum
+    double origin[3];       // reference point of relative positions and of the volume sum
     int bend_variant;
     // rigid body
     const double *Xbody;    // [3nv] rest coordinates about the centre

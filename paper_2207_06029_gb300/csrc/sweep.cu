@@ -28,8 +28,7 @@ __host__ __device__ constexpr unsigned dirmask(int a, int sgn) {
 //   N_b = 1/2 sum_{e_A=0} g e_b - rho uw_b / 3
 //   g_i = g_opp + 6 w_i rho (e_i . uw) - sum_{b != A} e_ib N_b   (s e_iA > 0)
 template <int A, typename R>
-__device__ __forceinline__ void zouhe_face(R (&g)[Q], int s, const double *uwd) {
-    const R uw[3] = {R(uwd[0]), R(uwd[1]), R(uwd[2])};
+__device__ __forceinline__ void zouhe_face(R (&g)[Q], int s, const R *uw) {
     R sum0 = R(0), sumout = R(0), t[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -66,8 +65,7 @@ __device__ __forceinline__ void zouhe_face(R (&g)[Q], int s, const double *uwd) 
 // wall velocity and rho0 = 1; buried links (opposite also unknown) take
 // the equilibrium f^eq(1, uw).
 template <typename R>
-__device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const double *uwd) {
-    const R uw[3] = {R(uwd[0]), R(uwd[1]), R(uwd[2])};
+__device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const R *uw) {
     const R uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -116,9 +114,8 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
     }
 
     // walls (faces -x,+x,-y,+y,-z,+z; the index-0 face has inward normal +)
-    int nf = 0, fa = 0, fs = 0, face = 0;
+    int nf = 0, fa = 0, fs = 0, code[3] = {0, 0, 0};
     unsigned unknown = 0;
-    double uwsum[3] = {0.0, 0.0, 0.0};
     const int c[3] = {x, y, z}, n[3] = {nx, ny, nz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -132,27 +129,25 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
         ++nf;
         fa = a;
         fs = s;
-        face = 2 * a + (s < 0);
+        code[a] = s > 0 ? 1 : 2;
         unknown |= (a == 0 ? (s > 0 ? dirmask(0, 1) : dirmask(0, -1))
                            : a == 1 ? (s > 0 ? dirmask(1, 1) : dirmask(1, -1))
                                     : (s > 0 ? dirmask(2, 1) : dirmask(2, -1)));
     }
-    if (nf == 1) {
-        if (fa == 0)
-            zouhe_face<0>(g, fs, L.wall_u[face]);
-        else if (fa == 1)
-            zouhe_face<1>(g, fs, L.wall_u[face]);
-        else
-            zouhe_face<2>(g, fs, L.wall_u[face]);
-    } else if (nf > 1) {
-        for (int a = 0; a < 3; ++a) {
-            if (L.bc[a] != kWall) continue;
-            int s = c[a] == 0 ? 1 : (c[a] == n[a] - 1 ? -1 : 0);
-            if (!s) continue;
-            const int fc = 2 * a + (s < 0);
-            for (int b = 0; b < 3; ++b) uwsum[b] += L.wall_u[fc][b] / nf;
+    if (nf) {
+        const int wc = wall_code(code[0], code[1], code[2]);
+        R uw[3];
+        for (int b = 0; b < 3; ++b) uw[b] = pick<R>(L.uw_d[wc][b], L.uw_f[wc][b]);
+        if (nf == 1) {
+            if (fa == 0)
+                zouhe_face<0>(g, fs, uw);
+            else if (fa == 1)
+                zouhe_face<1>(g, fs, uw);
+            else
+                zouhe_face<2>(g, fs, uw);
+        } else {
+            wall_corner(g, unknown, uw);
         }
-        wall_corner(g, unknown, uwsum);
     }
 
     // moments of the streamed populations
@@ -173,9 +168,9 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
     // force of flagged tiles
     R F0 = R(0), F1 = R(0), F2 = R(0);
     if (nf == 0) {
-        F0 = R(L.gext[0]);
-        F1 = R(L.gext[1]);
-        F2 = R(L.gext[2]);
+        F0 = pick<R>(L.gext_d[0], L.gext_f[0]);
+        F1 = pick<R>(L.gext_d[1], L.gext_f[1]);
+        F2 = pick<R>(L.gext_d[2], L.gext_f[2]);
     }
     const int tile = (x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3));
     if (__ldg(stamp + tile) == step) {
@@ -193,7 +188,7 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
     // BGK collision with the Guo term, u = (sum f e + f_lb/2)/rho
     const R inv = R(1) / rho;
     const R ux = (jx + R(0.5) * F0) * inv, uy = (jy + R(0.5) * F1) * inv, uz = (jz + R(0.5) * F2) * inv;
-    const R omega = R(1.0 / L.tau), cF = R(1.0 - 0.5 / L.tau);
+    const R omega = pick<R>(L.omega_d, L.omega_f), cF = pick<R>(L.cF_d, L.cF_f);
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * F0 + uy * F1 + uz * F2;
 #pragma unroll

