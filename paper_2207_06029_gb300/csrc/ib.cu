@@ -15,7 +15,7 @@
 namespace lbib {
 
 constexpr int kPts = 32;          // MLS points per block
-constexpr int kMlsThreads = 128;  // 4 warps, 8 points each
+constexpr int kMlsThreads = 256;  // 8 warps, 4 points each
 constexpr double kAlpha = 0.3;    // Eq. (intKernel)
 constexpr double kRw = 1.3;       // support size r_w (Sec. 2.2)
 constexpr double kProbe = 1.2;    // probe length (Sec. 2.3)
@@ -244,8 +244,9 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     __syncthreads();
 
     // ---------------- phase 1: one warp per point, one lane per node ----------------
-    for (int j = 0; j < kPts / 4; ++j) {
-        const int lp = warp * (kPts / 4) + j;
+    constexpr int kPerWarp = kPts / (kMlsThreads / 32);
+    for (int j = 0; j < kPerWarp; ++j) {
+        const int lp = warp * kPerWarp + j;
         const int p = p0 + lp;
         if (p >= npts) break;
         R W = R(0), dk[3] = {R(0), R(0), R(0)};
@@ -294,7 +295,9 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                      W * dk[0] * dk[2], W * dk[1] * dk[1], W * dk[1] * dk[2], W * dk[2] * dk[2]};
 #pragma unroll
         for (int q = 0; q < 10; ++q) a10[q] = warp_sum(a10[q]);
-        if (lane < 10) sm.A[lp][lane] = a10[lane];
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 10; ++q) sm.A[lp][q] = a10[q];
     }
     __syncthreads();
 
@@ -305,17 +308,28 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
         if (!spd_inverse4(a, inv)) atomicCAS(err, 0, -1);
         for (int q = 0; q < 16; ++q) sm.Ai[lane][q] = R(inv[q]);
     }
-    if (threadIdx.x == 32 && B.vol_part) {  // fixed-order partial of the enclosed volume
+    if (threadIdx.x == 32) {
+        // enclosed volume: fixed-order partial per block, and the last block
+        // to finish sums the partials in block order (deterministic)
         double s = 0.0;
         for (int k = 0; k < kPts; ++k) s += sm.vol[k];
         B.vol_part[blockIdx.x] = s;
+        __threadfence();
+        const unsigned int done = atomicAdd(B.vol_count, 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            double tot = 0.0;
+            for (int k = 0; k < (int)gridDim.x; ++k) tot += ((volatile double *)B.vol_part)[k];
+            *B.vol_sum = tot;
+            *B.vol_count = 0u;
+        }
     }
     __syncthreads();
 
     // ---------------- phase 3 ----------------
     const R nu = pick<R>(L.nu_d, L.nu_f);
-    for (int j = 0; j < kPts / 4; ++j) {
-        const int lp = warp * (kPts / 4) + j;
+    for (int j = 0; j < kPerWarp; ++j) {
+        const int lp = warp * kPerWarp + j;
         const int p = p0 + lp;
         if (p >= npts) break;
         R W = R(0), d0 = R(0), d1 = R(0), d2 = R(0), rk = R(0), u0 = R(0), u1 = R(0), u2 = R(0);
@@ -415,23 +429,18 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
                                                   uint32_t *__restrict__ stamp, uint32_t step) {
     __shared__ R s_cv;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        double s = 0.0;
-        for (int i = lane; i < B.nvol_part; i += 32) s += B.vol_part[i];
-        s = warp_sum(s);
-        if (lane == 0) s_cv = R(B.kv * (1.0 - (s / 6.0) / B.V0));
-    }
+    if (threadIdx.x == 0) s_cv = R(B.kv * (1.0 - (*B.vol_sum / 6.0) / B.V0));
     __syncthreads();
     const R cv = s_cv;
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (v >= B.nv) return;
     const R *Xr = (const R *)B.Xrel;
-    const R *ks = (const R *)B.ks, *l0 = (const R *)B.l0, *kb = (const R *)B.kb, *th0 = (const R *)B.theta0;
     R F[3] = {R(0), R(0), R(0)};
     for (int q = B.vh_ptr[v] + lane; q < B.vh_ptr[v + 1]; q += 32) {
-        const int code = B.vh_list[q];
-        const int h = code >> 2, role = code & 3;
-        const int4 H = B.hinge[h];
+        const int role = B.vh_list[q] & 3;
+        const int4 H = B.vh_verts[q];
+        const R *par = (const R *)B.vh_par + 4 * q;  // k_s, l0, k_b, theta0
+        const R ksh = par[0], l0h = par[1], kbh = par[2], th0h = par[3];
         R e[3], ac[3], ad[3];
         for (int a = 0; a < 3; ++a) {
             const R xa = Xr[3 * H.x + a];
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         const R le = sqrt(le2);
         if (role < 2) {
             // F_a = -k (l - l0) (x_a - x_b)/l = k (l - l0) e / l, F_b = -F_a
-            const R c = ks[h] * (le - l0[h]) / le;
+            const R c = ksh * (le - l0h) / le;
             const R sg = role == 0 ? R(1) : R(-1);
             for (int a = 0; a < 3; ++a) F[a] += sg * c * e[a];
         }
@@ -459,8 +468,8 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         const R cx[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
         const R theta = atan2((cx[0] * e[0] + cx[1] * e[1] + cx[2] * e[2]) / le,
                               n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
-        const R dth = theta - th0[h];
-        const R dE = B.bend_variant ? kb[h] * dth : kb[h] * sin(dth);
+        const R dth = theta - th0h;
+        const R dE = B.bend_variant ? kbh * dth : kbh * sin(dth);
         const R h1 = l1 / le, h2 = l2 / le;
         const R tc = (ac[0] * e[0] + ac[1] * e[1] + ac[2] * e[2]) / le2;
         const R td = (ad[0] * e[0] + ad[1] * e[1] + ad[2] * e[2]) / le2;
@@ -668,7 +677,7 @@ int mls_blocks(const BodyView &B) { return (B.nv + 2 * B.nt + kPts - 1) / kPts; 
 template <typename S, typename R>
 static cudaError_t ib_front_t(const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm, int *err,
                               cudaStream_t s) {
-    k_moments<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, L, B.bbox, B.bbox_next, (R *)mom);
+    k_moments<S, R><<<2 * nsm, 256, 0, s>>>((const S *)fin, L, B.bbox, B.bbox_next, (R *)mom);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(MlsSmem<R>);

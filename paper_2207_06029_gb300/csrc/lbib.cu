@@ -37,7 +37,10 @@ struct DevBody {
     double *Xbody = nullptr, *rstate = nullptr;
     int *bbox[2] = {nullptr, nullptr};  // support-region node boxes, current and next
     int bcur = 0;
-    double *vol_part = nullptr;
+    double *vol_part = nullptr, *vol_sum = nullptr;
+    unsigned int *vol_count = nullptr;
+    int4 *vh_verts = nullptr;
+    void *vh_par = nullptr;
     int nvol_part = 0;
     double V0 = 0, A0 = 0, mv = 0, origin[3] = {0, 0, 0};
 };
@@ -268,6 +271,10 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.bbox_next = b.bbox[1 - b.bcur];
     v.vol_part = b.vol_part;
     v.nvol_part = b.nvol_part;
+    v.vol_count = b.vol_count;
+    v.vol_sum = b.vol_sum;
+    v.vh_verts = b.vh_verts;
+    v.vh_par = b.vh_par;
     (void)c;
     return v;
 }
@@ -680,6 +687,21 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         tmp.nt = nt;
         b.nvol_part = mls_blocks(tmp);
         b.vol_part = upload(c, std::vector<double>((size_t)b.nvol_part, 0.0), &rc);
+        b.vol_sum = upload(c, std::vector<double>(1, 6.0 * V0), &rc);
+        b.vol_count = upload(c, std::vector<unsigned int>(1, 0u), &rc);
+        // per (vertex, hinge) entry: the hinge's vertices and parameters
+        std::vector<int4> hv(vh_list.size());
+        std::vector<double> hp(4 * vh_list.size());
+        for (size_t q = 0; q < vh_list.size(); ++q) {
+            const int h2 = vh_list[q] >> 2;
+            hv[q] = hinge[h2];
+            hp[4 * q] = ks[h2];
+            hp[4 * q + 1] = l0[h2];
+            hp[4 * q + 2] = kb[h2];
+            hp[4 * q + 3] = th0[h2];
+        }
+        b.vh_verts = upload(c, hv, &rc);
+        b.vh_par = upload_r(c, hp, &rc);
     }
     if (rc || !b.phi || !b.node || !b.tri_geo || !b.tri_vol || !b.probe) {
         c->err = rc ? rc : LBIB_ENOMEM;

@@ -133,6 +133,8 @@ struct BodyView {
     // membrane topology (CSR over vertices)
     const int *vh_ptr;      // [nv+1]
     const int *vh_list;     // hinge*4 + role
+    const int4 *vh_verts;   // per entry: the hinge's vertices (a, b, c, d)
+    const void *vh_par;     // per entry, R: k_s, l0, k_b, theta0 of the hinge
     const int *vt_ptr;      // [nv+1]
     const int *vt_list;     // triangle*3 + corner
     const int4 *hinge;      // (a, b, c, d)
@@ -148,6 +150,8 @@ struct BodyView {
     int *bbox_next;         // [6], reset by the moments kernel, filled by the update kernel
     double *vol_part;       // [one per MLS block] partial sums of the volume terms
     int nvol_part;
+    unsigned int *vol_count; // blocks of the MLS kernel done (reset by the last one)
+    double *vol_sum;        // enclosed volume times 6, written by the last MLS block
 };
 
 // Layout of the rigid-body state block (doubles).

@@ -14,6 +14,11 @@
 
 namespace lbib {
 
+// representatives of the 9 pairs (i, opp(i)) with i < opp(i)
+__host__ __device__ constexpr int pair_rep(int k) {
+    return k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 5 : k == 3 ? 7 : k == 4 ? 8 : k == 5 ? 9 : k == 6 ? 10 : k == 7 ? 15 : 16;
+}
+
 __host__ __device__ constexpr unsigned dirmask(int a, int sgn) {
     unsigned m = 0;
     for (int i = 0; i < Q; ++i)
@@ -150,17 +155,16 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
         }
     }
 
-    // moments of the streamed populations
-    R dr = R(0), jx = R(0), jy = R(0), jz = R(0);
+    // moments of the streamed populations, over the pairs (i, opp(i))
+    R dr = g[0], jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        dr += g[i];
-        if (ex(i) > 0) jx += g[i];
-        if (ex(i) < 0) jx -= g[i];
-        if (ey(i) > 0) jy += g[i];
-        if (ey(i) < 0) jy -= g[i];
-        if (ez(i) > 0) jz += g[i];
-        if (ez(i) < 0) jz -= g[i];
+    for (int k = 0; k < 9; ++k) {
+        const int i = pair_rep(k), o = opp(i);
+        const R sum = g[i] + g[o], dif = g[i] - g[o];
+        dr += sum;
+        if (ex(i)) jx += R(ex(i)) * dif;
+        if (ey(i)) jy += R(ey(i)) * dif;
+        if (ez(i)) jz += R(ez(i)) * dif;
     }
     const R rho = R(1) + dr;
 
@@ -185,21 +189,34 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
         }
     }
 
-    // BGK collision with the Guo term, u = (sum f e + f_lb/2)/rho
+    // BGK collision with the Guo term, u = (sum f e + f_lb/2)/rho.  Per
+    // direction, with a = 3 omega rho, b = 4.5 omega rho, c3 = 3 cF,
+    // c9 = 9 cF and A0 = omega (drho - 1.5 rho u.u) - 3 cF u.F:
+    //   g*_i = (1 - omega) g_i + w_i [A0 + E_i + O_i],
+    //   E_i = eu (b eu + c9 eF) (even in e_i),  O_i = a eu + c3 eF (odd),
+    // which is g - omega (g - (f^eq - w)) + F_i of Eqs. (evoleq, eqfunc,
+    // forcing) regrouped so that each pair (i, opp(i)) shares E and O.
     const R inv = R(1) / rho;
     const R ux = (jx + R(0.5) * F0) * inv, uy = (jy + R(0.5) * F1) * inv, uz = (jz + R(0.5) * F2) * inv;
     const R omega = pick<R>(L.omega_d, L.omega_f), cF = pick<R>(L.cF_d, L.cF_f);
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * F0 + uy * F1 + uz * F2;
+    const R om1 = R(1) - omega, ca = R(3) * omega * rho, cb = R(4.5) * omega * rho;
+    const R c3 = R(3) * cF, c9 = R(9) * cF;
+    const R A0 = omega * (dr - R(1.5) * rho * uu) - c3 * uF;
+    Pop<S, R>::st(fout + idx, om1 * g[0] + wq<R>(0) * A0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const R eu = R(ex(i)) * ux + R(ey(i)) * uy + R(ez(i)) * uz;
-        const R eF = R(ex(i)) * F0 + R(ey(i)) * F1 + R(ez(i)) * F2;
+    for (int k = 0; k < 9; ++k) {
+        const int i = pair_rep(k), o = opp(i);
+        R eu = R(0), eF = R(0);
+        if (ex(i)) { eu += R(ex(i)) * ux; eF += R(ex(i)) * F0; }
+        if (ey(i)) { eu += R(ey(i)) * uy; eF += R(ey(i)) * F1; }
+        if (ez(i)) { eu += R(ez(i)) * uz; eF += R(ez(i)) * F2; }
         const R w = wq<R>(i);
-        const R dfeq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
-        const R Fi = cF * w * (R(3) * (eF - uF) + R(9) * eu * eF);
-        const R gn = g[i] - omega * (g[i] - dfeq) + Fi;
-        Pop<S, R>::st(fout + (long long)i * st + idx, gn);
+        const R E = eu * (cb * eu + c9 * eF), Od = ca * eu + c3 * eF;
+        const R base = w * (A0 + E), odd = w * Od;
+        Pop<S, R>::st(fout + (long long)i * st + idx, om1 * g[i] + (base + odd));
+        Pop<S, R>::st(fout + (long long)o * st + idx, om1 * g[o] + (base - odd));
     }
     if (fields) {
         fields[idx] = rho;
