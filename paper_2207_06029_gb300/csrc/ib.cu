@@ -90,6 +90,8 @@ __global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Latt
     }
 }
 
+constexpr int kSums = 26;  // A (10 entries), b for rho (4), b for u (12)
+
 template <typename R>
 struct MlsSmem {
     // per point, filled in phase 0 (one lane per point)
@@ -99,13 +101,14 @@ struct MlsSmem {
     R fracR[kPts][3];
     R nrm[kPts][3];
     double vol[kPts];
-    // per point and support node
+    // per point and support node, kept for the transfer weights of markers
     R W[kPts][27];
     R d[kPts][27][3];
-    R rho[kPts][27];
-    R u[kPts][27][3];
-    R A[kPts][10];
-    R Ai[kPts][16];
+    // per point: A = sum W p p^T, b_f = sum W p f for f = rho - 1, u_x, u_y, u_z
+    R sums[kPts][kSums];
+    R row0[kPts][4];  // first row of A^-1
+    // per warp: transpose buffer of the 26 products of each node
+    R red[kMlsThreads / 32][kSums][33];
 };
 
 // Inverse of a symmetric positive definite 4x4 matrix given by its upper
@@ -160,18 +163,21 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
     return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
 }
 
-// MLS at markers and probes, one warp per point, 32 points per block.
-// Points 0..nv-1 are the markers; point nv + 2t + side is the probe of
-// triangle t on the outer (side 0) or inner (side 1) face.
+// MLS at markers and probes, 32 points per block.  Points 0..nv-1 are the
+// markers; point nv + 2t + side is the probe of triangle t on the outer
+// (side 0) or inner (side 1) face.  With p_k = (1, x_k - X) the fit of a
+// field f is a = A^-1 b_f, A = sum_k W_k p_k p_k^T, b_f = sum_k W_k p_k f_k
+// (Eq. l2norm), i.e. f(X) = a_0 and grad f = (a_1, a_2, a_3).
 //  phase 0: one lane per point: position (probes: triangle geometry), the
 //           nearest node base = floor(X + 1/2) and the exact offset X - base;
 //  phase 1: one warp per point, one lane per support node: weight
 //           W = exp(-(r/alpha)^2) for r <= 1 (the cut-off decided exactly as
-//           in FP64), node moments, moment matrix A (warp reduction);
-//  phase 2: one lane per point: FP64 Cholesky inverse of A;
-//  phase 3: shape functions psi_k = W_k A^-1 p_k; markers interpolate U and
-//           keep phi = psi[0] for spreading; probes fit rho and u and store
-//           pressure and traction.
+//           in FP64), node moments, the 26 products W p p^T and W p f,
+//           summed over the nodes through a shared-memory transpose;
+//  phase 2: one lane per point: FP64 Cholesky inverse of A; markers get
+//           U = (A^-1 b_u)_0 (Eq. uLag), probes the pressure c_s^2 rho and
+//           the traction rho nu (grad u + grad u^T) . n from the fits;
+//  phase 3: markers keep phi_k = W_k (A^-1 p_k)_0 for spreading.
 template <typename R>
 __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, Lattice L, BodyView B,
                                                      int *err) {
@@ -245,11 +251,13 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
 
     // ---------------- phase 1: one warp per point, one lane per node ----------------
     constexpr int kPerWarp = kPts / (kMlsThreads / 32);
+    R(*red)[33] = sm.red[warp];
     for (int j = 0; j < kPerWarp; ++j) {
         const int lp = warp * kPerWarp + j;
         const int p = p0 + lp;
         if (p >= npts) break;
-        R W = R(0), dk[3] = {R(0), R(0), R(0)};
+        const bool probe = p >= B.nv;
+        R W = R(0), dk[3] = {R(0), R(0), R(0)}, rk = R(0), uk[3] = {R(0), R(0), R(0)};
         if (lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
             int cw[3];
@@ -282,31 +290,83 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                 W = exp(-(r / R(kAlpha)) * (r / R(kAlpha)));
             }
             const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
-            if (p < B.nv) B.node[27 * p + lane] = node;
+            uk[0] = mom[st + node];
+            uk[1] = mom[2 * st + node];
+            uk[2] = mom[3 * st + node];
+            if (probe) {
+                rk = mom[node];
+            } else {
+                B.node[27 * p + lane] = node;
+            }
             sm.W[lp][lane] = W;
-            sm.rho[lp][lane] = mom[node];
-            sm.u[lp][lane][0] = mom[st + node];
-            sm.u[lp][lane][1] = mom[2 * st + node];
-            sm.u[lp][lane][2] = mom[3 * st + node];
             for (int a = 0; a < 3; ++a) sm.d[lp][lane][a] = dk[a];
         }
-        // moment matrix A = sum W p p^T, p = (1, x_k - X)
-        R a10[10] = {W, W * dk[0], W * dk[1], W * dk[2], W * dk[0] * dk[0], W * dk[0] * dk[1],
-                     W * dk[0] * dk[2], W * dk[1] * dk[1], W * dk[1] * dk[2], W * dk[2] * dk[2]};
+        // the 26 products of this node (zero on lanes 27..31)
+        const R Wd[4] = {W, W * dk[0], W * dk[1], W * dk[2]};
+        red[0][lane] = Wd[0];
+        red[1][lane] = Wd[1];
+        red[2][lane] = Wd[2];
+        red[3][lane] = Wd[3];
+        red[4][lane] = Wd[1] * dk[0];
+        red[5][lane] = Wd[1] * dk[1];
+        red[6][lane] = Wd[1] * dk[2];
+        red[7][lane] = Wd[2] * dk[1];
+        red[8][lane] = Wd[2] * dk[2];
+        red[9][lane] = Wd[3] * dk[2];
 #pragma unroll
-        for (int q = 0; q < 10; ++q) a10[q] = warp_sum(a10[q]);
-        if (lane == 0)
+        for (int q = 0; q < 4; ++q) {
+            red[10 + q][lane] = Wd[q] * rk;
+            red[14 + q][lane] = Wd[q] * uk[0];
+            red[18 + q][lane] = Wd[q] * uk[1];
+            red[22 + q][lane] = Wd[q] * uk[2];
+        }
+        __syncwarp();
+        if (lane < kSums) {
+            R acc = R(0);
 #pragma unroll
-            for (int q = 0; q < 10; ++q) sm.A[lp][q] = a10[q];
+            for (int k = 0; k < 27; ++k) acc += red[lane][k];
+            sm.sums[lp][lane] = acc;
+        }
+        __syncwarp();
     }
     __syncthreads();
 
-    // ---------------- phase 2: FP64 solves, one lane per point ----------------
+    // ---------------- phase 2: one lane per point ----------------
     if (warp == 0 && p0 + lane < npts) {
+        const int p = p0 + lane;
+        const R *S = sm.sums[lane];
         double a[10], inv[16];
-        for (int q = 0; q < 10; ++q) a[q] = (double)sm.A[lane][q];
+        for (int q = 0; q < 10; ++q) a[q] = (double)S[q];
         if (!spd_inverse4(a, inv)) atomicCAS(err, 0, -1);
-        for (int q = 0; q < 16; ++q) sm.Ai[lane][q] = R(inv[q]);
+        R Ai[16];
+        for (int q = 0; q < 16; ++q) Ai[q] = R(inv[q]);
+        if (p < B.nv) {
+            for (int q = 0; q < 4; ++q) sm.row0[lane][q] = Ai[q];
+            for (int jj = 0; jj < 3; ++jj) {
+                const R *bu = S + 14 + 4 * jj;
+                B.U[3 * p + jj] = (double)(Ai[0] * bu[0] + Ai[1] * bu[1] + Ai[2] * bu[2] + Ai[3] * bu[3]);
+            }
+        } else {
+            // fits: c_f[i] = sum_m Ai[i][m] b_f[m]
+            R cr[4], cu[3][4];
+            for (int i = 0; i < 4; ++i) {
+                cr[i] = Ai[4 * i] * S[10] + Ai[4 * i + 1] * S[11] + Ai[4 * i + 2] * S[12] + Ai[4 * i + 3] * S[13];
+                for (int jj = 0; jj < 3; ++jj) {
+                    const R *bu = S + 14 + 4 * jj;
+                    cu[jj][i] = Ai[4 * i] * bu[0] + Ai[4 * i + 1] * bu[1] + Ai[4 * i + 2] * bu[2] + Ai[4 * i + 3] * bu[3];
+                }
+            }
+            const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
+            const R rho = R(1) + cr[0];
+            const R nu = pick<R>(L.nu_d, L.nu_f);
+            R *pr = (R *)B.probe + 8 * t + 4 * side;
+            pr[0] = cr[0] / R(3);  // p - c_s^2 rho0
+            for (int jj = 0; jj < 3; ++jj) {
+                R acc = R(0);
+                for (int m = 0; m < 3; ++m) acc += rho * nu * (cu[jj][1 + m] + cu[m][1 + jj]) * sm.nrm[lane][m];
+                pr[1 + jj] = acc;
+            }
+        }
     }
     if (threadIdx.x == 32) {
         // enclosed volume: fixed-order partial per block, and the last block
@@ -326,57 +386,16 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     }
     __syncthreads();
 
-    // ---------------- phase 3 ----------------
-    const R nu = pick<R>(L.nu_d, L.nu_f);
+    // ---------------- phase 3: transfer weights of the markers ----------------
     for (int j = 0; j < kPerWarp; ++j) {
         const int lp = warp * kPerWarp + j;
         const int p = p0 + lp;
-        if (p >= npts) break;
-        R W = R(0), d0 = R(0), d1 = R(0), d2 = R(0), rk = R(0), u0 = R(0), u1 = R(0), u2 = R(0);
+        if (p >= B.nv || p >= npts) break;
         if (lane < 27) {
-            W = sm.W[lp][lane];
-            d0 = sm.d[lp][lane][0];
-            d1 = sm.d[lp][lane][1];
-            d2 = sm.d[lp][lane][2];
-            rk = sm.rho[lp][lane];
-            u0 = sm.u[lp][lane][0];
-            u1 = sm.u[lp][lane][1];
-            u2 = sm.u[lp][lane][2];
-        }
-        const R *Ai = sm.Ai[lp];
-        if (p < B.nv) {
-            const R phi = W * (Ai[0] + Ai[1] * d0 + Ai[2] * d1 + Ai[3] * d2);
-            if (lane < 27) ((R *)B.phi)[27 * p + lane] = phi;
-            const R U0 = warp_sum(phi * u0), U1 = warp_sum(phi * u1), U2 = warp_sum(phi * u2);
-            if (lane < 3) B.U[3 * p + lane] = (double)(lane == 0 ? U0 : lane == 1 ? U1 : U2);
-        } else {
-            R psi[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                psi[i] = W * (Ai[4 * i] + Ai[4 * i + 1] * d0 + Ai[4 * i + 2] * d1 + Ai[4 * i + 3] * d2);
-            R fit[16];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                fit[i] = warp_sum(psi[i] * rk);
-                fit[4 + i] = warp_sum(psi[i] * u0);
-                fit[8 + i] = warp_sum(psi[i] * u1);
-                fit[12 + i] = warp_sum(psi[i] * u2);
-            }
-            if (lane == 0) {
-                const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
-                const R rho = R(1) + fit[0];
-                // grad u: du_j/dx_m = fit[4 + 4j + 1 + m]
-                R *pr = (R *)B.probe + 8 * t + 4 * side;
-                pr[0] = fit[0] / R(3);  // p - c_s^2 rho0
-#pragma unroll
-                for (int jj = 0; jj < 3; ++jj) {
-                    R acc = R(0);
-#pragma unroll
-                    for (int m = 0; m < 3; ++m)
-                        acc += rho * nu * (fit[4 + 4 * jj + 1 + m] + fit[4 + 4 * m + 1 + jj]) * sm.nrm[lp][m];
-                    pr[1 + jj] = acc;
-                }
-            }
+            const R *r0 = sm.row0[lp];
+            const R phi = sm.W[lp][lane] *
+                          (r0[0] + r0[1] * sm.d[lp][lane][0] + r0[2] * sm.d[lp][lane][1] + r0[3] * sm.d[lp][lane][2]);
+            ((R *)B.phi)[27 * p + lane] = phi;
         }
     }
 }
