@@ -30,12 +30,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19+IB MLUPS & % HBM peak; served runs/h, p50/p99 latency vs plain"
 UNIT = "MLUPS"
-WORKLOAD = "capsule_shear_96^3_Ca0.05_fp32"
 FALLBACK_HBM_GBS = 6800.0
 
 
-def workload_case():
+WORKLOADS = {
+    "capsule96": "capsule_shear_96^3_Ca0.05_fp32",
+    "settling": "settling_sphere_160x160x480_fp32",
+}
+
+
+def workload_case(name="capsule96"):
     from paper_2207_06029_gb300 import workloads as W
+    if name == "settling":
+        return W.case_settling(precision=W.PREC_FP32)
     return W.case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=0.05, Eb=0.01, kv=1.0,
                                 precision=W.PREC_FP32)
 
@@ -149,7 +156,7 @@ def run_gpu(args, rank, world):
     # L2 flush are all ordered on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    case = workload_case()
+    case = workload_case(args.workload)
     alloc_fn, free_fn, live = torch_allocator(torch)
     params = lbib.make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
                               stream=stream.cuda_stream)
@@ -184,9 +191,16 @@ def run_gpu(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, stops))
-    mls_ms, struct_ms, sweep_ms, nprof = lbib.lbib_get_profile(h)
-    lbib.lbib_profile(h, 0)
+    mls_ms, struct_ms, sweep_ms, step_ms, nprof = lbib.lbib_get_profile(h)
     _, launches1 = lbib.lbib_counters(h)
+    # the sweep alone (no concurrent IB work): a short extra loop with the
+    # overlap off, outside the timed region
+    lbib.lbib_set_overlap(h, 0)
+    for k in range(min(args.steps, 50)):
+        flush.zero_()
+        lbib.lbib_step(h, 1)
+    _, _, iso_sweep_ms, _, iso_n = lbib.lbib_get_profile(h)
+    lbib.lbib_profile(h, 0)
     lbib.lbib_destroy(h)
     live.clear()
 
@@ -223,16 +237,17 @@ def run_gpu(args, rank, world):
     h2d = (rho0.nbytes + u0.nbytes + b.verts.nbytes + b.tris.nbytes) / e2e_steps
     d2h = 3 * Xh.numel() * 8 + (rho_h.numel() + u_h.numel()) * 8 / e2e_steps
     return {"ms": ms, "sweep_ms": sweep_ms, "mls_ms": mls_ms, "struct_ms": struct_ms, "nprof": nprof,
+            "step_ms": step_ms, "iso_sweep_us": 1e3 * iso_sweep_ms / max(iso_n, 1),
             "launches": launches1 - launches0,
             "clocks": clk.summary(), "ncell": ncell, "e2e_s": e2e_s, "e2e_steps": e2e_steps, "h2d": h2d,
             "d2h": d2h, "nv": int(b.verts.shape[0]), "nt": int(b.tris.shape[0])}
 
 
-def cpu_baseline(seconds=12.0, min_steps=2):
+def cpu_baseline(seconds=12.0, min_steps=2, workload="capsule96"):
     """The FP64 oracle on the same workload, on the host cores, for a bounded
     number of steps (about `seconds` of CPU work)."""
     import oracle
-    case = workload_case()
+    case = workload_case(workload)
     s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
     s.set_fields(*case.initial_fields())
     b = case.bodies[0]
@@ -245,7 +260,7 @@ def cpu_baseline(seconds=12.0, min_steps=2):
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": case.ncell * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} steps of the 96^3 capsule case (FP64 oracle, OpenMP over z-planes)"}
+            "sample": f"{steps} steps of the {WORKLOADS[workload]} case (FP64 oracle, OpenMP over z-planes)"}
 
 
 def main():
@@ -256,6 +271,7 @@ def main():
     ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="capsule96", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -270,7 +286,7 @@ def main():
         for _ in range(args.warmup):
             pass
         import oracle
-        case = workload_case()
+        case = workload_case(args.workload)
         s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
         s.set_fields(*case.initial_fields())
         b = case.bodies[0]
@@ -285,9 +301,9 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": ksteps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / ksteps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": WORKLOAD, "cells": case.ncell},
+                "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "cells": case.ncell},
                 "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                 "sample": f"{ksteps} steps of the 96^3 capsule case"},
+                                 "sample": f"{ksteps} steps of the {WORKLOADS[args.workload]} case"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -319,22 +335,28 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
+        "config": {"workload": WORKLOADS[args.workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write)",
                    "fields_output": "off in the timed loop (e2e reads them)",
                    "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(), "kernel": "k_sweep<float,float>",
                      "peak_source": peak_kind, "sweep_us_per_step": 1e3 * r["sweep_ms"] / max(r["nprof"], 1),
+                     "sweep_alone_us": r["iso_sweep_us"],
+                     "sweep_alone_frac": bytes_per_launch / (r["iso_sweep_us"] * 1e-6) / 1e9 / peak,
                      "mls_us_per_step": 1e3 * r["mls_ms"] / max(r["nprof"], 1),
-                     "structure_us_per_step": 1e3 * r["struct_ms"] / max(r["nprof"], 1)},
+                     "structure_us_per_step": 1e3 * r["struct_ms"] / max(r["nprof"], 1),
+                     "step_us_per_step": 1e3 * r["step_ms"] / max(r["nprof"], 1),
+                     "note": "achieved = 152 B/cell x cells over the summed durations of the two sweep launches "
+                             "(outside and inside the body box) as they ran concurrently with the IB stage; "
+                             "sweep_alone_* is the same sweep timed with the overlap off"},
         "e2e": {"value": r["ncell"] * r["e2e_steps"] * world / r["e2e_s"] / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"])},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, workload=args.workload)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

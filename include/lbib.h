@@ -154,9 +154,16 @@ int lbib_profile(void *ctx, int enable);
 /* Timing since profiling was enabled or last read: ms[0] total
  * milliseconds of the MLS stage (support-region moments, interpolation and
  * probes), ms[1] of the structure update and spreading, ms[2] of the
- * collide-stream sweeps; nsteps receives the number of steps timed.
- * Synchronises and resets the accumulators. */
+ * collide-stream sweeps (both parts when they overlap the IB stage), ms[3]
+ * of the steps from start to end; nsteps receives the number of steps
+ * timed.  ms has 4 entries.  Synchronises and resets the accumulators. */
 int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
+
+/* With a single body, the sweep of the nodes outside the body's support
+ * box runs on a second stream concurrently with the IB stage (default 1);
+ * 0 runs one whole-lattice sweep after the IB stage.  Results are the same
+ * either way. */
+int lbib_set_overlap(void *ctx, int enable);
 
 /* When the sweep also writes the macroscopic fields read by
  * lbib_get_fields: fields_every = 0 (default) on the last step of each

@@ -111,48 +111,62 @@ struct MlsSmem {
     R red[kMlsThreads / 32][kSums][33];
 };
 
+// 1/d in FP64 from the FP32 reciprocal refined by two Newton steps
+// (relative error ~1e-7 -> ~1e-14 -> below the double rounding).
+__device__ __forceinline__ double recip64(double d) {
+    double r = (double)__frcp_rn((float)d);
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return r;
+}
+
 // Inverse of a symmetric positive definite 4x4 matrix given by its upper
-// triangle (00,01,02,03,11,12,13,22,23,33), through its Cholesky factor.
+// triangle (00,01,02,03,11,12,13,22,23,33), through A = L D L^T with unit
+// lower-triangular L: A^-1 = L^-T D^-1 L^-1.  Returns false if a pivot is
+// not positive.
 __device__ bool spd_inverse4(const double *a, double *inv) {
     double M[4][4];
     M[0][0] = a[0]; M[0][1] = M[1][0] = a[1]; M[0][2] = M[2][0] = a[2]; M[0][3] = M[3][0] = a[3];
     M[1][1] = a[4]; M[1][2] = M[2][1] = a[5]; M[1][3] = M[3][1] = a[6];
     M[2][2] = a[7]; M[2][3] = M[3][2] = a[8]; M[3][3] = a[9];
-    double Lw[4][4] = {{0}}, Li[4][4] = {{0}};
+    double Lw[4][4] = {{0}}, D[4], Di[4], Li[4][4] = {{0}};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        double s = M[j][j];
+        double dj = M[j][j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) s -= Lw[j][k] * Lw[j][k];
-        if (!(s > 0.0)) return false;
-        Lw[j][j] = sqrt(s);
+        for (int k = 0; k < j; ++k) dj -= Lw[j][k] * Lw[j][k] * D[k];
+        if (!(dj > 0.0)) return false;
+        D[j] = dj;
+        Di[j] = recip64(dj);
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
             double t = M[i][j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) t -= Lw[i][k] * Lw[j][k];
-            Lw[i][j] = t / Lw[j][j];
+            for (int k = 0; k < j; ++k) t -= Lw[i][k] * Lw[j][k] * D[k];
+            Lw[i][j] = t * Di[j];
         }
     }
+    // L^-1 (unit lower triangular)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        Li[i][i] = 1.0 / Lw[i][i];
+        Li[i][i] = 1.0;
 #pragma unroll
         for (int j = 0; j < i; ++j) {
             double t = 0.0;
 #pragma unroll
             for (int k = j; k < i; ++k) t += Lw[i][k] * Li[k][j];
-            Li[i][j] = -t * Li[i][i];
+            Li[i][j] = -t;
         }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = r; c < 4; ++c) {
             double t = 0.0;
 #pragma unroll
-            for (int k = (r > c ? r : c); k < 4; ++k) t += Li[k][r] * Li[k][c];
+            for (int k = c; k < 4; ++k) t += Li[k][r] * Di[k] * Li[k][c];
             inv[4 * r + c] = t;
+            inv[4 * c + r] = t;
         }
     return true;
 }
@@ -204,9 +218,14 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                 const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
                 const int *tv = B.tri + 3 * t;
                 const double *X = B.X;
+                const R *Xr = (const R *)B.Xrel;
                 const double x0[3] = {X[3 * tv[0]], X[3 * tv[0] + 1], X[3 * tv[0] + 2]};
-                const R e1[3] = {R(X[3 * tv[1]] - x0[0]), R(X[3 * tv[1] + 1] - x0[1]), R(X[3 * tv[1] + 2] - x0[2])};
-                const R e2[3] = {R(X[3 * tv[2]] - x0[0]), R(X[3 * tv[2] + 1] - x0[1]), R(X[3 * tv[2] + 2] - x0[2])};
+                R e1[3], e2[3];
+                for (int a = 0; a < 3; ++a) {
+                    const R r0 = Xr[3 * tv[0] + a];
+                    e1[a] = Xr[3 * tv[1] + a] - r0;
+                    e2[a] = Xr[3 * tv[2] + a] - r0;
+                }
                 const R N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                                 e1[0] * e2[1] - e1[1] * e2[0]};
                 const R nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);

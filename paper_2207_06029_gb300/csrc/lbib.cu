@@ -59,7 +59,9 @@ struct Ctx {
     int *h_err = nullptr;
     double *scratch = nullptr;
     size_t scratch_bytes = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr, stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_far = nullptr, ev_near = nullptr;
+    bool split_sweep = true;
     bool own_stream = false;
     std::vector<DevBody> bodies;
     uint32_t stamp_step = 0;
@@ -415,6 +417,14 @@ int lbib_create(const lbib_params *p, void **out) {
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_far, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_near, cudaEventDisableTiming) != cudaSuccess) {
+        g_create_error = std::string("stream/event creation: ") + cudaGetErrorString(cudaGetLastError());
+        lbib_destroy(c);
+        return LBIB_ECUDA;
+    }
     const size_t pop_bytes = (size_t)Q * L.stride * c->elem;
     c->fA = dev_alloc(c, pop_bytes);
     c->fB = dev_alloc(c, pop_bytes);
@@ -468,7 +478,11 @@ void lbib_destroy(void *h) {
     if (!h) return;
     Ctx *c = as_ctx(h);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->stream2) cudaStreamSynchronize(c->stream2);
     for (auto ev : c->events) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_far, c->ev_near})
+        if (ev) cudaEventDestroy(ev);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
     dev_free_all(c);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -719,22 +733,47 @@ int lbib_step(void *h, int nsteps) {
     if (!c) return LBIB_EINVAL;
     if (c->err) return c->err;
     if (nsteps < 0) return fail(c, LBIB_EINVAL, "nsteps < 0");
+    // With one body, the nodes outside its support box do not depend on the
+    // IB work of the step: they are swept on a second stream concurrently
+    // with it, and the box is swept after the spreading.
+    const bool split = c->bodies.size() == 1 && c->split_sweep;
+    if (split) {
+        cudaEventRecord(c->ev_fork, c->stream);
+        cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
+    }
     for (int it = 0; it < nsteps; ++it) {
         if (++c->stamp_step == 0) {  // flag wrap-around: clear the tile flags
             cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
             c->stamp_step = 1;
+            if (split) {
+                cudaEventRecord(c->ev_fork, c->stream);
+                cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
+            }
         }
         cudaEvent_t *ev = nullptr;
         if (c->profile) {
-            if (c->nev + 4 > c->events.size())
-                for (int k = 0; k < 4; ++k) {
+            if (c->nev + 6 > c->events.size())
+                for (int k = 0; k < 6; ++k) {
                     cudaEvent_t x;
                     if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
                     c->events.push_back(x);
                 }
             ev = &c->events[c->nev];
-            c->nev += 4;
+            c->nev += 6;
             cudaEventRecord(ev[0], c->stream);
+        }
+        const bool store = c->fields_every == 0 ? (it == nsteps - 1)
+                                                : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
+        void *fields = store ? c->fields : nullptr;
+        const int *box = split ? c->bodies[0].bbox[c->bodies[0].bcur] : nullptr;
+        if (split) {  // far field on the second stream
+            if (ev) cudaEventRecord(ev[4], c->stream2);
+            cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L, fields, 1,
+                                         box, c->nsm, c->stream2);
+            c->launches++;
+            if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel (outside the body box)");
+            if (ev) cudaEventRecord(ev[5], c->stream2);
+            cudaEventRecord(c->ev_far, c->stream2);
         }
         // IB front: support-region moments + MLS at markers and probes
         for (auto &b : c->bodies) {
@@ -758,13 +797,21 @@ int lbib_step(void *h, int nsteps) {
             if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
         }
         if (ev) cudaEventRecord(ev[2], c->stream);
-        const bool store = c->fields_every == 0 ? (it == nsteps - 1)
-                                                : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
-        cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L,
-                                     store ? c->fields : nullptr, c->stream);
+        cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L, fields,
+                                     split ? 2 : 0, box, c->nsm, c->stream);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
         if (ev) cudaEventRecord(ev[3], c->stream);
+        if (split) {
+            // the next step reads what both sweeps wrote and overwrites what
+            // this step's IB work and box sweep read
+            cudaStreamWaitEvent(c->stream, c->ev_far, 0);
+            cudaEventRecord(c->ev_near, c->stream);
+            cudaStreamWaitEvent(c->stream2, c->ev_near, 0);
+        } else if (ev) {
+            cudaEventRecord(ev[4], c->stream);
+            cudaEventRecord(ev[5], c->stream);
+        }
         std::swap(c->fA, c->fB);
         for (auto &b : c->bodies) {
             b.cur = (b.cur + 1) % 3;
@@ -909,17 +956,33 @@ int lbib_get_profile(void *h, double *ms, long long *nsteps) {
     Ctx *c = as_ctx(h);
     if (!c || !ms) return LBIB_EINVAL;
     cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream2);
     if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (size_t k = 0; k + 4 <= c->nev; k += 4)
-        for (int j = 0; j < 3; ++j) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, c->events[k + j], c->events[k + j + 1]);
-            acc[j] += t;
-        }
-    for (int j = 0; j < 3; ++j) ms[j] = acc[j];
-    if (nsteps) *nsteps = (long long)(c->nev / 4);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t k = 0; k + 6 <= c->nev; k += 6) {
+        const cudaEvent_t *ev = &c->events[k];
+        float t01 = 0.f, t12 = 0.f, t23 = 0.f, t45 = 0.f, t03 = 0.f, t05 = 0.f;
+        cudaEventElapsedTime(&t01, ev[0], ev[1]);
+        cudaEventElapsedTime(&t12, ev[1], ev[2]);
+        cudaEventElapsedTime(&t23, ev[2], ev[3]);
+        cudaEventElapsedTime(&t45, ev[4], ev[5]);
+        cudaEventElapsedTime(&t03, ev[0], ev[3]);
+        cudaEventElapsedTime(&t05, ev[0], ev[5]);
+        acc[0] += t01;
+        acc[1] += t12;
+        acc[2] += t23 + t45;
+        acc[3] += t03 > t05 ? t03 : t05;
+    }
+    for (int j = 0; j < 4; ++j) ms[j] = acc[j];
+    if (nsteps) *nsteps = (long long)(c->nev / 6);
     c->nev = 0;
+    return LBIB_OK;
+}
+
+int lbib_set_overlap(void *h, int enable) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    c->split_sweep = enable != 0;
     return LBIB_OK;
 }
 

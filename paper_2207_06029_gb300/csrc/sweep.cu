@@ -83,15 +83,12 @@ __device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const R
     }
 }
 
+// Stream, walls and collision of node (x, y, z).
 template <typename S, typename R>
-__global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
-                                               R *__restrict__ force, const uint32_t *__restrict__ stamp,
-                                               uint32_t step, Lattice L, R *__restrict__ fields) {
+__device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restrict__ fout, R *__restrict__ force,
+                                           const uint32_t *__restrict__ stamp, uint32_t step, const Lattice &L,
+                                           R *__restrict__ fields, int x, int y, int z) {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= nx || y >= ny) return;
     const int idx = x + nx * (y + ny * z);
     const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
     // neighbour coordinates; on walled axes an outside source is clamped to
@@ -226,6 +223,70 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
     }
 }
 
+// Node box of the current step, clamped to the lattice (walled axes) or to
+// one period (periodic axes); ext = 0 on an empty box.
+__device__ __forceinline__ void clamp_box(const Lattice &L, const int *box, int *lo, int *ext) {
+    const int n[3] = {L.nx, L.ny, L.nz};
+    for (int a = 0; a < 3; ++a) {
+        long long l = box[a], h = box[3 + a];
+        if (L.bc[a] == kWall) {
+            l = l < 0 ? 0 : l;
+            h = h > n[a] - 1 ? n[a] - 1 : h;
+        } else if (h - l + 1 > n[a]) {
+            l = 0;
+            h = n[a] - 1;
+        }
+        lo[a] = (int)l;
+        ext[a] = h < l ? 0 : (int)(h - l + 1);
+    }
+}
+
+__device__ __forceinline__ bool in_box(const Lattice &L, const int *lo, const int *ext, int x, int y, int z) {
+    const int c[3] = {x, y, z}, n[3] = {L.nx, L.ny, L.nz};
+    for (int a = 0; a < 3; ++a) {
+        int d = c[a] - lo[a];
+        if (L.bc[a] == kPeriodic) d = ((d % n[a]) + n[a]) % n[a];
+        if (d < 0 || d >= ext[a]) return false;
+    }
+    return true;
+}
+
+// Whole lattice (box == nullptr), or every node outside the box.
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
+                                               R *__restrict__ force, const uint32_t *__restrict__ stamp,
+                                               uint32_t step, Lattice L, R *__restrict__ fields,
+                                               const int *__restrict__ box) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= L.nx || y >= L.ny) return;
+    if (box) {
+        int lo[3], ext[3];
+        clamp_box(L, box, lo, ext);
+        if (in_box(L, lo, ext, x, y, z)) return;
+    }
+    sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z);
+}
+
+// The nodes inside the box (grid-stride; periodic coordinates wrap).
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S *__restrict__ fout,
+                                                   R *__restrict__ force, const uint32_t *__restrict__ stamp,
+                                                   uint32_t step, Lattice L, R *__restrict__ fields,
+                                                   const int *__restrict__ box) {
+    int lo[3], ext[3];
+    clamp_box(L, box, lo, ext);
+    const int total = ext[0] * ext[1] * ext[2];
+    const int n[3] = {L.nx, L.ny, L.nz};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
+        for (int a = 0; a < 3; ++a)
+            if (L.bc[a] == kPeriodic) c[a] = ((c[a] % n[a]) + n[a]) % n[a];
+        sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, c[0], c[1], c[2]);
+    }
+}
+
 // f = f^eq(rho, u) from double fields (Eq. eqfunc), stored as deviations.
 template <typename S, typename R>
 __global__ void k_init_equilibrium(S *__restrict__ fout, Lattice L, const double *__restrict__ rho,
@@ -293,22 +354,30 @@ static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
     grid = dim3((L.nx + bx - 1) / bx, (L.ny + by - 1) / by, L.nz);
 }
 
+// part: 0 whole lattice, 1 outside the box, 2 inside the box
 template <typename S, typename R>
 static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, uint32_t step,
-                           const Lattice &L, void *fields, cudaStream_t s) {
-    dim3 grid, block;
-    sweep_shape(L, grid, block);
-    k_sweep<S, R><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L, (R *)fields);
+                           const Lattice &L, void *fields, int part, const int *box, int nsm, cudaStream_t s) {
+    if (part == 2) {
+        k_sweep_box<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
+                                                  (R *)fields, box);
+    } else {
+        dim3 grid, block;
+        sweep_shape(L, grid, block);
+        k_sweep<S, R><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L, (R *)fields,
+                                             part == 1 ? box : nullptr);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
-                         uint32_t step, const Lattice &L, void *fields, cudaStream_t s) {
+                         uint32_t step, const Lattice &L, void *fields, int part, const int *box, int nsm,
+                         cudaStream_t s) {
     switch (prec) {
-        case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, s);
-        case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, s);
-        case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, s);
-        default: return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, s);
+        case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
+        case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
+        case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
+        default: return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
     }
 }
 

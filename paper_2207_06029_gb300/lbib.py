@@ -55,7 +55,7 @@ _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
-           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_device_bytes", "lbib_destroy",
+           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_device_bytes", "lbib_destroy",
            "lbib_last_error"]
 
 
@@ -84,6 +84,7 @@ def load():
         L.lbib_profile.argtypes = [vp, C.c_int]
         L.lbib_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
         L.lbib_set_output.argtypes = [vp, C.c_int]
+        L.lbib_set_overlap.argtypes = [vp, C.c_int]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_destroy.argtypes = [vp]
         L.lbib_destroy.restype = None
@@ -185,11 +186,15 @@ def lbib_profile(ctx, enable):
 
 
 def lbib_get_profile(ctx):
-    """Returns (mls_ms, structure_ms, sweep_ms, nsteps) accumulated since the last read."""
-    ms = (C.c_double * 3)()
+    """Returns (mls_ms, structure_ms, sweep_ms, step_ms, nsteps) accumulated since the last read."""
+    ms = (C.c_double * 4)()
     n = C.c_longlong()
     _check(ctx, load().lbib_get_profile(ctx, ms, C.byref(n)))
-    return ms[0], ms[1], ms[2], n.value
+    return ms[0], ms[1], ms[2], ms[3], n.value
+
+
+def lbib_set_overlap(ctx, enable):
+    return _check(ctx, load().lbib_set_overlap(ctx, int(enable)))
 
 
 def lbib_set_output(ctx, fields_every):

@@ -192,6 +192,23 @@ def test_fp32_settling_box_full_size(lbib):
     check_fp32(g, o)
 
 
+def test_overlapped_and_serial_sweeps_agree(lbib):
+    """The far-field sweep on the second stream plus the box sweep equals one
+    whole-lattice sweep (FP64; only the order of the atomic spreading sums
+    may differ)."""
+    case = W.case_capsule_shear(n=28, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01,
+                                kv=1.0, precision=W.PREC_FP64)
+    out = []
+    for overlap in (1, 0):
+        ctx = lbib.Context.from_case(case)
+        lbib.lbib_set_overlap(ctx.h, overlap)
+        ctx.step(25)
+        out.append((ctx.populations(), ctx.markers(0)[0]))
+        ctx.close()
+    assert rel(out[0][0], out[1][0]) < 1e-14
+    assert rel(out[0][1], out[1][1]) < 1e-14
+
+
 # ---------------------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------------------
