@@ -387,20 +387,33 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
             }
         }
     }
-    if (threadIdx.x == 32) {
-        // enclosed volume: fixed-order partial per block, and the last block
-        // to finish sums the partials in block order (deterministic)
-        double s = 0.0;
-        for (int k = 0; k < kPts; ++k) s += sm.vol[k];
-        B.vol_part[blockIdx.x] = s;
-        __threadfence();
-        const unsigned int done = atomicAdd(B.vol_count, 1u);
-        if (done == gridDim.x - 1) {
+    // enclosed volume (membranes): fixed-order partial per block; the last
+    // block to finish sums the partials with a fixed-shape tree
+    // (deterministic whichever block is last)
+    __shared__ int s_last;
+    if (!B.rigid) {
+        if (threadIdx.x == 32) {
+            double s = 0.0;
+            for (int k = 0; k < kPts; ++k) s += sm.vol[k];
+            B.vol_part[blockIdx.x] = s;
             __threadfence();
-            double tot = 0.0;
-            for (int k = 0; k < (int)gridDim.x; ++k) tot += ((volatile double *)B.vol_part)[k];
-            *B.vol_sum = tot;
-            *B.vol_count = 0u;
+            s_last = atomicAdd(B.vol_count, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double s = 0.0;
+            for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) s += __ldcg(B.vol_part + k);
+            s = warp_sum(s);
+            __shared__ double wpart[kMlsThreads / 32];
+            if (lane == 0) wpart[warp] = s;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < kMlsThreads / 32; ++w) tot += wpart[w];
+                *B.vol_sum = tot;
+                *B.vol_count = 0u;
+            }
         }
     }
     __syncthreads();
