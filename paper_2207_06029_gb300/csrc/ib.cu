@@ -21,6 +21,9 @@ constexpr double kRw = 1.3;       // support size r_w (Sec. 2.2)
 constexpr double kProbe = 1.2;    // probe length (Sec. 2.3)
 constexpr int kBoxLo = 3, kBoxHi = 4;  // node margins that cover marker and probe supports
 
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -95,8 +98,7 @@ constexpr int kSums = 26;  // A (10 entries), b for rho (4), b for u (12)
 template <typename R>
 struct MlsSmem {
     // per point, filled in phase 0 (one lane per point)
-    double P[kPts][3];
-    double frac[kPts][3];  // P - base, exact
+    double frac[kPts][3];  // X - base, exact
     int base[kPts][3];
     R fracR[kPts][3];
     R nrm[kPts][3];
@@ -121,53 +123,46 @@ __device__ __forceinline__ double recip64(double d) {
 }
 
 // Inverse of a symmetric positive definite 4x4 matrix given by its upper
-// triangle (00,01,02,03,11,12,13,22,23,33), through A = L D L^T with unit
-// lower-triangular L: A^-1 = L^-T D^-1 L^-1.  Returns false if a pivot is
-// not positive.
+// triangle (00,01,02,03,11,12,13,22,23,33), as the adjugate over the
+// determinant, both from the 2x2 minors of the top and bottom row pairs
+// (a shallow dependency chain: FP64 latency, not throughput, limits this
+// per-point solve).  Returns false unless the determinant is positive.
 __device__ bool spd_inverse4(const double *a, double *inv) {
-    double M[4][4];
-    M[0][0] = a[0]; M[0][1] = M[1][0] = a[1]; M[0][2] = M[2][0] = a[2]; M[0][3] = M[3][0] = a[3];
-    M[1][1] = a[4]; M[1][2] = M[2][1] = a[5]; M[1][3] = M[3][1] = a[6];
-    M[2][2] = a[7]; M[2][3] = M[3][2] = a[8]; M[3][3] = a[9];
-    double Lw[4][4] = {{0}}, D[4], Di[4], Li[4][4] = {{0}};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        double dj = M[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) dj -= Lw[j][k] * Lw[j][k] * D[k];
-        if (!(dj > 0.0)) return false;
-        D[j] = dj;
-        Di[j] = recip64(dj);
-#pragma unroll
-        for (int i = j + 1; i < 4; ++i) {
-            double t = M[i][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t -= Lw[i][k] * Lw[j][k] * D[k];
-            Lw[i][j] = t * Di[j];
-        }
-    }
-    // L^-1 (unit lower triangular)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        Li[i][i] = 1.0;
-#pragma unroll
-        for (int j = 0; j < i; ++j) {
-            double t = 0.0;
-#pragma unroll
-            for (int k = j; k < i; ++k) t += Lw[i][k] * Li[k][j];
-            Li[i][j] = -t;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = r; c < 4; ++c) {
-            double t = 0.0;
-#pragma unroll
-            for (int k = c; k < 4; ++k) t += Li[k][r] * Di[k] * Li[k][c];
-            inv[4 * r + c] = t;
-            inv[4 * c + r] = t;
-        }
+    const double m00 = a[0], m01 = a[1], m02 = a[2], m03 = a[3];
+    const double m11 = a[4], m12 = a[5], m13 = a[6], m22 = a[7], m23 = a[8], m33 = a[9];
+    // rows 0,1 and rows 2,3 (symmetric: m10 = m01, ...)
+    const double s0 = m00 * m11 - m01 * m01;
+    const double s1 = m00 * m12 - m02 * m01;
+    const double s2 = m00 * m13 - m03 * m01;
+    const double s3 = m01 * m12 - m02 * m11;
+    const double s4 = m01 * m13 - m03 * m11;
+    const double s5 = m02 * m13 - m03 * m12;
+    const double c5 = m22 * m33 - m23 * m23;
+    const double c4 = m12 * m33 - m13 * m23;
+    const double c3 = m12 * m23 - m13 * m22;
+    const double c2 = m02 * m33 - m03 * m23;
+    const double c1 = m02 * m23 - m03 * m22;
+    const double c0 = m02 * m13 - m03 * m12;
+    const double det = s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
+    if (!(det > 0.0)) return false;
+    const double id = recip64(det);
+    // rows of the adjugate (the matrix is symmetric, so is its inverse)
+    inv[0] = (m11 * c5 - m12 * c4 + m13 * c3) * id;
+    inv[1] = (-m01 * c5 + m02 * c4 - m03 * c3) * id;
+    inv[2] = (m13 * s5 - m23 * s4 + m33 * s3) * id;
+    inv[3] = (-m12 * s5 + m22 * s4 - m23 * s3) * id;
+    inv[5] = (m00 * c5 - m02 * c2 + m03 * c1) * id;
+    inv[6] = (-m03 * s5 + m23 * s2 - m33 * s1) * id;
+    inv[7] = (m02 * s5 - m22 * s2 + m23 * s1) * id;
+    inv[10] = (m03 * s4 - m13 * s2 + m33 * s0) * id;
+    inv[11] = (-m02 * s4 + m12 * s2 - m23 * s0) * id;
+    inv[15] = (m02 * s3 - m12 * s1 + m22 * s0) * id;
+    inv[4] = inv[1];
+    inv[8] = inv[2];
+    inv[9] = inv[6];
+    inv[12] = inv[3];
+    inv[13] = inv[7];
+    inv[14] = inv[11];
     return true;
 }
 
@@ -215,51 +210,47 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                 P[1] = B.X[3 * p + 1];
                 P[2] = B.X[3 * p + 2];
             } else {
+                // probe X_c +- 1.2 n, with X_c = x_0 + (e1 + e2)/3 and the
+                // triangle's edges and normal from origin-relative positions
                 const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
                 const int *tv = B.tri + 3 * t;
-                const double *X = B.X;
                 const R *Xr = (const R *)B.Xrel;
-                const double x0[3] = {X[3 * tv[0]], X[3 * tv[0] + 1], X[3 * tv[0] + 2]};
-                R e1[3], e2[3];
+                R r0[3], e1[3], e2[3];
                 for (int a = 0; a < 3; ++a) {
-                    const R r0 = Xr[3 * tv[0] + a];
-                    e1[a] = Xr[3 * tv[1] + a] - r0;
-                    e2[a] = Xr[3 * tv[2] + a] - r0;
+                    r0[a] = Xr[3 * tv[0] + a];
+                    e1[a] = Xr[3 * tv[1] + a] - r0[a];
+                    e2[a] = Xr[3 * tv[2] + a] - r0[a];
                 }
                 const R N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                                 e1[0] * e2[1] - e1[1] * e2[0]};
                 const R nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-                R nr[3];
-                double cen[3];
+                const R inn = R(1) / nn, sg = side ? R(-kProbe) : R(kProbe);
                 for (int a = 0; a < 3; ++a) {
-                    nr[a] = N[a] / nn;
-                    cen[a] = x0[a] + (double)((e1[a] + e2[a]) / R(3));
-                    sm.nrm[lane][a] = nr[a];
-                }
-                const double sg = side ? -kProbe : kProbe;
-                for (int a = 0; a < 3; ++a) P[a] = cen[a] + sg * (double)nr[a];
-                if (side == 0) {
-                    R *tg = (R *)B.tri_geo + 8 * t;
-                    for (int a = 0; a < 3; ++a) {
-                        tg[a] = nr[a];
-                        tg[4 + a] = R(cen[a] - B.origin[a]);
+                    const R nr = N[a] * inn, c3 = (e1[a] + e2[a]) / R(3);
+                    sm.nrm[lane][a] = nr;
+                    P[a] = B.X[3 * tv[0] + a] + (double)(c3 + sg * nr);
+                    if (side == 0) {
+                        R *tg = (R *)B.tri_geo + 8 * t;
+                        tg[a] = nr;
+                        tg[4 + a] = r0[a] + c3;
                     }
-                    tg[3] = R(0.5) * nn;
-                    const double v6 = (x0[0] - B.origin[0]) * (double)N[0] + (x0[1] - B.origin[1]) * (double)N[1] +
-                                      (x0[2] - B.origin[2]) * (double)N[2];
+                }
+                if (side == 0) {
+                    ((R *)B.tri_geo)[8 * t + 3] = R(0.5) * nn;
+                    const double v6 = (double)r0[0] * (double)N[0] + (double)r0[1] * (double)N[1] +
+                                      (double)r0[2] * (double)N[2];
                     B.tri_vol[t] = v6;
                     sm.vol[lane] = v6;
                 }
             }
             bool bad = false;
             for (int a = 0; a < 3; ++a) {
-                int b = (int)floor(P[a] + 0.5);
+                int b = __double2int_rd(P[a] + 0.5);  // floor(X + 1/2)
                 if (L.bc[a] == kWall && (b - 1 < 1 || b + 1 > n[a] - 2)) {
                     bad = true;
                     b = b < 2 ? 2 : (b > n[a] - 3 ? n[a] - 3 : b);
                 }
                 sm.base[lane][a] = b;
-                sm.P[lane][a] = P[a];
                 sm.frac[lane][a] = P[a] - (double)b;
                 sm.fracR[lane][a] = R(sm.frac[lane][a]);
             }
@@ -269,23 +260,43 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     __syncthreads();
 
     // ---------------- phase 1: one warp per point, one lane per node ----------------
+    // The gathers of the warp's points are issued together, then each
+    // point's weights and products are reduced in turn.
     constexpr int kPerWarp = kPts / (kMlsThreads / 32);
     R(*red)[33] = sm.red[warp];
+    R gu[kPerWarp][4];
+#pragma unroll
+    for (int j = 0; j < kPerWarp; ++j) {
+        const int lp = warp * kPerWarp + j;
+        const int p = p0 + lp;
+        gu[j][0] = gu[j][1] = gu[j][2] = gu[j][3] = R(0);
+        if (p < npts && lane < 27) {
+            const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+            int cw[3];
+            for (int a = 0; a < 3; ++a) {
+                const int cc = sm.base[lp][a] + dd[a];
+                cw[a] = L.bc[a] == kPeriodic ? ((cc % n[a]) + n[a]) % n[a] : cc;
+            }
+            const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
+            gu[j][1] = mom[st + node];
+            gu[j][2] = mom[2 * st + node];
+            gu[j][3] = mom[3 * st + node];
+            if (p >= B.nv)
+                gu[j][0] = mom[node];
+            else
+                B.node[27 * p + lane] = node;
+        }
+    }
+#pragma unroll
     for (int j = 0; j < kPerWarp; ++j) {
         const int lp = warp * kPerWarp + j;
         const int p = p0 + lp;
         if (p >= npts) break;
-        const bool probe = p >= B.nv;
-        R W = R(0), dk[3] = {R(0), R(0), R(0)}, rk = R(0), uk[3] = {R(0), R(0), R(0)};
+        R W = R(0), dk[3] = {R(0), R(0), R(0)};
         if (lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-            int cw[3];
-            for (int a = 0; a < 3; ++a) {
-                // x_k - X = dd - (X - base), one rounding like (base + dd) - X
-                dk[a] = R(dd[a]) - sm.fracR[lp][a];
-                const int cc = sm.base[lp][a] + dd[a];
-                cw[a] = L.bc[a] == kPeriodic ? ((cc % n[a]) + n[a]) % n[a] : cc;
-            }
+            // x_k - X = dd - (X - base), one rounding like (base + dd) - X
+            for (int a = 0; a < 3; ++a) dk[a] = R(dd[a]) - sm.fracR[lp][a];
             // support cut-off r_k <= 1 of Eq. (intKernel), decided on the FP64
             // squared distance; the FP32 path computes it in FP64 only near
             // the cut-off, where its own rounding could flip the decision
@@ -308,15 +319,6 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
                 const R r = sqrt(dist2) / R(kRw);
                 W = exp(-(r / R(kAlpha)) * (r / R(kAlpha)));
             }
-            const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
-            uk[0] = mom[st + node];
-            uk[1] = mom[2 * st + node];
-            uk[2] = mom[3 * st + node];
-            if (probe) {
-                rk = mom[node];
-            } else {
-                B.node[27 * p + lane] = node;
-            }
             sm.W[lp][lane] = W;
             for (int a = 0; a < 3; ++a) sm.d[lp][lane][a] = dk[a];
         }
@@ -334,10 +336,10 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
         red[9][lane] = Wd[3] * dk[2];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            red[10 + q][lane] = Wd[q] * rk;
-            red[14 + q][lane] = Wd[q] * uk[0];
-            red[18 + q][lane] = Wd[q] * uk[1];
-            red[22 + q][lane] = Wd[q] * uk[2];
+            red[10 + q][lane] = Wd[q] * gu[j][0];
+            red[14 + q][lane] = Wd[q] * gu[j][1];
+            red[18 + q][lane] = Wd[q] * gu[j][2];
+            red[22 + q][lane] = Wd[q] * gu[j][3];
         }
         __syncwarp();
         if (lane < kSums) {
@@ -500,31 +502,32 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
             ad[a] = Xr[3 * H.w + a] - xa;
         }
         const R le2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-        const R le = sqrt(le2);
+        const R le = sqrt(le2), ile = rcp(le);
         if (role < 2) {
             // F_a = -k (l - l0) (x_a - x_b)/l = k (l - l0) e / l, F_b = -F_a
-            const R c = ksh * (le - l0h) / le;
+            const R c = ksh * (le - l0h) * ile;
             const R sg = role == 0 ? R(1) : R(-1);
             for (int a = 0; a < 3; ++a) F[a] += sg * c * e[a];
         }
         const R N1[3] = {e[1] * ac[2] - e[2] * ac[1], e[2] * ac[0] - e[0] * ac[2], e[0] * ac[1] - e[1] * ac[0]};
         const R N2[3] = {ad[1] * e[2] - ad[2] * e[1], ad[2] * e[0] - ad[0] * e[2], ad[0] * e[1] - ad[1] * e[0]};
-        const R l1 = sqrt(N1[0] * N1[0] + N1[1] * N1[1] + N1[2] * N1[2]);
-        const R l2 = sqrt(N2[0] * N2[0] + N2[1] * N2[1] + N2[2] * N2[2]);
+        const R l1s = N1[0] * N1[0] + N1[1] * N1[1] + N1[2] * N1[2];
+        const R l2s = N2[0] * N2[0] + N2[1] * N2[1] + N2[2] * N2[2];
+        const R il1 = rcp(sqrt(l1s)), il2 = rcp(sqrt(l2s));
         R n1[3], n2[3];
         for (int a = 0; a < 3; ++a) {
-            n1[a] = N1[a] / l1;
-            n2[a] = N2[a] / l2;
+            n1[a] = N1[a] * il1;
+            n2[a] = N2[a] * il2;
         }
         const R cx[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
-        const R theta = atan2((cx[0] * e[0] + cx[1] * e[1] + cx[2] * e[2]) / le,
+        const R theta = atan2((cx[0] * e[0] + cx[1] * e[1] + cx[2] * e[2]) * ile,
                               n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
         const R dth = theta - th0h;
         const R dE = B.bend_variant ? kbh * dth : kbh * sin(dth);
-        const R h1 = l1 / le, h2 = l2 / le;
-        const R tc = (ac[0] * e[0] + ac[1] * e[1] + ac[2] * e[2]) / le2;
-        const R td = (ad[0] * e[0] + ad[1] * e[1] + ad[2] * e[2]) / le2;
-        R c1, c2;  // dtheta/dx = c1 n1/h1 + c2 n2/h2
+        const R ile2 = ile * ile;
+        const R tc = (ac[0] * e[0] + ac[1] * e[1] + ac[2] * e[2]) * ile2;
+        const R td = (ad[0] * e[0] + ad[1] * e[1] + ad[2] * e[2]) * ile2;
+        R c1, c2;  // dtheta/dx = c1 n1/h1 + c2 n2/h2, h = |N|/|e|
         if (role == 0) {
             c1 = R(1) - tc;
             c2 = R(1) - td;
@@ -538,7 +541,8 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
             c1 = R(0);
             c2 = R(-1);
         }
-        for (int a = 0; a < 3; ++a) F[a] -= dE * (c1 * n1[a] / h1 + c2 * n2[a] / h2);
+        const R g1 = c1 * le * il1, g2 = c2 * le * il2;  // c / h
+        for (int a = 0; a < 3; ++a) F[a] -= dE * (g1 * n1[a] + g2 * n2[a]);
     }
     // element terms: volume penalty and hydrodynamic force, 1/3 per vertex
     R Al = R(0);

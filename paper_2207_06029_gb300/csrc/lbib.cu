@@ -59,8 +59,9 @@ struct Ctx {
     int *h_err = nullptr;
     double *scratch = nullptr;
     size_t scratch_bytes = 0;
-    cudaStream_t stream = nullptr, stream2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_far = nullptr, ev_near = nullptr;
+    cudaStream_t stream = nullptr;           // the caller's (or the library's) stream
+    cudaStream_t s_hi = nullptr, s_lo = nullptr;  // step streams: IB + box sweep (high priority), far field (low)
+    cudaEvent_t ev_fork = nullptr, ev_far = nullptr, ev_near = nullptr, ev_join = nullptr;
     bool split_sweep = true;
     bool own_stream = false;
     std::vector<DevBody> bodies;
@@ -417,10 +418,14 @@ int lbib_create(const lbib_params *p, void **out) {
         }
         c->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&c->s_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->s_lo, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_far, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_near, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_near, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         g_create_error = std::string("stream/event creation: ") + cudaGetErrorString(cudaGetLastError());
         lbib_destroy(c);
         return LBIB_ECUDA;
@@ -478,11 +483,13 @@ void lbib_destroy(void *h) {
     if (!h) return;
     Ctx *c = as_ctx(h);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->stream2) cudaStreamSynchronize(c->stream2);
+    for (cudaStream_t st : {c->s_hi, c->s_lo})
+        if (st) cudaStreamSynchronize(st);
     for (auto ev : c->events) cudaEventDestroy(ev);
-    for (cudaEvent_t ev : {c->ev_fork, c->ev_far, c->ev_near})
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_far, c->ev_near, c->ev_join})
         if (ev) cudaEventDestroy(ev);
-    if (c->stream2) cudaStreamDestroy(c->stream2);
+    for (cudaStream_t st : {c->s_hi, c->s_lo})
+        if (st) cudaStreamDestroy(st);
     dev_free_all(c);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -733,22 +740,24 @@ int lbib_step(void *h, int nsteps) {
     if (!c) return LBIB_EINVAL;
     if (c->err) return c->err;
     if (nsteps < 0) return fail(c, LBIB_EINVAL, "nsteps < 0");
-    // With one body, the nodes outside its support box do not depend on the
-    // IB work of the step: they are swept on a second stream concurrently
-    // with it, and the box is swept after the spreading.
+    if (nsteps == 0) return LBIB_OK;
+    // The steps run on two library streams forked from the caller's stream
+    // and joined back into it.  With one body, the nodes outside its
+    // support box do not depend on the IB work of the step: they are swept
+    // on the low-priority stream concurrently with the IB kernels (high
+    // priority, so the block scheduler serves them first), and the box is
+    // swept after the spreading.
     const bool split = c->bodies.size() == 1 && c->split_sweep;
-    if (split) {
-        cudaEventRecord(c->ev_fork, c->stream);
-        cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
-    }
+    cudaStream_t hi = c->s_hi, lo = c->s_lo;
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(hi, c->ev_fork, 0);
+    cudaStreamWaitEvent(lo, c->ev_fork, 0);
     for (int it = 0; it < nsteps; ++it) {
         if (++c->stamp_step == 0) {  // flag wrap-around: clear the tile flags
-            cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
+            cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, hi);
             c->stamp_step = 1;
-            if (split) {
-                cudaEventRecord(c->ev_fork, c->stream);
-                cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
-            }
+            cudaEventRecord(c->ev_near, hi);
+            cudaStreamWaitEvent(lo, c->ev_near, 0);
         }
         cudaEvent_t *ev = nullptr;
         if (c->profile) {
@@ -760,57 +769,57 @@ int lbib_step(void *h, int nsteps) {
                 }
             ev = &c->events[c->nev];
             c->nev += 6;
-            cudaEventRecord(ev[0], c->stream);
+            cudaEventRecord(ev[0], hi);
         }
         const bool store = c->fields_every == 0 ? (it == nsteps - 1)
                                                 : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
         void *fields = store ? c->fields : nullptr;
         const int *box = split ? c->bodies[0].bbox[c->bodies[0].bcur] : nullptr;
-        if (split) {  // far field on the second stream
-            if (ev) cudaEventRecord(ev[4], c->stream2);
+        if (split) {  // far field on the low-priority stream
+            if (ev) cudaEventRecord(ev[4], lo);
             cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L, fields, 1,
-                                         box, c->nsm, c->stream2);
+                                         box, c->nsm, lo);
             c->launches++;
             if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel (outside the body box)");
-            if (ev) cudaEventRecord(ev[5], c->stream2);
-            cudaEventRecord(c->ev_far, c->stream2);
+            if (ev) cudaEventRecord(ev[5], lo);
+            cudaEventRecord(c->ev_far, lo);
         }
         // IB front: support-region moments + MLS at markers and probes
         for (auto &b : c->bodies) {
             const BodyView v = make_view(c, b);
-            cudaError_t e = launch_ib_front(c->prec, c->fA, c->L, v, c->mom, c->nsm, c->d_err, c->stream);
+            cudaError_t e = launch_ib_front(c->prec, c->fA, c->L, v, c->mom, c->nsm, c->d_err, hi);
             c->launches += 2;
             if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernels");
         }
-        if (ev) cudaEventRecord(ev[1], c->stream);
+        if (ev) cudaEventRecord(ev[1], hi);
         // structure update and spreading
         for (auto &b : c->bodies) {
             const BodyView v = make_view(c, b);
             cudaError_t e;
             if (b.rigid) {
-                e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, c->stream);
+                e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, hi);
                 c->launches += 2;
             } else {
-                e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, c->stream);
+                e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, hi);
                 c->launches += 1;
             }
             if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
         }
-        if (ev) cudaEventRecord(ev[2], c->stream);
+        if (ev) cudaEventRecord(ev[2], hi);
         cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L, fields,
-                                     split ? 2 : 0, box, c->nsm, c->stream);
+                                     split ? 2 : 0, box, c->nsm, hi);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
-        if (ev) cudaEventRecord(ev[3], c->stream);
+        if (ev) cudaEventRecord(ev[3], hi);
         if (split) {
             // the next step reads what both sweeps wrote and overwrites what
             // this step's IB work and box sweep read
-            cudaStreamWaitEvent(c->stream, c->ev_far, 0);
-            cudaEventRecord(c->ev_near, c->stream);
-            cudaStreamWaitEvent(c->stream2, c->ev_near, 0);
+            cudaStreamWaitEvent(hi, c->ev_far, 0);
+            cudaEventRecord(c->ev_near, hi);
+            cudaStreamWaitEvent(lo, c->ev_near, 0);
         } else if (ev) {
-            cudaEventRecord(ev[4], c->stream);
-            cudaEventRecord(ev[5], c->stream);
+            cudaEventRecord(ev[4], hi);
+            cudaEventRecord(ev[5], hi);
         }
         std::swap(c->fA, c->fB);
         for (auto &b : c->bodies) {
@@ -819,6 +828,10 @@ int lbib_step(void *h, int nsteps) {
         }
         c->steps++;
     }
+    // join: everything the steps did is ordered before later work on the
+    // caller's stream (the low stream's work is already ordered into hi)
+    cudaEventRecord(c->ev_join, hi);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
     cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "error word copy");
     return LBIB_OK;
@@ -956,7 +969,8 @@ int lbib_get_profile(void *h, double *ms, long long *nsteps) {
     Ctx *c = as_ctx(h);
     if (!c || !ms) return LBIB_EINVAL;
     cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream2);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_hi);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_lo);
     if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (size_t k = 0; k + 6 <= c->nev; k += 6) {
