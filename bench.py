@@ -169,6 +169,7 @@ def run_gpu(args, rank, world):
     ncell = case.ncell
 
     lbib.lbib_step(h, args.warmup)
+    tuned = lbib.lbib_autotune(h, 10)  # launch configuration (untimed; advances the run)
     lbib.lbib_sync(h)
     lbib.lbib_set_output(h, -1)  # no macroscopic-field output inside the timed loop
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
@@ -196,6 +197,7 @@ def run_gpu(args, rank, world):
     # the sweep alone (no concurrent IB work): a short extra loop with the
     # overlap off, outside the timed region
     lbib.lbib_set_overlap(h, 0)
+    lbib.lbib_get_profile(h)
     for k in range(min(args.steps, 50)):
         flush.zero_()
         lbib.lbib_step(h, 1)
@@ -237,7 +239,7 @@ def run_gpu(args, rank, world):
     h2d = (rho0.nbytes + u0.nbytes + b.verts.nbytes + b.tris.nbytes) / e2e_steps
     d2h = 3 * Xh.numel() * 8 + (rho_h.numel() + u_h.numel()) * 8 / e2e_steps
     return {"ms": ms, "sweep_ms": sweep_ms, "mls_ms": mls_ms, "struct_ms": struct_ms, "nprof": nprof,
-            "step_ms": step_ms, "iso_sweep_us": 1e3 * iso_sweep_ms / max(iso_n, 1),
+            "step_ms": step_ms, "iso_sweep_us": 1e3 * iso_sweep_ms / max(iso_n, 1), "tuned": tuned,
             "launches": launches1 - launches0,
             "clocks": clk.summary(), "ncell": ncell, "e2e_s": e2e_s, "e2e_steps": e2e_steps, "h2d": h2d,
             "d2h": d2h, "nv": int(b.verts.shape[0]), "nt": int(b.tris.shape[0])}
@@ -338,6 +340,7 @@ def main():
         "config": {"workload": WORKLOADS[args.workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write)",
                    "fields_output": "off in the timed loop (e2e reads them)",
+                   "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2])},
                    "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(), "kernel": "k_sweep<float,float>",

@@ -159,6 +159,14 @@ int lbib_profile(void *ctx, int enable);
  * timed.  ms has 4 entries.  Synchronises and resets the accumulators. */
 int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
 
+/* Times the step in several launch configurations and keeps the fastest:
+ * the block shape of the whole-lattice sweep, then (single-body contexts)
+ * the overlap of the far-field sweep with the IB stage.  Each trial runs
+ * `steps` real time steps, so the simulation advances by a few times
+ * `steps`.  choice (optional, 3 ints) receives block x, block y (0, 0: whole
+ * x-rows) and the overlap flag. */
+int lbib_autotune(void *ctx, int steps, int *choice);
+
 /* With a single body, the sweep of the nodes outside the body's support
  * box runs on a second stream concurrently with the IB stage (default 1);
  * 0 runs one whole-lattice sweep after the IB stage.  Results are the same

@@ -462,12 +462,26 @@ __device__ __forceinline__ void spread_warp(const Lattice &L, const BodyView &B,
     }
 }
 
-// Grows component a of the node box of level n+1 by one marker position.
-__device__ __forceinline__ void box_add(int *box, int a, double x) {
-    const int c = (int)floor(x);
-    atomicMin(box + a, c - kBoxLo);
-    atomicMax(box + 3 + a, c + kBoxHi);
-}
+// Node box of level n+1: each block reduces its markers' cells in shared
+// memory and then updates the global box once (contention on the six
+// global words stays at one update per block).
+struct BlockBox {
+    int v[6];
+    __device__ void init() {
+        if (threadIdx.x < 6) v[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+    }
+    __device__ void add(int a, double x) {
+        const int c = (int)floor(x);
+        atomicMin(&v[a], c - kBoxLo);
+        atomicMax(&v[3 + a], c + kBoxHi);
+    }
+    __device__ void flush(int *box) {
+        if (threadIdx.x < 3)
+            atomicMin(box + threadIdx.x, v[threadIdx.x]);
+        else if (threadIdx.x < 6)
+            atomicMax(box + threadIdx.x, v[threadIdx.x]);
+    }
+};
 
 // Membrane vertex update, one warp per vertex: spring (Eq. strainFor),
 // bending (gradient of k_b[1 - cos(theta - theta0)], reading of Eq. bendFor),
@@ -481,12 +495,14 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
                                                   uint32_t *__restrict__ stamp, uint32_t step) {
     __shared__ R s_cv;
+    __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_cv = R(B.kv * (1.0 - (*B.vol_sum / 6.0) / B.V0));
+    sbox.init();
     __syncthreads();
     const R cv = s_cv;
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (v >= B.nv) return;
+    if (v < B.nv) {
     const R *Xr = (const R *)B.Xrel;
     R F[3] = {R(0), R(0), R(0)};
     for (int q = B.vh_ptr[v] + lane; q < B.vh_ptr[v + 1]; q += 32) {
@@ -573,12 +589,15 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
         ((R *)B.Xrel_next)[3 * v + a] = R(xn - B.origin[a]);
         B.Ub[3 * v + a] = Ub;
         B.Fl[3 * v + a] = Fla;
-        box_add(B.bbox_next, a, xn);
+        sbox.add(a, xn);
         fl = R(Fla);
     }
     const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
                      __shfl_sync(0xffffffffu, fl, 2)};
     spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
+    }
+    __syncthreads();
+    sbox.flush(B.bbox_next);
 }
 
 // Rigid body, one block: total force and moment of the element stresses,
@@ -696,9 +715,12 @@ __global__ void __launch_bounds__(1024) k_rigid_update(BodyView B) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
                                                        uint32_t *__restrict__ stamp, uint32_t step) {
+    __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (v >= B.nv) return;
+    sbox.init();
+    __syncthreads();
+    if (v < B.nv) {
     const double *S = B.rstate;
     R Al = R(0);
     for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32)
@@ -718,12 +740,15 @@ __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R 
         const double xn = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
         B.Xnew[3 * v + a] = xn;
         ((R *)B.Xrel_next)[3 * v + a] = R(xn - B.origin[a]);
-        box_add(B.bbox_next, a, xn);
+        sbox.add(a, xn);
         fl = R(Fla);
     }
     const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
                      __shfl_sync(0xffffffffu, fl, 2)};
     spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
+    }
+    __syncthreads();
+    sbox.flush(B.bbox_next);
 }
 
 // ---- launchers ----

@@ -993,6 +993,62 @@ int lbib_get_profile(void *h, double *ms, long long *nsteps) {
     return LBIB_OK;
 }
 
+int lbib_autotune(void *h, int steps, int *choice) {
+    Ctx *c = as_ctx(h);
+    if (!c || steps < 1) return LBIB_EINVAL;
+    if (c->err) return c->err;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "autotune events");
+    auto trial = [&](float *ms) -> int {
+        cudaEventRecord(e0, c->stream);
+        int rc = lbib_step(h, steps);
+        if (rc) return rc;
+        cudaEventRecord(e1, c->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune sync");
+        cudaEventElapsedTime(ms, e0, e1);
+        return check_device_error(c);
+    };
+    // sweep block shapes: whole x-rows (default), then fixed 2D shapes
+    const int shapes[][2] = {{0, 0}, {32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}};
+    const bool saved_split = c->split_sweep;
+    c->split_sweep = false;
+    float best = 1e30f;
+    int best_shape = 0, rc = 0;
+    for (int k = 0; k < (int)(sizeof(shapes) / sizeof(shapes[0])); ++k) {
+        if (shapes[k][0] > 0 && shapes[k][0] > (c->L.nx + 31) / 32 * 32) continue;
+        c->L.sweep_bx = shapes[k][0];
+        c->L.sweep_by = shapes[k][1];
+        float ms = 0.f;
+        if ((rc = trial(&ms))) break;
+        if (ms < best) {
+            best = ms;
+            best_shape = k;
+        }
+    }
+    c->L.sweep_bx = shapes[best_shape][0];
+    c->L.sweep_by = shapes[best_shape][1];
+    // overlap of the far-field sweep with the IB stage
+    int overlap = 0;
+    if (!rc && c->bodies.size() == 1) {
+        float ms = 0.f;
+        c->split_sweep = true;
+        if (!(rc = trial(&ms)) && ms < best) overlap = 1;
+    } else {
+        (void)saved_split;
+    }
+    c->split_sweep = overlap != 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (choice) {
+        choice[0] = c->L.sweep_bx;
+        choice[1] = c->L.sweep_by;
+        choice[2] = overlap;
+    }
+    return rc;
+}
+
 int lbib_set_overlap(void *h, int enable) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;

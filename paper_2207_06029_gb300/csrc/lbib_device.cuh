@@ -98,6 +98,7 @@ struct Lattice {
     double gext[3];
     double wall_u[6][3];
     double dist2_cut;       // largest |X - x_k|^2 whose MLS weight is non-zero
+    int sweep_bx, sweep_by; // block shape of the whole-lattice sweep (0: default)
     // derived, double and float copies
     double omega_d, cF_d, nu_d, gext_d[3], uw_d[27][3];
     float omega_f, cF_f, nu_f, gext_f[3], uw_f[27][3], dist2_cut_f;

@@ -348,6 +348,10 @@ static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
     int bx = (L.nx + 31) / 32 * 32;
     if (bx > 256) bx = 256;
     int by = 256 / bx;
+    if (L.sweep_bx > 0 && L.sweep_by > 0) {  // tuned shape
+        bx = L.sweep_bx;
+        by = L.sweep_by;
+    }
     if (by < 1) by = 1;
     if (by > L.ny) by = L.ny;
     block = dim3(bx, by, 1);

@@ -55,7 +55,8 @@ _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
-           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_device_bytes", "lbib_destroy",
+           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_autotune", "lbib_device_bytes",
+           "lbib_destroy",
            "lbib_last_error"]
 
 
@@ -85,6 +86,7 @@ def load():
         L.lbib_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
         L.lbib_set_output.argtypes = [vp, C.c_int]
         L.lbib_set_overlap.argtypes = [vp, C.c_int]
+        L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_destroy.argtypes = [vp]
         L.lbib_destroy.restype = None
@@ -191,6 +193,13 @@ def lbib_get_profile(ctx):
     n = C.c_longlong()
     _check(ctx, load().lbib_get_profile(ctx, ms, C.byref(n)))
     return ms[0], ms[1], ms[2], ms[3], n.value
+
+
+def lbib_autotune(ctx, steps):
+    """Returns (block_x, block_y, overlap) chosen; advances the run by several times `steps`."""
+    ch = (C.c_int * 3)()
+    _check(ctx, load().lbib_autotune(ctx, int(steps), ch))
+    return ch[0], ch[1], ch[2]
 
 
 def lbib_set_overlap(ctx, enable):

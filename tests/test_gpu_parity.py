@@ -209,6 +209,23 @@ def test_overlapped_and_serial_sweeps_agree(lbib):
     assert rel(out[0][1], out[1][1]) < 1e-14
 
 
+def test_autotuned_launch_configurations_keep_parity(lbib):
+    """Every block shape and overlap mode the autotuner tries computes the
+    same step: after tuning (which advances the run) the state still matches
+    the oracle advanced by the same number of steps."""
+    case = W.case_capsule_shear(n=26, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01,
+                                kv=1.0, precision=W.PREC_FP64)
+    ctx = lbib.Context.from_case(case)
+    choice = lbib.lbib_autotune(ctx.h, 3)
+    assert choice[2] in (0, 1)
+    ctx.step(4)
+    nsteps, _ = ctx.counters()
+    g = {"f": ctx.populations(), "fields": ctx.fields(), "markers": [ctx.markers(0)]}
+    ctx.close()
+    o = run_oracle(case, nsteps)
+    check_fp64(g, o)
+
+
 # ---------------------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------------------
