@@ -199,8 +199,13 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     const int nxy = L.nx * L.ny;
     const int n[3] = {L.nx, L.ny, L.nz};
 
+    // The lane-per-point phases (0 and 2) run FP64 code; FP64 issues per
+    // warp-instruction on one SM sub-partition, so blocks rotate the warp
+    // that runs them over the four sub-partitions.
+    const int w0 = blockIdx.x & 3, w2 = (blockIdx.x + 2) & 3;
+
     // ---------------- phase 0: one lane per point ----------------
-    if (warp == 0) {
+    if (warp == w0) {
         const int p = p0 + lane;
         sm.vol[lane] = 0.0;
         if (p < npts) {
@@ -274,8 +279,15 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
             int cw[3];
             for (int a = 0; a < 3; ++a) {
-                const int cc = sm.base[lp][a] + dd[a];
-                cw[a] = L.bc[a] == kPeriodic ? ((cc % n[a]) + n[a]) % n[a] : cc;
+                int cc = sm.base[lp][a] + dd[a];
+                if (L.bc[a] == kPeriodic) {
+                    if (cc < 0)
+                        cc += n[a];
+                    else if (cc >= n[a])
+                        cc -= n[a];
+                    if (cc < 0 || cc >= n[a]) cc = ((cc % n[a]) + n[a]) % n[a];
+                }
+                cw[a] = cc;
             }
             const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
             gu[j][1] = mom[st + node];
@@ -353,7 +365,7 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     __syncthreads();
 
     // ---------------- phase 2: one lane per point ----------------
-    if (warp == 0 && p0 + lane < npts) {
+    if (warp == w2 && p0 + lane < npts) {
         const int p = p0 + lane;
         const R *S = sm.sums[lane];
         double a[10], inv[16];
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     // (deterministic whichever block is last)
     __shared__ int s_last;
     if (!B.rigid) {
-        if (threadIdx.x == 32) {
+        if (threadIdx.x == 32 * ((w2 + 1) & 3)) {
             double s = 0.0;
             for (int k = 0; k < kPts; ++k) s += sm.vol[k];
             B.vol_part[blockIdx.x] = s;
@@ -462,6 +474,22 @@ __device__ __forceinline__ void spread_warp(const Lattice &L, const BodyView &B,
     }
 }
 
+// Lane k < 27 of a marker's warp adds w F to the force field at its
+// support node; the lanes of the 8 block corners flag their tiles.
+template <typename R>
+__device__ __forceinline__ void spread_node(const Lattice &L, int lane, int node, R w, const R *Fl,
+                                            R *__restrict__ force, uint32_t *stamp, uint32_t step) {
+    if (lane >= 27) return;
+    const long long st = L.stride;
+    atomicAdd(force + node, w * Fl[0]);
+    atomicAdd(force + st + node, w * Fl[1]);
+    atomicAdd(force + 2 * st + node, w * Fl[2]);
+    if (lane == 0 || lane == 2 || lane == 6 || lane == 8 || lane == 18 || lane == 20 || lane == 24 || lane == 26) {
+        const int x = node % L.nx, yz = node / L.nx, y = yz % L.ny, z = yz / L.ny;
+        stamp[(x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3))] = step;
+    }
+}
+
 // Node box of level n+1: each block reduces its markers' cells in shared
 // memory and then updates the global box once (contention on the six
 // global words stays at one update per block).
@@ -497,11 +525,18 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
     __shared__ R s_cv;
     __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_cv = R(B.kv * (1.0 - (*B.vol_sum / 6.0) / B.V0));
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // the spreading lanes fetch their node and weight first
+    int snode = 0;
+    R sphi = R(0);
+    if (v < B.nv && lane < 27) {
+        snode = B.node[27 * v + lane];
+        sphi = ((const R *)B.phi)[27 * v + lane];
+    }
+    if (threadIdx.x == 0) s_cv = R(B.kv * (1.0 - *B.vol_sum * B.inv_6V0));
     sbox.init();
     __syncthreads();
     const R cv = s_cv;
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (v < B.nv) {
     const R *Xr = (const R *)B.Xrel;
     R F[3] = {R(0), R(0), R(0)};
@@ -577,7 +612,7 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
     R fl = R(0);
     if (lane < 3) {
         const int a = lane;
-        const double acc = (double)(a == 0 ? F[0] : a == 1 ? F[1] : F[2]) / B.mv;
+        const double acc = (double)(a == 0 ? F[0] : a == 1 ? F[1] : F[2]) * B.inv_mv;
         const double U = B.U[3 * v + a];
         const double Ub = U + acc;
         const double Fla = Ub - U;
@@ -594,119 +629,183 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
     }
     const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
                      __shfl_sync(0xffffffffu, fl, 2)};
-    spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
+    spread_node<R>(L, lane, snode, Al * sphi, Fl, force, stamp, step);
     }
     __syncthreads();
     sbox.flush(B.bbox_next);
 }
 
-// Rigid body, one block: total force and moment of the element stresses,
-// gravity minus buoyancy, F = m du/dt and M = I dw/dt with I in the world
-// frame, second-order backward velocities (Eqs. linearVelRig,
-// angularVelRig), centre and orientation advanced with the new velocities.
+// Rigid body: total force and moment of the element stresses, gravity
+// minus buoyancy, F = m du/dt and M = I dw/dt with I in the world frame,
+// second-order backward velocities (Eqs. linearVelRig, angularVelRig),
+// centre and orientation advanced with the new velocities.
+// One thread per triangle sums force and moment (fixed-shape block
+// reduction, FP64 partial per block); the last block to finish reduces the
+// partials in block order and integrates with lanes 0..8 of one warp
+// working on the components side by side (FP64 issues per
+// warp-instruction, so the update is written across lanes).
 template <typename R>
-__global__ void __launch_bounds__(1024) k_rigid_update(BodyView B) {
-    __shared__ double red[6][32];
+__global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
+    __shared__ double red[6][8];
+    __shared__ int s_last;
+    __shared__ double sF[6], sR[9], sY[3], sQ[4];
     double *S = B.rstate;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const R xc[3] = {R(S[RigidState::XC] - B.origin[0]), R(S[RigidState::XC + 1] - B.origin[1]),
                      R(S[RigidState::XC + 2] - B.origin[2])};
-    R f[3] = {R(0), R(0), R(0)}, m[3] = {R(0), R(0), R(0)};
-    for (int t = threadIdx.x; t < B.nt; t += blockDim.x) {
+    R f[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < B.nt) {
         R Fh[3];
         tri_hydro<R>(B, t, Fh);
         const R *tg = (const R *)B.tri_geo + 8 * t;
         const R r[3] = {tg[4] - xc[0], tg[5] - xc[1], tg[6] - xc[2]};
-        f[0] += Fh[0];
-        f[1] += Fh[1];
-        f[2] += Fh[2];
-        m[0] += r[1] * Fh[2] - r[2] * Fh[1];
-        m[1] += r[2] * Fh[0] - r[0] * Fh[2];
-        m[2] += r[0] * Fh[1] - r[1] * Fh[0];
+        f[0] = Fh[0];
+        f[1] = Fh[1];
+        f[2] = Fh[2];
+        f[3] = r[1] * Fh[2] - r[2] * Fh[1];
+        f[4] = r[2] * Fh[0] - r[0] * Fh[2];
+        f[5] = r[0] * Fh[1] - r[1] * Fh[0];
     }
-    double acc6[6] = {(double)f[0], (double)f[1], (double)f[2], (double)m[0], (double)m[1], (double)m[2]};
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < 6; ++q) {
-        const double w = warp_sum(acc6[q]);
-        if (lane == 0) red[q][warp] = w;
+        const R w = warp_sum(f[q]);
+        if (lane == 0) red[q][warp] = (double)w;
     }
     __syncthreads();
-    if (warp != 0) return;
-    for (int q = 0; q < 6; ++q) acc6[q] = warp_sum(lane < (int)(blockDim.x >> 5) ? red[q][lane] : 0.0);
-    if (lane != 0) return;
-    double F[3], M[3];
-    for (int a = 0; a < 3; ++a) {
-        F[a] = acc6[a] + (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + a];
-        M[a] = acc6[3 + a];
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int w = 0; w < 8; ++w) acc += red[threadIdx.x][w];
+        B.vol_part[6 * blockIdx.x + threadIdx.x] = acc;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(B.vol_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || warp != 0) return;
+    __threadfence();
+    // totals: lane q < 6 sums partial q over the blocks in block order
+    if (lane < 6) {
+        double acc = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) acc += __ldcg(B.vol_part + 6 * b + lane);
+        if (lane < 3) acc += (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + lane];
+        sF[lane] = acc;
+    }
+    if (lane == 0) *B.vol_count = 0u;
+    __syncwarp();
     const double *q = S + RigidState::Q4;
-    const double *Ib = S + RigidState::IB;
-    double Rm[9];
-    {
+    // rotation matrix of q, entry lane < 9
+    if (lane < 9) {
         const double w = q[0], x = q[1], y = q[2], z = q[3];
-        Rm[0] = 1 - 2 * (y * y + z * z); Rm[1] = 2 * (x * y - w * z); Rm[2] = 2 * (x * z + w * y);
-        Rm[3] = 2 * (x * y + w * z); Rm[4] = 1 - 2 * (x * x + z * z); Rm[5] = 2 * (y * z - w * x);
-        Rm[6] = 2 * (x * z - w * y); Rm[7] = 2 * (y * z + w * x); Rm[8] = 1 - 2 * (x * x + y * y);
-    }
-    double T[9], Iw[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += Rm[3 * i + k] * Ib[3 * k + j];
-            T[3 * i + j] = acc;
+        const int i = lane / 3, j = lane % 3;
+        double v;
+        if (i == j) {
+            const double a2 = i == 0 ? y * y + z * z : i == 1 ? x * x + z * z : x * x + y * y;
+            v = 1.0 - 2.0 * a2;
+        } else {
+            // off-diagonal 2 (u_i u_j -+ w u_k), k the third axis
+            const double ui = i == 0 ? x : i == 1 ? y : z, uj = j == 0 ? x : j == 1 ? y : z;
+            const int k = 3 - i - j;
+            const double uk = k == 0 ? x : k == 1 ? y : z;
+            const bool plus = (i == 0 && j == 2) || (i == 1 && j == 0) || (i == 2 && j == 1);
+            v = 2.0 * (ui * uj + (plus ? w * uk : -w * uk));
         }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += T[3 * i + k] * Rm[3 * j + k];
-            Iw[3 * i + j] = acc;
+        sR[lane] = v;
+    }
+    __syncwarp();
+    // dw/dt = I_world^-1 M = R I_b^-1 R^T M, lanes 0..2
+    if (lane < 3) sY[lane] = sR[lane] * sF[3] + sR[3 + lane] * sF[4] + sR[6 + lane] * sF[5];  // R^T M
+    __syncwarp();
+    double zl = 0.0;
+    if (lane < 3) {
+        const double *Ii = S + RigidState::IBINV + 3 * lane;
+        zl = Ii[0] * sY[0] + Ii[1] * sY[1] + Ii[2] * sY[2];
+    }
+    __syncwarp();
+    if (lane < 3) sY[lane] = zl;
+    __syncwarp();
+    // lanes 0..2: linear velocity and centre; lanes 3..5: angular velocity
+    double vn = 0.0;
+    if (lane < 6) {
+        const int a = lane % 3;
+        double vdot, v1, v2;
+        if (lane < 3) {
+            vdot = sF[a] * S[RigidState::INVM];
+            v1 = S[RigidState::U + a];
+            v2 = S[RigidState::UP + a];
+        } else {
+            vdot = sR[3 * a] * sY[0] + sR[3 * a + 1] * sY[1] + sR[3 * a + 2] * sY[2];
+            v1 = S[RigidState::W + a];
+            v2 = S[RigidState::WP + a];
         }
-    const double det = Iw[0] * (Iw[4] * Iw[8] - Iw[5] * Iw[7]) - Iw[1] * (Iw[3] * Iw[8] - Iw[5] * Iw[6]) +
-                       Iw[2] * (Iw[3] * Iw[7] - Iw[4] * Iw[6]);
-    double Ii[9];
-    Ii[0] = (Iw[4] * Iw[8] - Iw[5] * Iw[7]) / det;
-    Ii[1] = (Iw[2] * Iw[7] - Iw[1] * Iw[8]) / det;
-    Ii[2] = (Iw[1] * Iw[5] - Iw[2] * Iw[4]) / det;
-    Ii[3] = (Iw[5] * Iw[6] - Iw[3] * Iw[8]) / det;
-    Ii[4] = (Iw[0] * Iw[8] - Iw[2] * Iw[6]) / det;
-    Ii[5] = (Iw[2] * Iw[3] - Iw[0] * Iw[5]) / det;
-    Ii[6] = (Iw[3] * Iw[7] - Iw[4] * Iw[6]) / det;
-    Ii[7] = (Iw[1] * Iw[6] - Iw[0] * Iw[7]) / det;
-    Ii[8] = (Iw[0] * Iw[4] - Iw[1] * Iw[3]) / det;
-    double un[3], wn[3];
-    for (int a = 0; a < 3; ++a) {
-        const double udot = F[a] / S[RigidState::MASS];
-        const double wdot = Ii[3 * a] * M[0] + Ii[3 * a + 1] * M[1] + Ii[3 * a + 2] * M[2];
-        un[a] = 2.0 / 3.0 * (2.0 * S[RigidState::U + a] - 0.5 * S[RigidState::UP + a] + udot);
-        wn[a] = 2.0 / 3.0 * (2.0 * S[RigidState::W + a] - 0.5 * S[RigidState::WP + a] + wdot);
+        vn = 2.0 / 3.0 * (2.0 * v1 - 0.5 * v2 + vdot);
     }
-    for (int a = 0; a < 3; ++a) {
-        const double x0 = S[RigidState::XC + a];
-        S[RigidState::XC_OLD + a] = x0;
-        S[RigidState::XC + a] = x0 + un[a];
-        S[RigidState::UP + a] = S[RigidState::U + a];
-        S[RigidState::U + a] = un[a];
-        S[RigidState::WP + a] = S[RigidState::W + a];
-        S[RigidState::W + a] = wn[a];
+    __syncwarp();
+    if (lane < 3) {
+        const double x0 = S[RigidState::XC + lane];
+        S[RigidState::XC_OLD + lane] = x0;
+        S[RigidState::XC + lane] = x0 + vn;
+        S[RigidState::UP + lane] = S[RigidState::U + lane];
+        S[RigidState::U + lane] = vn;
+    } else if (lane < 6) {
+        S[RigidState::WP + lane - 3] = S[RigidState::W + lane - 3];
+        S[RigidState::W + lane - 3] = vn;
     }
-    const double wl = sqrt(wn[0] * wn[0] + wn[1] * wn[1] + wn[2] * wn[2]);
-    double qn[4] = {q[0], q[1], q[2], q[3]};
-    if (wl > 0.0) {
-        const double c = cos(0.5 * wl), s = sin(0.5 * wl);
-        const double dq[4] = {c, s * wn[0] / wl, s * wn[1] / wl, s * wn[2] / wl};
-        qn[0] = dq[0] * q[0] - dq[1] * q[1] - dq[2] * q[2] - dq[3] * q[3];
-        qn[1] = dq[0] * q[1] + dq[1] * q[0] + dq[2] * q[3] - dq[3] * q[2];
-        qn[2] = dq[0] * q[2] - dq[1] * q[3] + dq[2] * q[0] + dq[3] * q[1];
-        qn[3] = dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0];
-        const double qq = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
-        for (int k = 0; k < 4; ++k) qn[k] /= qq;
+    // rotation by |w| about w: dq = (cos(|w|/2), sin(|w|/2) w/|w|)
+    const double w0 = __shfl_sync(0xffffffffu, vn, 3), w1 = __shfl_sync(0xffffffffu, vn, 4),
+                 w2 = __shfl_sync(0xffffffffu, vn, 5);
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double c, sth;  // cos(|w|/2) and sin(|w|/2)/|w|
+    if (th2 < 1e-6) {
+        // series in x^2 = |w|^2/4 (terms beyond x^8 are below double rounding)
+        const double x2 = 0.25 * th2;
+        c = 1.0 + x2 * (-0.5 + x2 * (1.0 / 24.0 + x2 * (-1.0 / 720.0 + x2 * (1.0 / 40320.0))));
+        sth = 0.5 * (1.0 + x2 * (-1.0 / 6.0 + x2 * (1.0 / 120.0 + x2 * (-1.0 / 5040.0))));
+    } else {
+        const double wl = sqrt(th2);
+        double sn;
+        sincos(0.5 * wl, &sn, &c);
+        sth = sn / wl;
     }
-    for (int k = 0; k < 4; ++k) S[RigidState::Q4 + k] = qn[k];
-    {
-        const double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
-        double *Rn = S + RigidState::ROT;
-        Rn[0] = 1 - 2 * (y * y + z * z); Rn[1] = 2 * (x * y - w * z); Rn[2] = 2 * (x * z + w * y);
-        Rn[3] = 2 * (x * y + w * z); Rn[4] = 1 - 2 * (x * x + z * z); Rn[5] = 2 * (y * z - w * x);
-        Rn[6] = 2 * (x * z - w * y); Rn[7] = 2 * (y * z + w * x); Rn[8] = 1 - 2 * (x * x + y * y);
+    const double dq[4] = {c, sth * w0, sth * w1, sth * w2};
+    double qn = q[0];
+    if (th2 > 0.0 && lane < 4) {
+        // component lane of dq (x) q
+        if (lane == 0) qn = dq[0] * q[0] - dq[1] * q[1] - dq[2] * q[2] - dq[3] * q[3];
+        if (lane == 1) qn = dq[0] * q[1] + dq[1] * q[0] + dq[2] * q[3] - dq[3] * q[2];
+        if (lane == 2) qn = dq[0] * q[2] - dq[1] * q[3] + dq[2] * q[0] + dq[3] * q[1];
+        if (lane == 3) qn = dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0];
+    } else if (lane < 4) {
+        qn = q[lane];
+    }
+    double qq = lane < 4 ? qn * qn : 0.0;
+    qq += __shfl_xor_sync(0xffffffffu, qq, 1);
+    qq += __shfl_xor_sync(0xffffffffu, qq, 2);
+    if (lane < 4) {
+        double r = (double)rsqrtf((float)qq);  // 1/sqrt(qq), refined twice
+        r = r * (1.5 - 0.5 * qq * r * r);
+        r = r * (1.5 - 0.5 * qq * r * r);
+        if (th2 > 0.0) qn *= r;
+        sQ[lane] = qn;
+        S[RigidState::Q4 + lane] = qn;
+    }
+    __syncwarp();
+    if (lane < 9) {
+        const double w = sQ[0], x = sQ[1], y = sQ[2], z = sQ[3];
+        const int i = lane / 3, j = lane % 3;
+        double v;
+        if (i == j) {
+            const double a2 = i == 0 ? y * y + z * z : i == 1 ? x * x + z * z : x * x + y * y;
+            v = 1.0 - 2.0 * a2;
+        } else {
+            const double ui = i == 0 ? x : i == 1 ? y : z, uj = j == 0 ? x : j == 1 ? y : z;
+            const int k = 3 - i - j;
+            const double uk = k == 0 ? x : k == 1 ? y : z;
+            const bool plus = (i == 0 && j == 2) || (i == 1 && j == 0) || (i == 2 && j == 1);
+            v = 2.0 * (ui * uj + (plus ? w * uk : -w * uk));
+        }
+        S[RigidState::ROT + lane] = v;
     }
 }
 
@@ -793,10 +892,11 @@ cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void 
 
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
                          uint32_t step, cudaStream_t s) {
+    const unsigned gf = (unsigned)((B.nt + 255) / 256);
     if (prec == 0)
-        k_rigid_update<double><<<1, 1024, 0, s>>>(B);
+        k_rigid_forces<double><<<gf, 256, 0, s>>>(B);
     else
-        k_rigid_update<float><<<1, 1024, 0, s>>>(B);
+        k_rigid_forces<float><<<gf, 256, 0, s>>>(B);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)((B.nv + 7) / 8);

@@ -265,6 +265,8 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.theta0 = b.theta0;
     v.V0 = b.V0;
     v.mv = b.mv;
+    v.inv_mv = 1.0 / b.mv;
+    v.inv_6V0 = 1.0 / (6.0 * b.V0);
     v.kv = b.p.kv;
     for (int a = 0; a < 3; ++a) v.origin[a] = b.origin[a];
     v.bend_variant = b.p.bend_variant;
@@ -684,7 +686,25 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         st[RigidState::Q4] = 1.0;
         st[RigidState::ROT] = st[RigidState::ROT + 4] = st[RigidState::ROT + 8] = 1.0;
         for (int k = 0; k < 9; ++k) st[RigidState::IB + k] = rs * I[k];
+        {
+            // body-frame inverse inertia (I_world^-1 = R I_b^-1 R^T)
+            const double *M = st.data() + RigidState::IB;
+            const double det = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                               M[2] * (M[3] * M[7] - M[4] * M[6]);
+            if (!(det > 0.0)) return fail(c, LBIB_EINVAL, "rigid body with a singular inertia tensor");
+            double *Mi = st.data() + RigidState::IBINV;
+            Mi[0] = (M[4] * M[8] - M[5] * M[7]) / det;
+            Mi[1] = (M[2] * M[7] - M[1] * M[8]) / det;
+            Mi[2] = (M[1] * M[5] - M[2] * M[4]) / det;
+            Mi[3] = (M[5] * M[6] - M[3] * M[8]) / det;
+            Mi[4] = (M[0] * M[8] - M[2] * M[6]) / det;
+            Mi[5] = (M[2] * M[3] - M[0] * M[5]) / det;
+            Mi[6] = (M[3] * M[7] - M[4] * M[6]) / det;
+            Mi[7] = (M[1] * M[6] - M[0] * M[7]) / det;
+            Mi[8] = (M[0] * M[4] - M[1] * M[3]) / det;
+        }
         st[RigidState::MASS] = rs * V;
+        st[RigidState::INVM] = 1.0 / (rs * V);
         st[RigidState::VOL] = V;
         st[RigidState::DENS] = rs;
         b.Xbody = upload(c, Xb, &rc);
@@ -706,7 +726,9 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         BodyView tmp{};
         tmp.nv = nv;
         tmp.nt = nt;
-        b.nvol_part = mls_blocks(tmp);
+        // partial sums: one per MLS block (membrane volume) or six per
+        // force block (rigid force and moment)
+        b.nvol_part = std::max(mls_blocks(tmp), 6 * ((nt + 255) / 256));
         b.vol_part = upload(c, std::vector<double>((size_t)b.nvol_part, 0.0), &rc);
         b.vol_sum = upload(c, std::vector<double>(1, 6.0 * V0), &rc);
         b.vol_count = upload(c, std::vector<unsigned int>(1, 0u), &rc);

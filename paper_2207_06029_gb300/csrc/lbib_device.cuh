@@ -141,6 +141,7 @@ struct BodyView {
     const int4 *hinge;      // (a, b, c, d)
     const void *ks, *l0, *kb, *theta0;  // R per hinge
     double V0, mv, kv;
+    double inv_mv, inv_6V0; // 1/m_v, 1/(6 V0)
     double origin[3];       // reference point of relative positions and of the volume sum
     int bend_variant;
     // rigid body
@@ -159,7 +160,7 @@ struct BodyView {
 struct RigidState {
     enum {
         XC = 0, Q4 = 3, U = 7, UP = 10, W = 13, WP = 16, XC_OLD = 19, ROT = 22, IB = 31, MASS = 40,
-        VOL = 41, DENS = 42, GRAV = 43, SIZE = 46
+        VOL = 41, DENS = 42, GRAV = 43, IBINV = 46, INVM = 55, SIZE = 56
     };
 };
 
