@@ -169,7 +169,13 @@ def run_gpu(args, rank, world):
     ncell = case.ncell
 
     lbib.lbib_step(h, args.warmup)
-    tuned = lbib.lbib_autotune(h, 10)  # launch configuration (untimed; advances the run)
+    if args.autotune:
+        tuned = lbib.lbib_autotune(h, 10)  # launch configuration (untimed; advances the run)
+    else:
+        tuned = (0, 0, 1)
+    if args.overlap != "auto":
+        lbib.lbib_set_overlap(h, 1 if args.overlap == "on" else 0)
+        tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0)
     lbib.lbib_sync(h)
     lbib.lbib_set_output(h, -1)  # no macroscopic-field output inside the timed loop
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
@@ -274,6 +280,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="capsule96", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch configuration")
+    ap.add_argument("--overlap", default="auto", choices=["auto", "on", "off"],
+                    help="far-field sweep concurrent with the IB stage (auto: as tuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
