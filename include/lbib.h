@@ -173,6 +173,13 @@ int lbib_autotune(void *ctx, int steps, int *choice);
  * either way. */
 int lbib_set_overlap(void *ctx, int enable);
 
+/* Steps that do not store the fields run as CUDA graphs captured on first
+ * use (one per phase of the six-step rotation of the population, position
+ * and support-box buffers) and launched into the context stream (enable = 1,
+ * default); 0 enqueues every kernel of every step.  Results are identical.
+ * Adding a body, changing the overlap or autotuning recaptures. */
+int lbib_set_graphs(void *ctx, int enable);
+
 /* When the sweep also writes the macroscopic fields read by
  * lbib_get_fields: fields_every = 0 (default) on the last step of each
  * lbib_step call, k > 0 on every k-th step, < 0 never (lbib_get_fields then

@@ -39,7 +39,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Lattice L, const int *__restrict__ box,
-                                                 int *__restrict__ box_next, R *__restrict__ mom) {
+                                                 int *__restrict__ box_next, R *__restrict__ mom,
+                                                 uint32_t *__restrict__ step_inc) {
+    if (step_inc && blockIdx.x == 0 && threadIdx.x == 0) *step_inc += 1u;  // read by the later kernels of the step
     const int n[3] = {L.nx, L.ny, L.nz};
     int lo[3], ext[3];
     for (int a = 0; a < 3; ++a) {
@@ -521,7 +523,8 @@ struct BlockBox {
 // c_l = A_l (Eq. bodyforce).
 template <typename R>
 __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
-                                                  uint32_t *__restrict__ stamp, uint32_t step) {
+                                                  uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
+    const uint32_t step = *dstep;
     __shared__ R s_cv;
     __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
@@ -813,7 +816,8 @@ __global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
 // level n, IB force and spreading, then the markers of level n+1.
 template <typename R>
 __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
-                                                       uint32_t *__restrict__ stamp, uint32_t step) {
+                                                       uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
+    const uint32_t step = *dstep;
     __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -855,33 +859,37 @@ int mls_blocks(const BodyView &B) { return (B.nv + 2 * B.nt + kPts - 1) / kPts; 
 
 template <typename S, typename R>
 static cudaError_t ib_front_t(const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm, int *err,
-                              cudaStream_t s) {
-    k_moments<S, R><<<2 * nsm, 256, 0, s>>>((const S *)fin, L, B.bbox, B.bbox_next, (R *)mom);
+                              uint32_t *step_inc, cudaStream_t s) {
+    k_moments<S, R><<<2 * nsm, 256, 0, s>>>((const S *)fin, L, B.bbox, B.bbox_next, (R *)mom, step_inc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(MlsSmem<R>);
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_mls<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    k_mls<R><<<mls_blocks(B), kMlsThreads, smem, s>>>((const R *)mom, L, B, err);
+    k_mls<R><<<mls_blocks(B), kMlsThreads, sizeof(MlsSmem<R>), s>>>((const R *)mom, L, B, err);
     return cudaGetLastError();
 }
 
+// Kernel attributes that must be set before the first launch (and before
+// any stream capture): the MLS kernel's dynamic shared memory.
+cudaError_t prepare_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_mls<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(MlsSmem<float>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mls<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(MlsSmem<double>));
+    return e;
+}
+
 cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm,
-                            int *err, cudaStream_t s) {
+                            int *err, uint32_t *step_inc, cudaStream_t s) {
     switch (prec) {
-        case 0: return ib_front_t<double, double>(fin, L, B, mom, nsm, err, s);
-        case 1: return ib_front_t<float, float>(fin, L, B, mom, nsm, err, s);
-        case 2: return ib_front_t<__half, float>(fin, L, B, mom, nsm, err, s);
-        default: return ib_front_t<__nv_bfloat16, float>(fin, L, B, mom, nsm, err, s);
+        case 0: return ib_front_t<double, double>(fin, L, B, mom, nsm, err, step_inc, s);
+        case 1: return ib_front_t<float, float>(fin, L, B, mom, nsm, err, step_inc, s);
+        case 2: return ib_front_t<__half, float>(fin, L, B, mom, nsm, err, step_inc, s);
+        default: return ib_front_t<__nv_bfloat16, float>(fin, L, B, mom, nsm, err, step_inc, s);
     }
 }
 
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                            uint32_t step, cudaStream_t s) {
+                            const uint32_t *step, cudaStream_t s) {
     const unsigned g = (unsigned)((B.nv + 7) / 8);  // 8 warps (vertices) per block
     if (prec == 0)
         k_membrane<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
@@ -891,7 +899,7 @@ cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void 
 }
 
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                         uint32_t step, cudaStream_t s) {
+                         const uint32_t *step, cudaStream_t s) {
     const unsigned gf = (unsigned)((B.nt + 255) / 256);
     if (prec == 0)
         k_rigid_forces<double><<<gf, 256, 0, s>>>(B);

@@ -65,7 +65,17 @@ struct Ctx {
     bool split_sweep = true;
     bool own_stream = false;
     std::vector<DevBody> bodies;
-    uint32_t stamp_step = 0;
+    uint32_t *d_step = nullptr;  // device step counter (tile flags of the IB force)
+    uint32_t step_host = 0;      // host mirror of *d_step
+    // CUDA graphs of one step, one per phase of the buffer rotation (period 6)
+    cudaStream_t s_cap = nullptr;
+    cudaGraphExec_t gexec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool graphs_valid = false, use_graphs = true;
+    long long graph_origin = 0;
+    cudaEvent_t gev[6][6] = {};  // timing events recorded by the graphs
+    bool gev_pending[6] = {false, false, false, false, false, false};
+    double prof_acc[4] = {0.0, 0.0, 0.0, 0.0};
+    long long prof_n = 0;
     long long steps = 0, launches = 0;
     int err = 0;
     std::string msg;
@@ -165,6 +175,8 @@ double mls_dist2_cut() {
 }
 
 Ctx *as_ctx(void *h) { return static_cast<Ctx *>(h); }
+
+void invalidate_graphs(Ctx *c);
 
 // ---- host geometry (FP64) ----
 inline void v_sub(const double *a, const double *b, double *o) {
@@ -448,7 +460,8 @@ int lbib_create(const lbib_params *p, void **out) {
     }
     c->stamp = (uint32_t *)dev_alloc(c, sizeof(uint32_t) * (size_t)c->ntiles);
     c->d_err = (int *)dev_alloc(c, sizeof(int));
-    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err) {
+    c->d_step = (uint32_t *)dev_alloc(c, sizeof(uint32_t));
+    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step) {
         g_create_error = "device allocation failed";
         lbib_destroy(c);
         return LBIB_ENOMEM;
@@ -464,6 +477,11 @@ int lbib_create(const lbib_params *p, void **out) {
     e = cudaMemsetAsync(c->force, 0, 3 * (size_t)L.stride * c->relem, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = prepare_kernels();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        for (int j = 0; j < 6 && e == cudaSuccess; ++j) e = cudaEventCreate(&c->gev[k][j]);
     if (e != cudaSuccess) {
         g_create_error = std::string("cudaMemset: ") + cudaGetErrorString(e);
         lbib_destroy(c);
@@ -488,6 +506,12 @@ void lbib_destroy(void *h) {
     for (cudaStream_t st : {c->s_hi, c->s_lo})
         if (st) cudaStreamSynchronize(st);
     for (auto ev : c->events) cudaEventDestroy(ev);
+    for (int k = 0; k < 6; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        for (int j = 0; j < 6; ++j)
+            if (c->gev[k][j]) cudaEventDestroy(c->gev[k][j]);
+    }
+    if (c->s_cap) cudaStreamDestroy(c->s_cap);
     for (cudaEvent_t ev : {c->ev_fork, c->ev_far, c->ev_near, c->ev_join})
         if (ev) cudaEventDestroy(ev);
     for (cudaStream_t st : {c->s_hi, c->s_lo})
@@ -752,10 +776,163 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);  // host vectors are released on return
     if (e != cudaSuccess) return cuda_fail(c, e, "add_body upload");
+    invalidate_graphs(c);
     c->bodies.push_back(b);
     if (body_id) *body_id = (int)c->bodies.size() - 1;
     return LBIB_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Enqueues one step on the two step streams (the caller forks them from,
+// and joins them into, an origin stream).  With one body, the nodes
+// outside its support box do not depend on the IB work of the step: they
+// are swept on the low-priority stream concurrently with the IB kernels
+// (high priority, so the block scheduler serves them first), and the box is
+// swept after the spreading.  ev (6 events or nullptr) receives the stage
+// timestamps; `external` records them as graph nodes during capture.
+// Advances the host-side buffer rotation but not the step count.
+int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external) {
+    const bool split = c->bodies.size() == 1 && c->split_sweep;
+    cudaStream_t hi = c->s_hi, lo = c->s_lo;
+    auto rec = [&](int k, cudaStream_t st) {
+        if (ev) cudaEventRecordWithFlags(ev[k], st, external ? cudaEventRecordExternal : cudaEventRecordDefault);
+    };
+    rec(0, hi);
+    void *fields = store_fields ? c->fields : nullptr;
+    const int *box = split ? c->bodies[0].bbox[c->bodies[0].bcur] : nullptr;
+    uint32_t *stamp = c->bodies.empty() ? nullptr : c->stamp;
+    if (split) {  // far field on the low-priority stream; it never carries IB force
+        rec(4, lo);
+        cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, nullptr, c->d_step, c->L, fields, 1, box,
+                                     c->nsm, lo);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel (outside the body box)");
+        rec(5, lo);
+        cudaEventRecord(c->ev_far, lo);
+    }
+    // IB front: support-region moments + MLS at markers and probes
+    for (size_t k = 0; k < c->bodies.size(); ++k) {
+        const BodyView v = make_view(c, c->bodies[k]);
+        cudaError_t e = launch_ib_front(c->prec, c->fA, c->L, v, c->mom, c->nsm, c->d_err,
+                                        k == 0 ? c->d_step : nullptr, hi);
+        c->launches += 2;
+        if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernels");
+    }
+    rec(1, hi);
+    // structure update and spreading
+    for (auto &b : c->bodies) {
+        const BodyView v = make_view(c, b);
+        cudaError_t e;
+        if (b.rigid) {
+            e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->d_step, hi);
+            c->launches += 2;
+        } else {
+            e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->d_step, hi);
+            c->launches += 1;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
+    }
+    rec(2, hi);
+    cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, stamp, c->d_step, c->L, fields, split ? 2 : 0,
+                                 box, c->nsm, hi);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
+    rec(3, hi);
+    if (split) {
+        // the next step reads what both sweeps wrote and overwrites what
+        // this step's IB work and box sweep read
+        cudaStreamWaitEvent(hi, c->ev_far, 0);
+        cudaEventRecord(c->ev_near, hi);
+        cudaStreamWaitEvent(lo, c->ev_near, 0);
+    } else {
+        rec(4, hi);
+        rec(5, hi);
+    }
+    std::swap(c->fA, c->fB);
+    for (auto &b : c->bodies) {
+        b.cur = (b.cur + 1) % 3;
+        b.bcur ^= 1;
+    }
+    return LBIB_OK;
+}
+
+// Adds the stage times of one step's six events.
+void accumulate_profile(Ctx *c, const cudaEvent_t *ev) {
+    float t01 = 0.f, t12 = 0.f, t23 = 0.f, t45 = 0.f, t03 = 0.f, t05 = 0.f;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    cudaEventElapsedTime(&t45, ev[4], ev[5]);
+    cudaEventElapsedTime(&t03, ev[0], ev[3]);
+    cudaEventElapsedTime(&t05, ev[0], ev[5]);
+    c->prof_acc[0] += t01;
+    c->prof_acc[1] += t12;
+    c->prof_acc[2] += t23 + t45;
+    c->prof_acc[3] += t03 > t05 ? t03 : t05;
+    c->prof_n++;
+}
+
+void harvest_graph_events(Ctx *c, int k) {
+    if (!c->gev_pending[k]) return;
+    cudaEventSynchronize(c->gev[k][3]);
+    cudaEventSynchronize(c->gev[k][5]);
+    accumulate_profile(c, c->gev[k]);
+    c->gev_pending[k] = false;
+}
+
+void invalidate_graphs(Ctx *c) {
+    for (int k = 0; k < 6; ++k) {
+        harvest_graph_events(c, k);
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        c->gexec[k] = nullptr;
+    }
+    c->graphs_valid = false;
+}
+
+// Captures one step per phase of the buffer rotation (six steps return the
+// rotation to where it started) as CUDA graphs on the capture stream.
+int build_graphs(Ctx *c) {
+    invalidate_graphs(c);
+    for (int k = 0; k < 6; ++k) {
+        cudaError_t e = cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+        cudaEventRecord(c->ev_fork, c->s_cap);
+        cudaStreamWaitEvent(c->s_hi, c->ev_fork, 0);
+        cudaStreamWaitEvent(c->s_lo, c->ev_fork, 0);
+        const long long launches = c->launches;
+        int rc = enqueue_step(c, false, c->gev[k], true);
+        c->launches = launches;
+        cudaEventRecord(c->ev_join, c->s_hi);
+        cudaStreamWaitEvent(c->s_cap, c->ev_join, 0);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->s_cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
+        e = cudaGraphInstantiate(&c->gexec[k], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    }
+    c->graph_origin = c->steps;
+    c->graphs_valid = true;
+    return LBIB_OK;
+}
+
+// launches per step (for the counters when a graph runs the step)
+long long launches_per_step(const Ctx *c) {
+    long long n = 1 + (c->bodies.size() == 1 && c->split_sweep ? 1 : 0);
+    for (auto &b : c->bodies) n += 2 + (b.rigid ? 2 : 1);
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
 
 int lbib_step(void *h, int nsteps) {
     Ctx *c = as_ctx(h);
@@ -763,97 +940,55 @@ int lbib_step(void *h, int nsteps) {
     if (c->err) return c->err;
     if (nsteps < 0) return fail(c, LBIB_EINVAL, "nsteps < 0");
     if (nsteps == 0) return LBIB_OK;
-    // The steps run on two library streams forked from the caller's stream
-    // and joined back into it.  With one body, the nodes outside its
-    // support box do not depend on the IB work of the step: they are swept
-    // on the low-priority stream concurrently with the IB kernels (high
-    // priority, so the block scheduler serves them first), and the box is
-    // swept after the spreading.
-    const bool split = c->bodies.size() == 1 && c->split_sweep;
-    cudaStream_t hi = c->s_hi, lo = c->s_lo;
-    cudaEventRecord(c->ev_fork, c->stream);
-    cudaStreamWaitEvent(hi, c->ev_fork, 0);
-    cudaStreamWaitEvent(lo, c->ev_fork, 0);
     for (int it = 0; it < nsteps; ++it) {
-        if (++c->stamp_step == 0) {  // flag wrap-around: clear the tile flags
-            cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, hi);
-            c->stamp_step = 1;
-            cudaEventRecord(c->ev_near, hi);
-            cudaStreamWaitEvent(lo, c->ev_near, 0);
-        }
-        cudaEvent_t *ev = nullptr;
-        if (c->profile) {
-            if (c->nev + 6 > c->events.size())
-                for (int k = 0; k < 6; ++k) {
-                    cudaEvent_t x;
-                    if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
-                    c->events.push_back(x);
-                }
-            ev = &c->events[c->nev];
-            c->nev += 6;
-            cudaEventRecord(ev[0], hi);
+        if (!c->bodies.empty() && ++c->step_host == 0xFFFFFFFFu) {
+            // before the counter wraps: clear the tile flags and restart it
+            cudaError_t e = cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "step counter reset");
+            c->step_host = 1;
         }
         const bool store = c->fields_every == 0 ? (it == nsteps - 1)
                                                 : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
-        void *fields = store ? c->fields : nullptr;
-        const int *box = split ? c->bodies[0].bbox[c->bodies[0].bcur] : nullptr;
-        if (split) {  // far field on the low-priority stream
-            if (ev) cudaEventRecord(ev[4], lo);
-            cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L, fields, 1,
-                                         box, c->nsm, lo);
-            c->launches++;
-            if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel (outside the body box)");
-            if (ev) cudaEventRecord(ev[5], lo);
-            cudaEventRecord(c->ev_far, lo);
-        }
-        // IB front: support-region moments + MLS at markers and probes
-        for (auto &b : c->bodies) {
-            const BodyView v = make_view(c, b);
-            cudaError_t e = launch_ib_front(c->prec, c->fA, c->L, v, c->mom, c->nsm, c->d_err, hi);
-            c->launches += 2;
-            if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernels");
-        }
-        if (ev) cudaEventRecord(ev[1], hi);
-        // structure update and spreading
-        for (auto &b : c->bodies) {
-            const BodyView v = make_view(c, b);
-            cudaError_t e;
-            if (b.rigid) {
-                e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, hi);
-                c->launches += 2;
-            } else {
-                e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->stamp_step, hi);
-                c->launches += 1;
+        if (c->use_graphs && !store) {
+            if (!c->graphs_valid) {
+                int rc = build_graphs(c);
+                if (rc) return rc;
             }
-            if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
-        }
-        if (ev) cudaEventRecord(ev[2], hi);
-        cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, c->stamp, c->stamp_step, c->L, fields,
-                                     split ? 2 : 0, box, c->nsm, hi);
-        c->launches++;
-        if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
-        if (ev) cudaEventRecord(ev[3], hi);
-        if (split) {
-            // the next step reads what both sweeps wrote and overwrites what
-            // this step's IB work and box sweep read
-            cudaStreamWaitEvent(hi, c->ev_far, 0);
-            cudaEventRecord(c->ev_near, hi);
-            cudaStreamWaitEvent(lo, c->ev_near, 0);
-        } else if (ev) {
-            cudaEventRecord(ev[4], hi);
-            cudaEventRecord(ev[5], hi);
-        }
-        std::swap(c->fA, c->fB);
-        for (auto &b : c->bodies) {
-            b.cur = (b.cur + 1) % 3;
-            b.bcur ^= 1;
+            const int k = (int)(((c->steps - c->graph_origin) % 6 + 6) % 6);
+            harvest_graph_events(c, k);
+            cudaError_t e = cudaGraphLaunch(c->gexec[k], c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+            if (c->profile) c->gev_pending[k] = true;
+            // the graph performs the buffer rotation of its step: mirror it
+            std::swap(c->fA, c->fB);
+            for (auto &b : c->bodies) {
+                b.cur = (b.cur + 1) % 3;
+                b.bcur ^= 1;
+            }
+            c->launches += launches_per_step(c);
+        } else {
+            cudaEvent_t *ev = nullptr;
+            if (c->profile) {
+                if (c->nev + 6 > c->events.size())
+                    for (int k = 0; k < 6; ++k) {
+                        cudaEvent_t x;
+                        if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
+                        c->events.push_back(x);
+                    }
+                ev = &c->events[c->nev];
+                c->nev += 6;
+            }
+            cudaEventRecord(c->ev_fork, c->stream);
+            cudaStreamWaitEvent(c->s_hi, c->ev_fork, 0);
+            cudaStreamWaitEvent(c->s_lo, c->ev_fork, 0);
+            int rc = enqueue_step(c, store, ev, false);
+            if (rc) return rc;
+            cudaEventRecord(c->ev_join, c->s_hi);
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
         }
         c->steps++;
     }
-    // join: everything the steps did is ordered before later work on the
-    // caller's stream (the low stream's work is already ordered into hi)
-    cudaEventRecord(c->ev_join, hi);
-    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
     cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "error word copy");
     return LBIB_OK;
@@ -983,6 +1118,8 @@ int lbib_counters(void *h, long long *steps, long long *launches) {
 int lbib_profile(void *h, int enable) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;
+    if (!enable)
+        for (int k = 0; k < 6; ++k) c->gev_pending[k] = false;
     c->profile = enable != 0;
     return LBIB_OK;
 }
@@ -994,24 +1131,20 @@ int lbib_get_profile(void *h, double *ms, long long *nsteps) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_hi);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_lo);
     if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (size_t k = 0; k + 6 <= c->nev; k += 6) {
-        const cudaEvent_t *ev = &c->events[k];
-        float t01 = 0.f, t12 = 0.f, t23 = 0.f, t45 = 0.f, t03 = 0.f, t05 = 0.f;
-        cudaEventElapsedTime(&t01, ev[0], ev[1]);
-        cudaEventElapsedTime(&t12, ev[1], ev[2]);
-        cudaEventElapsedTime(&t23, ev[2], ev[3]);
-        cudaEventElapsedTime(&t45, ev[4], ev[5]);
-        cudaEventElapsedTime(&t03, ev[0], ev[3]);
-        cudaEventElapsedTime(&t05, ev[0], ev[5]);
-        acc[0] += t01;
-        acc[1] += t12;
-        acc[2] += t23 + t45;
-        acc[3] += t03 > t05 ? t03 : t05;
-    }
-    for (int j = 0; j < 4; ++j) ms[j] = acc[j];
-    if (nsteps) *nsteps = (long long)(c->nev / 6);
+    for (size_t k = 0; k + 6 <= c->nev; k += 6) accumulate_profile(c, &c->events[k]);
+    for (int k = 0; k < 6; ++k) harvest_graph_events(c, k);
+    for (int j = 0; j < 4; ++j) ms[j] = c->prof_acc[j];
+    if (nsteps) *nsteps = c->prof_n;
     c->nev = 0;
+    for (int j = 0; j < 4; ++j) c->prof_acc[j] = 0.0;
+    c->prof_n = 0;
+    return LBIB_OK;
+}
+
+int lbib_set_graphs(void *h, int enable) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    c->use_graphs = enable != 0;
     return LBIB_OK;
 }
 
@@ -1042,6 +1175,7 @@ int lbib_autotune(void *h, int steps, int *choice) {
         if (shapes[k][0] > 0 && shapes[k][0] > (c->L.nx + 31) / 32 * 32) continue;
         c->L.sweep_bx = shapes[k][0];
         c->L.sweep_by = shapes[k][1];
+        invalidate_graphs(c);
         float ms = 0.f;
         if ((rc = trial(&ms))) break;
         if (ms < best) {
@@ -1051,16 +1185,19 @@ int lbib_autotune(void *h, int steps, int *choice) {
     }
     c->L.sweep_bx = shapes[best_shape][0];
     c->L.sweep_by = shapes[best_shape][1];
+    invalidate_graphs(c);
     // overlap of the far-field sweep with the IB stage
     int overlap = 0;
     if (!rc && c->bodies.size() == 1) {
         float ms = 0.f;
         c->split_sweep = true;
+        invalidate_graphs(c);
         if (!(rc = trial(&ms)) && ms < best) overlap = 1;
     } else {
         (void)saved_split;
     }
     c->split_sweep = overlap != 0;
+    invalidate_graphs(c);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (choice) {
@@ -1074,6 +1211,7 @@ int lbib_autotune(void *h, int steps, int *choice) {
 int lbib_set_overlap(void *h, int enable) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;
+    if (c->split_sweep != (enable != 0)) invalidate_graphs(c);
     c->split_sweep = enable != 0;
     return LBIB_OK;
 }

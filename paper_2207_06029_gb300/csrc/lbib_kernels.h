@@ -10,8 +10,9 @@ namespace lbib {
 
 // sweep.cu
 // part: 0 the whole lattice, 1 the nodes outside box, 2 the nodes inside box
+// stamp == nullptr: no IB force is read; step points to the device step counter
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
-                         uint32_t step, const Lattice &L, void *fields, int part, const int *box, int nsm,
+                         const uint32_t *step, const Lattice &L, void *fields, int part, const int *box, int nsm,
                          cudaStream_t s);
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
                                     void *fields, cudaStream_t s);
@@ -22,11 +23,14 @@ cudaError_t launch_fields_out(int prec, const void *fields, const Lattice &L, do
 
 // ib.cu
 int mls_blocks(const BodyView &B);
+cudaError_t prepare_kernels();
+// step_inc: device step counter incremented at the start of the step (first
+// body only), or nullptr
 cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm,
-                            int *err, cudaStream_t s);
+                            int *err, uint32_t *step_inc, cudaStream_t s);
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                            uint32_t step, cudaStream_t s);
+                            const uint32_t *step, cudaStream_t s);
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                         uint32_t step, cudaStream_t s);
+                         const uint32_t *step, cudaStream_t s);
 
 }  // namespace lbib

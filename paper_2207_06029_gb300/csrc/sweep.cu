@@ -174,7 +174,7 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
         F2 = pick<R>(L.gext_d[2], L.gext_f[2]);
     }
     const int tile = (x >> 3) + L.ntx * ((y >> 3) + L.nty * (z >> 3));
-    if (__ldg(stamp + tile) == step) {
+    if (stamp && __ldg(stamp + tile) == step) {
         const R fx = force[idx], fy = force[st + idx], fz = force[2 * st + idx];
         force[idx] = R(0);
         force[st + idx] = R(0);
@@ -255,8 +255,9 @@ __device__ __forceinline__ bool in_box(const Lattice &L, const int *lo, const in
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
                                                R *__restrict__ force, const uint32_t *__restrict__ stamp,
-                                               uint32_t step, Lattice L, R *__restrict__ fields,
-                                               const int *__restrict__ box) {
+                                               const uint32_t *__restrict__ dstep, Lattice L,
+                                               R *__restrict__ fields, const int *__restrict__ box) {
+    const uint32_t step = stamp ? *dstep : 0u;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -273,8 +274,9 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S *__restrict__ fout,
                                                    R *__restrict__ force, const uint32_t *__restrict__ stamp,
-                                                   uint32_t step, Lattice L, R *__restrict__ fields,
-                                                   const int *__restrict__ box) {
+                                                   const uint32_t *__restrict__ dstep, Lattice L,
+                                                   R *__restrict__ fields, const int *__restrict__ box) {
+    const uint32_t step = stamp ? *dstep : 0u;
     int lo[3], ext[3];
     clamp_box(L, box, lo, ext);
     const int total = ext[0] * ext[1] * ext[2];
@@ -360,7 +362,7 @@ static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
 
 // part: 0 whole lattice, 1 outside the box, 2 inside the box
 template <typename S, typename R>
-static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, uint32_t step,
+static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, const uint32_t *step,
                            const Lattice &L, void *fields, int part, const int *box, int nsm, cudaStream_t s) {
     if (part == 2) {
         k_sweep_box<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
@@ -375,7 +377,7 @@ static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint3
 }
 
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
-                         uint32_t step, const Lattice &L, void *fields, int part, const int *box, int nsm,
+                         const uint32_t *step, const Lattice &L, void *fields, int part, const int *box, int nsm,
                          cudaStream_t s) {
     switch (prec) {
         case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);

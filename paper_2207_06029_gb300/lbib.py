@@ -55,7 +55,8 @@ _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
-           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_autotune", "lbib_device_bytes",
+           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_autotune",
+           "lbib_device_bytes",
            "lbib_destroy",
            "lbib_last_error"]
 
@@ -86,6 +87,7 @@ def load():
         L.lbib_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
         L.lbib_set_output.argtypes = [vp, C.c_int]
         L.lbib_set_overlap.argtypes = [vp, C.c_int]
+        L.lbib_set_graphs.argtypes = [vp, C.c_int]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_destroy.argtypes = [vp]
@@ -204,6 +206,10 @@ def lbib_autotune(ctx, steps):
 
 def lbib_set_overlap(ctx, enable):
     return _check(ctx, load().lbib_set_overlap(ctx, int(enable)))
+
+
+def lbib_set_graphs(ctx, enable):
+    return _check(ctx, load().lbib_set_graphs(ctx, int(enable)))
 
 
 def lbib_set_output(ctx, fields_every):

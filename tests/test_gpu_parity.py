@@ -209,6 +209,31 @@ def test_overlapped_and_serial_sweeps_agree(lbib):
     assert rel(out[0][1], out[1][1]) < 1e-14
 
 
+@pytest.mark.parametrize("overlap", [1, 0])
+def test_graph_steps_match_enqueued_steps(lbib, overlap):
+    """Steps replayed from the six captured CUDA graphs equal steps whose
+    kernels are enqueued one by one (FP64; only the order of the atomic
+    spreading sums may differ), also when field-storing steps, which are
+    enqueued directly, interleave with graph steps at every phase of the
+    buffer rotation."""
+    case = W.case_capsule_shear(n=28, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01,
+                                kv=1.0, precision=W.PREC_FP64)
+    out = []
+    for graphs in (1, 0):
+        ctx = lbib.Context.from_case(case)
+        lbib.lbib_set_overlap(ctx.h, overlap)
+        lbib.lbib_set_graphs(ctx.h, graphs)
+        lbib.lbib_set_output(ctx.h, 5)
+        for n in (7, 1, 6, 11):
+            ctx.step(n)
+        out.append((ctx.populations(), ctx.markers(0)[0], ctx.fields()[1]))
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        assert rel(a, b) < 1e-14
+    o = run_oracle(case, 25)
+    assert rel(out[0][0], o["f"]) < 1e-12
+
+
 def test_autotuned_launch_configurations_keep_parity(lbib):
     """Every block shape and overlap mode the autotuner tries computes the
     same step: after tuning (which advances the run) the state still matches
