@@ -914,7 +914,8 @@ int build_graphs(Ctx *c) {
             return rc;
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
-        e = cudaGraphInstantiate(&c->gexec[k], g, 0);
+        // kernel nodes keep the priority of the stream they were captured from
+        e = cudaGraphInstantiateWithFlags(&c->gexec[k], g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
     }

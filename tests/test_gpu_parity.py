@@ -213,7 +213,7 @@ def test_overlapped_and_serial_sweeps_agree(lbib):
 def test_graph_steps_match_enqueued_steps(lbib, overlap):
     """Steps replayed from the six captured CUDA graphs equal steps whose
     kernels are enqueued one by one (FP64; only the order of the atomic
-    spreading sums may differ), also when field-storing steps, which are
+    spreading sums may differ, hence 1e-13), also when field-storing steps, which are
     enqueued directly, interleave with graph steps at every phase of the
     buffer rotation."""
     case = W.case_capsule_shear(n=28, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01,
@@ -229,7 +229,7 @@ def test_graph_steps_match_enqueued_steps(lbib, overlap):
         out.append((ctx.populations(), ctx.markers(0)[0], ctx.fields()[1]))
         ctx.close()
     for a, b in zip(out[0], out[1]):
-        assert rel(a, b) < 1e-14
+        assert rel(a, b) < 1e-13
     o = run_oracle(case, 25)
     assert rel(out[0][0], o["f"]) < 1e-12
 
