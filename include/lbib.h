@@ -48,7 +48,8 @@ enum {
     LBIB_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
     LBIB_EDIVERGED = -4,   /* reserved: non-finite state detected */
     LBIB_EBODY_WALL = -5,  /* an MLS support (marker or probe) reached a wall node */
-    LBIB_ETIMEOUT = -6     /* reserved: a bounded device wait expired */
+    LBIB_ETIMEOUT = -6,    /* reserved: a bounded device wait expired */
+    LBIB_ETOOBIG = -7      /* a size exceeds a fixed maximum (lbib_mesh_measures_noalloc) */
 };
 
 /* Storage precision of the populations.  FP64 stores and computes in
@@ -188,6 +189,39 @@ int lbib_set_output(void *ctx, int fields_every);
 
 /* Bytes of device memory held by the context. */
 int lbib_device_bytes(void *ctx, size_t *bytes);
+
+/* Largest triangle count lbib_mesh_measures_noalloc accepts. */
+#define LBIB_NOALLOC_MAX_TRIS (1 << 20)
+
+/* Enclosed volume and surface area of a closed triangle mesh, computed on
+ * the GPU without allocating any memory.  The paper has no counterpart: it
+ * is a stand-alone, allocation-free variant of the membrane-volume reduction
+ * the step performs (and gives the volume and area lbib_get_body reports).
+ *
+ * For callers that cannot call cudaMalloc: code that runs while another
+ * thread captures a CUDA graph in global capture mode (cudaMalloc is then
+ * an error), code whose device memory is reserved up front by a pool or a
+ * budget, and latency-bound loops where an allocation would synchronise
+ * the device.  No context is needed.
+ *
+ * X[3*nv] (vertex x, y, z) and tris[3*nt] (vertex indices of outward,
+ * counter-clockwise triangles) are device arrays; out[2] (device) receives
+ * the volume (sum over triangles of X0 . (X1 x X2) / 6) and the area.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = the default stream); the
+ * caller owns every array.  A vertex index outside [0, nv) is skipped and
+ * makes both outputs NaN.  nt = 0 gives zeros.
+ *
+ * Scratch: a 64 KiB file-scope device array (plus a counter), held on every
+ * GPU that loads the library until the process exits, so nt is limited to
+ * LBIB_NOALLOC_MAX_TRIS; larger nt returns LBIB_ETOOBIG, negative sizes or
+ * NULL arrays LBIB_EINVAL, a failed CUDA call LBIB_ECUDA.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current: make that first call before any stream capture.
+ * Every call shares the array (each clears its counter first), so calls
+ * that overlap on the GPU -- on different streams, or from different host
+ * threads -- race and must be serialised by the caller.  Allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine. */
+int lbib_mesh_measures_noalloc(const double *X, int nv, const int *tris, int nt, double *out, void *stream);
 
 /* Releases all device and host memory of the context (NULL is a no-op). */
 void lbib_destroy(void *ctx);

@@ -17,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbib.so")
 
 LBIB_OK, LBIB_EINVAL, LBIB_ENOMEM, LBIB_ECUDA, LBIB_EDIVERGED, LBIB_EBODY_WALL, LBIB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBIB_ETOOBIG = -7
+LBIB_NOALLOC_MAX_TRIS = 1 << 20
 LBIB_FP64, LBIB_FP32, LBIB_FP16_DEV, LBIB_BF16_DEV = 0, 1, 2, 3
 LBIB_PERIODIC, LBIB_WALL = 0, 1
 
@@ -56,7 +58,7 @@ _lib = None
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_autotune",
-           "lbib_device_bytes",
+           "lbib_device_bytes", "lbib_mesh_measures_noalloc",
            "lbib_destroy",
            "lbib_last_error"]
 
@@ -90,6 +92,7 @@ def load():
         L.lbib_set_graphs.argtypes = [vp, C.c_int]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.lbib_mesh_measures_noalloc.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
         L.lbib_destroy.argtypes = [vp]
         L.lbib_destroy.restype = None
         L.lbib_last_error.argtypes = [vp]
@@ -336,3 +339,23 @@ class Context:
 
     def counters(self):
         return lbib_counters(self.h)
+
+
+_NOALLOC_MESSAGES = {
+    LBIB_ETOOBIG: f"more than LBIB_NOALLOC_MAX_TRIS = {LBIB_NOALLOC_MAX_TRIS} triangles",
+    LBIB_EINVAL: "negative size or NULL array",
+    LBIB_ECUDA: "a CUDA call failed (device lookup of the scratch array or the launch)",
+}
+
+
+def lbib_mesh_measures_noalloc(X, nv, tris, nt, out, stream=None):
+    """Volume and area of a closed mesh into out[2], allocating nothing.
+    X, tris and out are device pointers (ints) or CUDA tensors; stream is a
+    cudaStream_t handle (int) or None for the default stream."""
+    def addr(a):
+        return C.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a)
+    rc = load().lbib_mesh_measures_noalloc(addr(X), int(nv), addr(tris), int(nt), addr(out),
+                                           C.c_void_p(stream) if stream else None)
+    if rc != LBIB_OK:
+        raise LbibError(rc, _NOALLOC_MESSAGES.get(rc, "error"))
+    return rc
