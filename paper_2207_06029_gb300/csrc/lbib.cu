@@ -70,7 +70,7 @@ struct Ctx {
     // CUDA graphs of one step, one per phase of the buffer rotation (period 6)
     cudaStream_t s_cap = nullptr;
     cudaGraphExec_t gexec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool graphs_valid = false, use_graphs = true;
+    bool graphs_valid = false, use_graphs = true, graphs_timed = false;
     long long graph_origin = 0;
     cudaEvent_t gev[6][6] = {};  // timing events recorded by the graphs
     bool gev_pending[6] = {false, false, false, false, false, false};
@@ -903,7 +903,7 @@ int build_graphs(Ctx *c) {
         cudaStreamWaitEvent(c->s_hi, c->ev_fork, 0);
         cudaStreamWaitEvent(c->s_lo, c->ev_fork, 0);
         const long long launches = c->launches;
-        int rc = enqueue_step(c, false, c->gev[k], true);
+        int rc = enqueue_step(c, false, c->profile ? c->gev[k] : nullptr, true);
         c->launches = launches;
         cudaEventRecord(c->ev_join, c->s_hi);
         cudaStreamWaitEvent(c->s_cap, c->ev_join, 0);
@@ -920,6 +920,7 @@ int build_graphs(Ctx *c) {
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
     }
     c->graph_origin = c->steps;
+    c->graphs_timed = c->profile;
     c->graphs_valid = true;
     return LBIB_OK;
 }
@@ -952,7 +953,7 @@ int lbib_step(void *h, int nsteps) {
         const bool store = c->fields_every == 0 ? (it == nsteps - 1)
                                                 : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
         if (c->use_graphs && !store) {
-            if (!c->graphs_valid) {
+            if (!c->graphs_valid || c->graphs_timed != c->profile) {
                 int rc = build_graphs(c);
                 if (rc) return rc;
             }

@@ -220,6 +220,20 @@ def case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=
                 precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), U))
 
 
+def case_jeffery_spheroid(n=32, tau=0.8, shear_rate=5e-3, axes=(6.0, 3.0, 3.0), level=3, precision=PREC_FP32,
+                          steps=800):
+    """Neutrally buoyant rigid prolate spheroid (aspect ratio 2, major axis
+    along the flow x) at the centre of a Couette cell n^3 with z walls: the
+    Jeffery-orbit configuration (quarter period pi (r + 1/r) / (2 shear_rate)
+    = 785 steps at the defaults)."""
+    U = shear_rate * (n - 1) / 2.0
+    c = (n - 1) / 2.0
+    v, f = icosphere(level, 1.0, (c, c, c), axes=axes)
+    body = Body(v, f, rigid=True, density_ratio=1.0, ref_radius=float(axes[1]))
+    return Case(f"jeffery_spheroid_{n}", (n, n, n), tau, (PERIODIC, PERIODIC, WALL), shear_walls(U),
+                precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), U))
+
+
 def case_settling(nx=160, ny=160, nz=480, tau=0.7, radius=8.0, level=5, Re=5.0, gamma=1.3, steps=50000,
                   precision=PREC_FP32, prolate=False):
     """Rigid sphere (radius 8, 10242 markers) settling along -z in a closed
