@@ -163,8 +163,8 @@ int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
 /* Times the step in several launch configurations and keeps the fastest:
  * the block shape of the whole-lattice sweep, then (single-body contexts)
  * the overlap of the far-field sweep with the IB stage.  Each trial runs
- * `steps` real time steps, so the simulation advances by a few times
- * `steps`.  choice (optional, 3 ints) receives block x, block y (0, 0: whole
+ * 1 + 2 * `steps` real time steps, so the simulation advances by about
+ * 16 * `steps` steps.  choice (optional, 3 ints) receives block x, block y (0, 0: whole
  * x-rows) and the overlap flag. */
 int lbib_autotune(void *ctx, int steps, int *choice);
 

@@ -295,19 +295,25 @@ __global__ void k_init_equilibrium(S *__restrict__ fout, Lattice L, const double
                                    const double *__restrict__ u, R *__restrict__ fields) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= L.ncell) return;
-    const double r = rho[idx], ux = u[3 * idx], uy = u[3 * idx + 1], uz = u[3 * idx + 2];
-    const double uu = ux * ux + uy * uy + uz * uz;
+    // in the arithmetic precision R; the density excess is formed in double
+    // before rounding (rho - 1 is small)
+    const R dr = R(rho[idx] - 1.0), r = R(1) + dr;
+    const R ux = R(u[3 * idx]), uy = R(u[3 * idx + 1]), uz = R(u[3 * idx + 2]);
+    const R uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const double eu = ex(i) * ux + ey(i) * uy + ez(i) * uz;
-        const double w = wq<double>(i);
-        const double g = w * (r - 1.0) + w * r * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-        Pop<S, R>::st(fout + (long long)i * L.stride + idx, R(g));
+        R eu = R(0);
+        if (ex(i)) eu += R(ex(i)) * ux;
+        if (ey(i)) eu += R(ey(i)) * uy;
+        if (ez(i)) eu += R(ez(i)) * uz;
+        const R w = wq<R>(i);
+        const R g = w * dr + w * r * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu);
+        Pop<S, R>::st(fout + (long long)i * L.stride + idx, g);
     }
-    fields[idx] = R(r);
-    fields[L.stride + idx] = R(ux);
-    fields[2 * L.stride + idx] = R(uy);
-    fields[3 * L.stride + idx] = R(uz);
+    fields[idx] = r;
+    fields[L.stride + idx] = ux;
+    fields[2 * L.stride + idx] = uy;
+    fields[3 * L.stride + idx] = uz;
 }
 
 template <typename S, typename R>
