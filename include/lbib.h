@@ -190,6 +190,48 @@ int lbib_set_output(void *ctx, int fields_every);
 /* Bytes of device memory held by the context. */
 int lbib_device_bytes(void *ctx, size_t *bytes);
 
+/* ---- batches -----------------------------------------------------------
+ * A batch advances the lattices and bodies of several contexts with common
+ * launches: per step one support-moments, one MLS, one membrane (and rigid)
+ * and one collide-stream launch cover every lattice of the batch, each
+ * launch splitting its blocks over the lattices or bodies by prefix sums.
+ * Steps run six at a time from one captured CUDA graph (one graph per batch;
+ * six steps bring every buffer rotation back to its start).  Each context
+ * computes exactly what lbib_step would (up to the order of the atomic
+ * spreading sums).  Used for many small, uneven runs at once. */
+
+/* Creates a batch of n contexts (same precision; each context in at most
+ * one live batch).  stream: cudaStream_t of the batch, or NULL for a
+ * library-owned one.  Waits for the contexts' queued work.  out receives
+ * the batch.  LBIB_EINVAL for mixed precisions, repeated or NULL contexts;
+ * the message is lbib_batch_last_error(NULL). */
+int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out);
+
+/* Advances every context of the batch by nsteps (asynchronously on the
+ * batch stream, ordered after each context's queued work; later work on a
+ * context's stream is ordered after it).  The fields of the last step are
+ * stored, as with lbib_step.  A context stepped on its own since the batch
+ * was built makes this return LBIB_EINVAL (rebuild the batch). */
+int lbib_batch_step(void *batch, int nsteps);
+
+/* Waits for the batch and reports the first context error. */
+int lbib_batch_sync(void *batch);
+
+/* Steps taken through the batch and kernels launched by it. */
+int lbib_batch_counters(void *batch, long long *steps, long long *launches);
+
+/* Times `steps` steps for each sweep block size (128, 256, 512 threads) and
+ * lattice order in the sweep launch (as given; largest lattice first) and
+ * keeps the fastest; the contexts advance by about 14 + 12 * steps steps.
+ * choice (optional, 2 ints): threads, order. */
+int lbib_batch_autotune(void *batch, int steps, int *choice);
+
+/* Releases the batch (not its contexts). */
+void lbib_batch_destroy(void *batch);
+
+/* Message of the last error of a batch (NULL: of the last failed create). */
+const char *lbib_batch_last_error(const void *batch);
+
 /* Largest triangle count lbib_mesh_measures_noalloc accepts. */
 #define LBIB_NOALLOC_MAX_TRIS (1 << 20)
 

@@ -38,10 +38,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 // recorded on the device by the previous step's update.
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-__global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Lattice L, const int *__restrict__ box,
-                                                 int *__restrict__ box_next, R *__restrict__ mom,
-                                                 uint32_t *__restrict__ step_inc) {
-    if (step_inc && blockIdx.x == 0 && threadIdx.x == 0) *step_inc += 1u;  // read by the later kernels of the step
+__device__ __forceinline__ void moments_body(const S *__restrict__ fin, const Lattice &L, const int *__restrict__ box,
+                                             int *__restrict__ box_next, R *__restrict__ mom,
+                                             uint32_t *__restrict__ step_inc, const int vb, const int nvb) {
+    if (step_inc && vb == 0 && threadIdx.x == 0) *step_inc += 1u;  // read by the later kernels of the step
     const int n[3] = {L.nx, L.ny, L.nz};
     int lo[3], ext[3];
     for (int a = 0; a < 3; ++a) {
@@ -56,11 +56,11 @@ __global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Latt
         lo[a] = (int)l;
         ext[a] = h < l ? 0 : (int)(h - l + 1);
     }
-    if (blockIdx.x == 0 && threadIdx.x < 6) box_next[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+    if (vb == 0 && threadIdx.x < 6) box_next[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
     const int total = ext[0] * ext[1] * ext[2];
     const int nxy = L.nx * L.ny;
     const long long st = L.stride;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    for (int k = vb * blockDim.x + threadIdx.x; k < total; k += nvb * blockDim.x) {
         int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
         int cm[3], cp[3];
         for (int a = 0; a < 3; ++a) {
@@ -93,6 +93,13 @@ __global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Latt
         mom[2 * st + node] = (jy + R(0.5) * pick<R>(L.gext_d[1], L.gext_f[1])) / rho;
         mom[3 * st + node] = (jz + R(0.5) * pick<R>(L.gext_d[2], L.gext_f[2])) / rho;
     }
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Lattice L, const int *__restrict__ box,
+                                                 int *__restrict__ box_next, R *__restrict__ mom,
+                                                 uint32_t *__restrict__ step_inc) {
+    moments_body<S, R>(fin, L, box, box_next, mom, step_inc, blockIdx.x, gridDim.x);
 }
 
 constexpr int kSums = 26;  // A (10 entries), b for rho (4), b for u (12)
@@ -190,13 +197,11 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
 //           the traction rho nu (grad u + grad u^T) . n from the fits;
 //  phase 3: markers keep phi_k = W_k (A^-1 p_k)_0 for spreading.
 template <typename R>
-__global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, Lattice L, BodyView B,
-                                                     int *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlsSmem<R> &sm = *reinterpret_cast<MlsSmem<R> *>(smem_raw);
+__device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattice &L, const BodyView &B, int *err,
+                                         MlsSmem<R> &sm, const int vb, const int nvb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npts = B.nv + 2 * B.nt;
-    const int p0 = blockIdx.x * kPts;
+    const int p0 = vb * kPts;
     const long long st = L.stride;
     const int nxy = L.nx * L.ny;
     const int n[3] = {L.nx, L.ny, L.nz};
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
     // The lane-per-point phases (0 and 2) run FP64 code; FP64 issues per
     // warp-instruction on one SM sub-partition, so blocks rotate the warp
     // that runs them over the four sub-partitions.
-    const int w0 = blockIdx.x & 3, w2 = (blockIdx.x + 2) & 3;
+    const int w0 = vb & 3, w2 = (vb + 2) & 3;
 
     // ---------------- phase 0: one lane per point ----------------
     if (warp == w0) {
@@ -411,15 +416,15 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
         if (threadIdx.x == 32 * ((w2 + 1) & 3)) {
             double s = 0.0;
             for (int k = 0; k < kPts; ++k) s += sm.vol[k];
-            B.vol_part[blockIdx.x] = s;
+            B.vol_part[vb] = s;
             __threadfence();
-            s_last = atomicAdd(B.vol_count, 1u) == gridDim.x - 1;
+            s_last = atomicAdd(B.vol_count, 1u) == (unsigned)nvb - 1;
         }
         __syncthreads();
         if (s_last) {
             __threadfence();
             double s = 0.0;
-            for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) s += __ldcg(B.vol_part + k);
+            for (int k = threadIdx.x; k < nvb; k += blockDim.x) s += __ldcg(B.vol_part + k);
             s = warp_sum(s);
             __shared__ double wpart[kMlsThreads / 32];
             if (lane == 0) wpart[warp] = s;
@@ -446,6 +451,13 @@ __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, 
             ((R *)B.phi)[27 * p + lane] = phi;
         }
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, Lattice L, BodyView B,
+                                                     int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    mls_body<R>(mom, L, B, err, *reinterpret_cast<MlsSmem<R> *>(smem_raw), blockIdx.x, gridDim.x);
 }
 
 // Hydrodynamic force on triangle t from its two probes (Eqs. hydroForP,
@@ -522,13 +534,14 @@ struct BlockBox {
 // U_b = U + F/m_v dt; the Lagrangian force F_l = U_b - U spread with
 // c_l = A_l (Eq. bodyforce).
 template <typename R>
-__global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
-                                                  uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
+__device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &B, R *__restrict__ force,
+                                              uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep,
+                                              const int vb) {
     const uint32_t step = *dstep;
     __shared__ R s_cv;
     __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int v = (vb * blockDim.x + threadIdx.x) >> 5;
     // the spreading lanes fetch their node and weight first
     int snode = 0;
     R sphi = R(0);
@@ -638,6 +651,12 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
     sbox.flush(B.bbox_next);
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
+                                                  uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
+    membrane_body<R>(L, B, force, stamp, dstep, blockIdx.x);
+}
+
 // Rigid body: total force and moment of the element stresses, gravity
 // minus buoyancy, F = m du/dt and M = I dw/dt with I in the world frame,
 // second-order backward velocities (Eqs. linearVelRig, angularVelRig),
@@ -648,7 +667,7 @@ __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__re
 // working on the components side by side (FP64 issues per
 // warp-instruction, so the update is written across lanes).
 template <typename R>
-__global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
+__device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int vb, const int nvb) {
     __shared__ double red[6][8];
     __shared__ int s_last;
     __shared__ double sF[6], sR[9], sY[3], sQ[4];
@@ -657,7 +676,7 @@ __global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
     const R xc[3] = {R(S[RigidState::XC] - B.origin[0]), R(S[RigidState::XC + 1] - B.origin[1]),
                      R(S[RigidState::XC + 2] - B.origin[2])};
     R f[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = vb * blockDim.x + threadIdx.x;
     if (t < B.nt) {
         R Fh[3];
         tri_hydro<R>(B, t, Fh);
@@ -678,12 +697,12 @@ __global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
     if (threadIdx.x < 6) {
         double acc = 0.0;
         for (int w = 0; w < 8; ++w) acc += red[threadIdx.x][w];
-        B.vol_part[6 * blockIdx.x + threadIdx.x] = acc;
+        B.vol_part[6 * vb + threadIdx.x] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(B.vol_count, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(B.vol_count, 1u) == (unsigned)nvb - 1;
     }
     __syncthreads();
     if (!s_last || warp != 0) return;
@@ -691,7 +710,7 @@ __global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
     // totals: lane q < 6 sums partial q over the blocks in block order
     if (lane < 6) {
         double acc = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) acc += __ldcg(B.vol_part + 6 * b + lane);
+        for (int b = 0; b < nvb; ++b) acc += __ldcg(B.vol_part + 6 * b + lane);
         if (lane < 3) acc += (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + lane];
         sF[lane] = acc;
     }
@@ -812,15 +831,21 @@ __global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_rigid_forces(BodyView B) {
+    rigid_forces_body<R>(B, blockIdx.x, gridDim.x);
+}
+
 // Rigid markers, one warp each: boundary velocity u + w x (X - x_c) of
 // level n, IB force and spreading, then the markers of level n+1.
 template <typename R>
-__global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
-                                                       uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
+__device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyView &B, R *__restrict__ force,
+                                                   uint32_t *__restrict__ stamp,
+                                                   const uint32_t *__restrict__ dstep, const int vb) {
     const uint32_t step = *dstep;
     __shared__ BlockBox sbox;
     const int lane = threadIdx.x & 31;
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int v = (vb * blockDim.x + threadIdx.x) >> 5;
     sbox.init();
     __syncthreads();
     if (v < B.nv) {
@@ -854,6 +879,76 @@ __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R 
     sbox.flush(B.bbox_next);
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
+                                                       uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
+    rigid_markers_body<R>(L, B, force, stamp, dstep, blockIdx.x);
+}
+
+// ---- batch kernels: the bodies of all lattices of a batch per launch ----
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) kb_moments(BatchTables T, int phase) {
+    const int j = batch_item(T.mom_pre, T.nb, blockIdx.x);
+    const int vb = blockIdx.x - __ldg(T.mom_pre + j), nvb = __ldg(T.mom_pre + j + 1) - __ldg(T.mom_pre + j);
+    const BodyRef &br = T.body[phase * T.nb + j];
+    const LatRef &F = T.ref[phase * T.nl + br.lat];
+    moments_body<S, R>((const S *)F.fin, T.lat[br.lat], br.v.bbox, br.v.bbox_next, (R *)F.mom,
+                       br.inc_step ? F.d_step : nullptr, vb, nvb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kMlsThreads) kb_mls(BatchTables T, int phase) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int j = batch_item(T.mls_pre, T.nb, blockIdx.x);
+    const int vb = blockIdx.x - __ldg(T.mls_pre + j), nvb = __ldg(T.mls_pre + j + 1) - __ldg(T.mls_pre + j);
+    const BodyRef &br = T.body[phase * T.nb + j];
+    const LatRef &F = T.ref[phase * T.nl + br.lat];
+    mls_body<R>((const R *)F.mom, T.lat[br.lat], br.v, F.err, *reinterpret_cast<MlsSmem<R> *>(smem_raw), vb, nvb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_membrane(BatchTables T, int phase) {
+    const int m = batch_item(T.memb_pre, T.nmemb, blockIdx.x);
+    const BodyRef &br = T.body[phase * T.nb + __ldg(T.memb_id + m)];
+    const LatRef &F = T.ref[phase * T.nl + br.lat];
+    membrane_body<R>(T.lat[br.lat], br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.memb_pre + m));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_rigid_forces(BatchTables T, int phase) {
+    const int m = batch_item(T.rf_pre, T.nrigid, blockIdx.x);
+    const BodyRef &br = T.body[phase * T.nb + __ldg(T.rigid_id + m)];
+    const int b0 = __ldg(T.rf_pre + m);
+    rigid_forces_body<R>(br.v, blockIdx.x - b0, __ldg(T.rf_pre + m + 1) - b0);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_rigid_markers(BatchTables T, int phase) {
+    const int m = batch_item(T.rm_pre, T.nrigid, blockIdx.x);
+    const BodyRef &br = T.body[phase * T.nb + __ldg(T.rigid_id + m)];
+    const LatRef &F = T.ref[phase * T.nl + br.lat];
+    rigid_markers_body<R>(T.lat[br.lat], br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.rm_pre + m));
+}
+
+template <typename S, typename R>
+static cudaError_t batch_ib_t(const BatchTables &T, const BatchGrid &G, int phase, cudaStream_t s) {
+    if (G.mom > 0) kb_moments<S, R><<<G.mom, 256, 0, s>>>(T, phase);
+    if (G.mls > 0) kb_mls<R><<<G.mls, kMlsThreads, sizeof(MlsSmem<R>), s>>>(T, phase);
+    if (G.memb > 0) kb_membrane<R><<<G.memb, 256, 0, s>>>(T, phase);
+    if (G.rf > 0) kb_rigid_forces<R><<<G.rf, 256, 0, s>>>(T, phase);
+    if (G.rm > 0) kb_rigid_markers<R><<<G.rm, 256, 0, s>>>(T, phase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ib(int prec, const BatchTables &T, const BatchGrid &G, int phase, cudaStream_t s) {
+    switch (prec) {
+        case 0: return batch_ib_t<double, double>(T, G, phase, s);
+        case 1: return batch_ib_t<float, float>(T, G, phase, s);
+        case 2: return batch_ib_t<__half, float>(T, G, phase, s);
+        default: return batch_ib_t<__nv_bfloat16, float>(T, G, phase, s);
+    }
+}
+
 // ---- launchers ----
 int mls_blocks(const BodyView &B) { return (B.nv + 2 * B.nt + kPts - 1) / kPts; }
 
@@ -874,6 +969,12 @@ cudaError_t prepare_kernels() {
                                          (int)sizeof(MlsSmem<float>));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mls<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(MlsSmem<double>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_mls<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(MlsSmem<float>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_mls<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(MlsSmem<double>));
     return e;
 }

@@ -1242,3 +1242,411 @@ int lbib_device_bytes(void *h, size_t *bytes) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: the lattices and bodies of several contexts advanced by common
+// launches (one moments, MLS, structure and sweep launch per step for the
+// whole batch), optionally replayed six steps at a time from a CUDA graph.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Batch {
+    std::vector<Ctx *> ctx;
+    std::vector<long long> base;      // step count of each context at the last table build
+    std::vector<cudaEvent_t> ctx_ev;  // per context: its stream's work before a batch call
+    int prec = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t done = nullptr;
+    void *dmem = nullptr;
+    BatchTables T{};
+    BatchGrid G{};
+    long long steps = 0;  // steps since the last table build (phase origin)
+    int sweep_threads = 256, order = 0;
+    cudaGraphExec_t g6 = nullptr;
+    long long launches = 0, total_steps = 0;
+    std::string msg;
+};
+
+std::string g_batch_error;
+
+int bfail(Batch *b, int code, const char *what) {
+    if (b)
+        b->msg = what;
+    else
+        g_batch_error = what;
+    return code;
+}
+
+int bcuda(Batch *b, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return bfail(b, LBIB_ECUDA, m.c_str());
+}
+
+void batch_free_tables(Batch *b) {
+    if (b->g6) cudaGraphExecDestroy(b->g6);
+    b->g6 = nullptr;
+    if (b->dmem) cudaFree(b->dmem);
+    b->dmem = nullptr;
+}
+
+// Builds the launch tables from the contexts' current state (phase 0) and
+// the five rotations that follow it.
+int batch_build(Batch *b) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free_tables(b);
+    const int nl = (int)b->ctx.size();
+    std::vector<Lattice> lat(nl);
+    std::vector<LatRef> ref(6 * (size_t)nl);
+    std::vector<std::pair<int, int>> bodies;  // (context, body)
+    for (int i = 0; i < nl; ++i)
+        for (int j = 0; j < (int)b->ctx[i]->bodies.size(); ++j) bodies.push_back({i, j});
+    const int nb = (int)bodies.size();
+    std::vector<BodyRef> body(6 * (size_t)nb);
+    for (int i = 0; i < nl; ++i) {
+        Ctx *c = b->ctx[i];
+        lat[i] = c->L;
+        for (int k = 0; k < 6; ++k) {
+            LatRef &r = ref[(size_t)k * nl + i];
+            r.fin = (k % 2 == 0) ? c->fA : c->fB;
+            r.fout = (k % 2 == 0) ? c->fB : c->fA;
+            r.force = c->force;
+            r.fields = c->fields;
+            r.mom = c->mom;
+            r.stamp = c->bodies.empty() ? nullptr : c->stamp;
+            r.d_step = c->d_step;
+            r.err = c->d_err;
+        }
+    }
+    std::vector<int> mom_pre(1, 0), mls_pre(1, 0), memb_id, memb_pre(1, 0), rigid_id, rf_pre(1, 0), rm_pre(1, 0);
+    for (int q = 0; q < nb; ++q) {
+        Ctx *c = b->ctx[bodies[q].first];
+        DevBody &d = c->bodies[bodies[q].second];
+        const int cur0 = d.cur, bcur0 = d.bcur;
+        for (int k = 0; k < 6; ++k) {
+            d.cur = (cur0 + k) % 3;
+            d.bcur = bcur0 ^ (k & 1);
+            BodyRef &br = body[(size_t)k * nb + q];
+            br.v = make_view(c, d);
+            br.lat = bodies[q].first;
+            br.inc_step = bodies[q].second == 0;
+        }
+        d.cur = cur0;
+        d.bcur = bcur0;
+        const BodyView &v = body[q].v;
+        mom_pre.push_back(mom_pre.back() + std::max(8, d.nv / 16));
+        mls_pre.push_back(mls_pre.back() + mls_blocks(v));
+        if (d.rigid) {
+            rigid_id.push_back(q);
+            rf_pre.push_back(rf_pre.back() + (d.nt + 255) / 256);
+            rm_pre.push_back(rm_pre.back() + (d.nv + 7) / 8);
+        } else {
+            memb_id.push_back(q);
+            memb_pre.push_back(memb_pre.back() + (d.nv + 7) / 8);
+        }
+    }
+    // sweep slots: lattices in launch order (0: as given, 1: largest first)
+    std::vector<int> order(nl);
+    for (int i = 0; i < nl; ++i) order[i] = i;
+    if (b->order == 1)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return lat[x].ncell > lat[y].ncell; });
+    std::vector<int> sweep_pre(1, 0);
+    for (int i = 0; i < nl; ++i)
+        sweep_pre.push_back(sweep_pre.back() + (lat[order[i]].ncell + b->sweep_threads - 1) / b->sweep_threads);
+    // one device block for all tables
+    size_t off = 0;
+    auto place = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_lat = place(sizeof(Lattice) * nl), o_ref = place(sizeof(LatRef) * ref.size()),
+                 o_body = place(sizeof(BodyRef) * body.size()), o_slat = place(sizeof(int) * nl),
+                 o_spre = place(sizeof(int) * sweep_pre.size()), o_mom = place(sizeof(int) * mom_pre.size()),
+                 o_mls = place(sizeof(int) * mls_pre.size()), o_mid = place(sizeof(int) * memb_id.size()),
+                 o_mpre = place(sizeof(int) * memb_pre.size()), o_rid = place(sizeof(int) * rigid_id.size()),
+                 o_rf = place(sizeof(int) * rf_pre.size()), o_rm = place(sizeof(int) * rm_pre.size());
+    cudaError_t e = cudaMalloc(&b->dmem, off);
+    if (e != cudaSuccess) {
+        b->dmem = nullptr;
+        return bcuda(b, e, "batch tables");
+    }
+    std::vector<unsigned char> host(off);
+    auto put = [&](size_t o, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(host.data() + o, src, bytes);
+    };
+    put(o_lat, lat.data(), sizeof(Lattice) * nl);
+    put(o_ref, ref.data(), sizeof(LatRef) * ref.size());
+    put(o_body, body.data(), sizeof(BodyRef) * body.size());
+    put(o_slat, order.data(), sizeof(int) * nl);
+    put(o_spre, sweep_pre.data(), sizeof(int) * sweep_pre.size());
+    put(o_mom, mom_pre.data(), sizeof(int) * mom_pre.size());
+    put(o_mls, mls_pre.data(), sizeof(int) * mls_pre.size());
+    put(o_mid, memb_id.data(), sizeof(int) * memb_id.size());
+    put(o_mpre, memb_pre.data(), sizeof(int) * memb_pre.size());
+    put(o_rid, rigid_id.data(), sizeof(int) * rigid_id.size());
+    put(o_rf, rf_pre.data(), sizeof(int) * rf_pre.size());
+    put(o_rm, rm_pre.data(), sizeof(int) * rm_pre.size());
+    e = cudaMemcpy(b->dmem, host.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(b, e, "batch tables upload");
+    unsigned char *d = static_cast<unsigned char *>(b->dmem);
+    BatchTables &T = b->T;
+    T.nl = nl;
+    T.nb = nb;
+    T.nmemb = (int)memb_id.size();
+    T.nrigid = (int)rigid_id.size();
+    T.lat = reinterpret_cast<const Lattice *>(d + o_lat);
+    T.ref = reinterpret_cast<const LatRef *>(d + o_ref);
+    T.body = reinterpret_cast<const BodyRef *>(d + o_body);
+    T.sweep_lat = reinterpret_cast<const int *>(d + o_slat);
+    T.sweep_pre = reinterpret_cast<const int *>(d + o_spre);
+    T.mom_pre = reinterpret_cast<const int *>(d + o_mom);
+    T.mls_pre = reinterpret_cast<const int *>(d + o_mls);
+    T.memb_id = reinterpret_cast<const int *>(d + o_mid);
+    T.memb_pre = reinterpret_cast<const int *>(d + o_mpre);
+    T.rigid_id = reinterpret_cast<const int *>(d + o_rid);
+    T.rf_pre = reinterpret_cast<const int *>(d + o_rf);
+    T.rm_pre = reinterpret_cast<const int *>(d + o_rm);
+    T.sweep_threads = b->sweep_threads;
+    b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back()};
+    b->steps = 0;
+    for (int i = 0; i < nl; ++i) b->base[i] = b->ctx[i]->steps;
+    return LBIB_OK;
+}
+
+int batch_enqueue(Batch *b, int phase, bool store) {
+    cudaError_t e = launch_batch_ib(b->prec, b->T, b->G, phase, b->stream);
+    if (e == cudaSuccess) e = launch_batch_sweep(b->prec, b->T, b->G, phase, store ? 1 : 0, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch launch");
+    return LBIB_OK;
+}
+
+int batch_launches_per_step(const Batch *b) {
+    int n = 0;
+    for (int v : {b->G.sweep, b->G.mom, b->G.mls, b->G.memb, b->G.rf, b->G.rm}) n += v > 0;
+    return n;
+}
+
+int batch_capture6(Batch *b) {
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "batch capture");
+    int rc = LBIB_OK;
+    for (int k = 0; k < 6 && rc == LBIB_OK; ++k) rc = batch_enqueue(b, k, false);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "batch capture end");
+    e = cudaGraphInstantiate(&b->g6, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->g6 = nullptr;
+        return bcuda(b, e, "batch graph instantiate");
+    }
+    return LBIB_OK;
+}
+
+// The contexts' host-side state after n batch steps.
+void batch_advance_contexts(Batch *b, int n) {
+    for (Ctx *c : b->ctx) {
+        if (n % 2) std::swap(c->fA, c->fB);
+        for (auto &d : c->bodies) {
+            d.cur = (d.cur + n) % 3;
+            d.bcur ^= (n & 1);
+        }
+        c->steps += n;
+        if (!c->bodies.empty()) c->step_host += (uint32_t)n;
+    }
+}
+
+Batch *as_batch(void *h) { return static_cast<Batch *>(h); }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbib_batch_last_error(const void *h) {
+    if (!h) return g_batch_error.c_str();
+    return static_cast<const Batch *>(h)->msg.c_str();
+}
+
+int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out) {
+    if (!out) return bfail(nullptr, LBIB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return bfail(nullptr, LBIB_EINVAL, "a batch needs at least one context");
+    Batch *b = new Batch();
+    for (int i = 0; i < n; ++i) {
+        Ctx *c = static_cast<Ctx *>(ctxs[i]);
+        if (!c) {
+            delete b;
+            return bfail(nullptr, LBIB_EINVAL, "NULL context");
+        }
+        for (Ctx *o : b->ctx)
+            if (o == c) {
+                delete b;
+                return bfail(nullptr, LBIB_EINVAL, "a context appears twice");
+            }
+        if (c->err) {
+            delete b;
+            return bfail(nullptr, c->err, "a context holds an error");
+        }
+        if (i > 0 && c->prec != b->prec) {
+            delete b;
+            return bfail(nullptr, LBIB_EINVAL, "the contexts of a batch share one precision");
+        }
+        b->prec = c->prec;
+        b->ctx.push_back(c);
+    }
+    b->base.assign(n, 0);
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    b->ctx_ev.assign(n, nullptr);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ctx_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        int rc = bcuda(nullptr, e, "batch stream or events");
+        lbib_batch_destroy(b);
+        return rc;
+    }
+    for (Ctx *c : b->ctx) sync_ctx(c);  // contexts idle before their tables are taken
+    int rc = batch_build(b);
+    if (rc) {
+        g_batch_error = b->msg;
+        lbib_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBIB_OK;
+}
+
+int lbib_batch_step(void *h, int nsteps) {
+    Batch *b = as_batch(h);
+    if (!b) return LBIB_EINVAL;
+    if (nsteps < 0) return bfail(b, LBIB_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return LBIB_OK;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        Ctx *c = b->ctx[i];
+        if (c->err) return bfail(b, c->err, "a context of the batch holds an error");
+        if (c->steps != b->base[i] + b->steps)
+            return bfail(b, LBIB_EINVAL, "a context was stepped outside the batch; rebuild the batch");
+        if (!c->bodies.empty() && (uint64_t)c->step_host + (uint64_t)nsteps >= 0xFFFFFFFFull)
+            return bfail(b, LBIB_EINVAL, "step counter would wrap; step the context alone once");
+        // the batch runs after the work already queued on the context's stream
+        cudaEventRecord(b->ctx_ev[i], c->stream);
+        cudaStreamWaitEvent(b->stream, b->ctx_ev[i], 0);
+    }
+    int remaining = nsteps;
+    while (remaining > 0) {
+        const int phase = (int)(b->steps % 6);
+        if (phase == 0 && remaining > 6) {
+            if (!b->g6) {
+                int rc = batch_capture6(b);
+                if (rc) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(b->g6, b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
+            b->steps += 6;
+            remaining -= 6;
+            b->launches += 6 * batch_launches_per_step(b);
+        } else {
+            int rc = batch_enqueue(b, phase, remaining == 1);
+            if (rc) return rc;
+            b->steps += 1;
+            remaining -= 1;
+            b->launches += batch_launches_per_step(b);
+        }
+    }
+    batch_advance_contexts(b, nsteps);
+    b->total_steps += nsteps;
+    // later work on each context's stream runs after the batch
+    cudaError_t e = cudaEventRecord(b->done, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch event");
+    for (Ctx *c : b->ctx) cudaStreamWaitEvent(c->stream, b->done, 0);
+    return LBIB_OK;
+}
+
+int lbib_batch_sync(void *h) {
+    Batch *b = as_batch(h);
+    if (!b) return LBIB_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch sync");
+    for (Ctx *c : b->ctx) {
+        int rc = sync_ctx(c);
+        if (rc) return bfail(b, rc, c->msg.c_str());
+    }
+    return LBIB_OK;
+}
+
+int lbib_batch_counters(void *h, long long *steps, long long *launches) {
+    Batch *b = as_batch(h);
+    if (!b) return LBIB_EINVAL;
+    if (steps) *steps = b->total_steps;
+    if (launches) *launches = b->launches;
+    return LBIB_OK;
+}
+
+int lbib_batch_autotune(void *h, int steps, int *choice) {
+    Batch *b = as_batch(h);
+    if (!b || steps < 1) return LBIB_EINVAL;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bcuda(b, cudaGetLastError(), "autotune events");
+    const int threads[] = {128, 256, 512};
+    float best = 1e30f;
+    int best_t = b->sweep_threads, best_o = b->order, rc = LBIB_OK;
+    for (int o = 0; o < 2 && !rc; ++o)
+        for (int t : threads) {
+            b->sweep_threads = t;
+            b->order = o;
+            if ((rc = batch_build(b))) break;
+            if ((rc = lbib_batch_step(h, 7))) break;  // captures the graph, untimed
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {
+                cudaEventRecord(e0, b->stream);
+                rc = lbib_batch_step(h, steps);
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float t_ms = 0.f;
+                cudaEventElapsedTime(&t_ms, e0, e1);
+                if (t_ms < ms) ms = t_ms;
+            }
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                best_t = t;
+                best_o = o;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->sweep_threads = best_t;
+    b->order = best_o;
+    int rc2 = batch_build(b);
+    if (choice) {
+        choice[0] = best_t;
+        choice[1] = best_o;
+    }
+    return rc ? rc : rc2;
+}
+
+void lbib_batch_destroy(void *h) {
+    Batch *b = as_batch(h);
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free_tables(b);
+    for (cudaEvent_t ev : b->ctx_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -156,6 +156,53 @@ struct BodyView {
     double *vol_sum;        // enclosed volume times 6, written by the last MLS block
 };
 
+// ---- batches: the lattices of several contexts advanced by common launches ----
+// Buffers of one lattice in one phase of the six-step rotation.
+struct LatRef {
+    const void *fin;
+    void *fout, *force, *fields, *mom;
+    uint32_t *stamp;   // tile flags of the IB force, nullptr without bodies
+    uint32_t *d_step;  // device step counter
+    int *err;          // device error word
+};
+// A body in one phase, with the lattice it lives in.
+struct BodyRef {
+    BodyView v;
+    int lat;
+    int inc_step;  // the first body of its lattice advances the step counter
+};
+// Launch tables (device pointers).  The blocks of a batch launch are split
+// over its items by prefix sums of per-item block counts.
+struct BatchTables {
+    int nl, nb, nmemb, nrigid;
+    const Lattice *lat;    // [nl]
+    const LatRef *ref;     // [6 nl]: phase-major
+    const BodyRef *body;   // [6 nb]: phase-major
+    const int *sweep_lat;  // [nl] lattice of each sweep slot (launch order)
+    const int *sweep_pre;  // [nl + 1] sweep blocks, by slot
+    const int *mom_pre;    // [nb + 1] moments blocks
+    const int *mls_pre;    // [nb + 1] MLS blocks
+    const int *memb_id;    // [nmemb] membrane bodies
+    const int *memb_pre;   // [nmemb + 1] blocks of 8 vertex warps
+    const int *rigid_id;   // [nrigid] rigid bodies
+    const int *rf_pre;     // [nrigid + 1] triangle blocks of the force reduction
+    const int *rm_pre;     // [nrigid + 1] blocks of 8 marker warps
+    int sweep_threads;     // threads per sweep block
+};
+
+// Item of block b: the largest i with pre[i] <= b (pre[0] = 0, increasing).
+__device__ __forceinline__ int batch_item(const int *pre, int n, int b) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // Layout of the rigid-body state block (doubles).
 struct RigidState {
     enum {

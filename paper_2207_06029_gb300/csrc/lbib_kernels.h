@@ -33,4 +33,12 @@ cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void 
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
                          const uint32_t *step, cudaStream_t s);
 
+// batches (sweep.cu and ib.cu); grid sizes are the totals of the prefix tables
+struct BatchGrid {
+    int sweep, mom, mls, memb, rf, rm;
+};
+cudaError_t launch_batch_ib(int prec, const BatchTables &T, const BatchGrid &G, int phase, cudaStream_t s);
+cudaError_t launch_batch_sweep(int prec, const BatchTables &T, const BatchGrid &G, int phase, int store_fields,
+                               cudaStream_t s);
+
 }  // namespace lbib

@@ -289,6 +289,22 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
     }
 }
 
+// All lattices of a batch: block b belongs to sweep slot batch_item(b); its
+// threads take consecutive cells of that lattice (x fastest).
+template <typename S, typename R>
+__global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int store_fields) {
+    const int slot = batch_item(T.sweep_pre, T.nl, blockIdx.x);
+    const int l = __ldg(T.sweep_lat + slot);
+    const Lattice &L = T.lat[l];
+    const LatRef &F = T.ref[phase * T.nl + l];
+    const int c = (blockIdx.x - __ldg(T.sweep_pre + slot)) * blockDim.x + threadIdx.x;
+    if (c >= L.ncell) return;
+    const int x = c % L.nx, yz = c / L.nx, y = yz % L.ny, z = yz / L.ny;
+    const uint32_t step = F.stamp ? *F.d_step : 0u;
+    sweep_cell<S, R>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L,
+                     store_fields ? (R *)F.fields : nullptr, x, y, z);
+}
+
 // f = f^eq(rho, u) from double fields (Eq. eqfunc), stored as deviations.
 template <typename S, typename R>
 __global__ void k_init_equilibrium(S *__restrict__ fout, Lattice L, const double *__restrict__ rho,
@@ -390,6 +406,22 @@ cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, con
         case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
         case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
         default: return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
+    }
+}
+
+template <typename S, typename R>
+static cudaError_t batch_sweep_t(const BatchTables &T, const BatchGrid &G, int phase, int store, cudaStream_t s) {
+    if (G.sweep > 0) kb_sweep<S, R><<<G.sweep, T.sweep_threads, 0, s>>>(T, phase, store);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sweep(int prec, const BatchTables &T, const BatchGrid &G, int phase, int store_fields,
+                               cudaStream_t s) {
+    switch (prec) {
+        case 0: return batch_sweep_t<double, double>(T, G, phase, store_fields, s);
+        case 1: return batch_sweep_t<float, float>(T, G, phase, store_fields, s);
+        case 2: return batch_sweep_t<__half, float>(T, G, phase, store_fields, s);
+        default: return batch_sweep_t<__nv_bfloat16, float>(T, G, phase, store_fields, s);
     }
 }
 

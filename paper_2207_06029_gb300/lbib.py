@@ -59,6 +59,8 @@ EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_b
            "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_autotune",
            "lbib_device_bytes", "lbib_mesh_measures_noalloc",
+           "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
+           "lbib_batch_destroy", "lbib_batch_last_error",
            "lbib_destroy",
            "lbib_last_error"]
 
@@ -93,12 +95,21 @@ def load():
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_mesh_measures_noalloc.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
+        L.lbib_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp, C.POINTER(C.c_void_p)]
+        L.lbib_batch_step.argtypes = [vp, C.c_int]
+        L.lbib_batch_sync.argtypes = [vp]
+        L.lbib_batch_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.lbib_batch_autotune.argtypes = [vp, C.c_int, ip]
+        L.lbib_batch_destroy.argtypes = [vp]
+        L.lbib_batch_destroy.restype = None
+        L.lbib_batch_last_error.argtypes = [vp]
+        L.lbib_batch_last_error.restype = C.c_char_p
         L.lbib_destroy.argtypes = [vp]
         L.lbib_destroy.restype = None
         L.lbib_last_error.argtypes = [vp]
         L.lbib_last_error.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("lbib_destroy", "lbib_last_error"):
+            if name not in ("lbib_destroy", "lbib_last_error", "lbib_batch_destroy", "lbib_batch_last_error"):
                 getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -359,3 +370,79 @@ def lbib_mesh_measures_noalloc(X, nv, tris, nt, out, stream=None):
     if rc != LBIB_OK:
         raise LbibError(rc, _NOALLOC_MESSAGES.get(rc, "error"))
     return rc
+
+
+# ---- batches ---------------------------------------------------------------------------
+
+def _bcheck(batch, rc):
+    if rc != LBIB_OK:
+        msg = load().lbib_batch_last_error(batch)
+        raise LbibError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lbib_batch_create(ctxs, stream=None):
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    h = C.c_void_p()
+    _bcheck(None, load().lbib_batch_create(arr, len(ctxs), C.c_void_p(stream) if stream else None, C.byref(h)))
+    return h
+
+
+def lbib_batch_step(batch, nsteps):
+    return _bcheck(batch, load().lbib_batch_step(batch, int(nsteps)))
+
+
+def lbib_batch_sync(batch):
+    return _bcheck(batch, load().lbib_batch_sync(batch))
+
+
+def lbib_batch_counters(batch):
+    s, l = C.c_longlong(), C.c_longlong()
+    _bcheck(batch, load().lbib_batch_counters(batch, C.byref(s), C.byref(l)))
+    return s.value, l.value
+
+
+def lbib_batch_autotune(batch, steps):
+    ch = (C.c_int * 2)()
+    _bcheck(batch, load().lbib_batch_autotune(batch, int(steps), ch))
+    return tuple(ch)
+
+
+def lbib_batch_destroy(batch):
+    load().lbib_batch_destroy(batch)
+
+
+def lbib_batch_last_error(batch):
+    m = load().lbib_batch_last_error(batch)
+    return m.decode() if m else ""
+
+
+class Batch:
+    """Several contexts advanced by common launches."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        self.h = lbib_batch_create([c.h for c in self.contexts], stream)
+
+    def step(self, n=1):
+        lbib_batch_step(self.h, n)
+
+    def sync(self):
+        lbib_batch_sync(self.h)
+
+    def autotune(self, steps=5):
+        return lbib_batch_autotune(self.h, steps)
+
+    def counters(self):
+        return lbib_batch_counters(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbib_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
