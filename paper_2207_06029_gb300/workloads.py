@@ -234,6 +234,33 @@ def case_jeffery_spheroid(n=32, tau=0.8, shear_rate=5e-3, axes=(6.0, 3.0, 3.0), 
                 precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), U))
 
 
+def case_batch(count=64, seed=2207, n_range=(48, 112), Ca_range=(0.005, 0.3), Eb_range=(0.0, 0.05),
+               mass_ratios=(0.5, 1.0, 2.0), tau=0.8, wall_speed=0.02, precision=PREC_FP32, steps=2000):
+    """Independent capsule-in-shear cases of uneven sizes: cubic lattices
+    N ~ U{48..112}, capsule radius N/10 (icosphere level 3, 642 markers, up
+    to radius 7; level 4, 2562 markers, above), Ca log-uniform, bending ratio
+    uniform, membrane mass ratio from the given set, z walls moving at
+    -+wall_speed.  Returns the cases and the drawn parameters."""
+    rng = np.random.default_rng(seed)
+    cases, params = [], []
+    for k in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        Ca = float(np.exp(rng.uniform(np.log(Ca_range[0]), np.log(Ca_range[1]))))
+        Eb = float(rng.uniform(*Eb_range))
+        mr = float(rng.choice(mass_ratios))
+        radius = n / 10.0
+        level = 3 if radius <= 7.0 else 4
+        shear_rate = 2.0 * wall_speed / (n - 1)
+        c = (n - 1) / 2.0
+        v, f = icosphere(level, radius, (c, c, c))
+        body = Body(v, f, rigid=False, ks0=ks0_from_capillary(Ca, tau, shear_rate, radius), Eb=Eb, kv=1.0,
+                    density_ratio=mr, ref_radius=radius)
+        cases.append(Case(f"batch_{k}_n{n}", (n, n, n), tau, (PERIODIC, PERIODIC, WALL), shear_walls(wall_speed),
+                          precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), wall_speed)))
+        params.append({"n": n, "Ca": Ca, "Eb": Eb, "mass_ratio": mr, "level": level, "radius": radius})
+    return cases, params
+
+
 def case_settling(nx=160, ny=160, nz=480, tau=0.7, radius=8.0, level=5, Re=5.0, gamma=1.3, steps=50000,
                   precision=PREC_FP32, prolate=False):
     """Rigid sphere (radius 8, 10242 markers) settling along -z in a closed
