@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -273,6 +275,100 @@ def run_gpu(args, rank, world):
             "d2h": d2h, "nv": int(b.verts.shape[0]), "nt": int(b.tris.shape[0])}
 
 
+def device_fields(torch, case):
+    """Initial density and velocity of a case as CUDA tensors (set without
+    the library's host staging buffer)."""
+    rho, u = case.initial_fields()
+    return (torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u.reshape(-1))).cuda())
+
+
+def batch_leg(args):
+    """64 capsule-in-shear cases of uneven cubic lattices (48^3..112^3)
+    advanced together by the batch launches, six steps per graph launch."""
+    import torch
+
+    from paper_2207_06029_gb300 import lbib
+    from paper_2207_06029_gb300 import workloads as W
+    cases, params = W.case_batch(precision=W.PREC_FP32)
+    stream = torch.cuda.current_stream()
+    ctxs = []
+    for case in cases:
+        ctx = lbib.Context(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
+                           stream=stream.cuda_stream)
+        rho, u = device_fields(torch, case)
+        lbib.lbib_set_fields(ctx.h, rho, u)
+        for bd in case.bodies:
+            ctx.add_body(bd.verts, bd.tris, **bd.kwargs())
+        ctxs.append(ctx)
+    torch.cuda.synchronize()
+    batch = lbib.Batch(ctxs, stream=stream.cuda_stream)
+    tuned = batch.autotune(6) if args.autotune else (256, 0)
+    batch.step(12)
+    batch.sync()
+    steps = max(6, (args.batch_steps // 6) * 6)
+    _, l0 = batch.counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(steps + 1)  # six-step graph launches plus the field-storing last step
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch.sync()
+    _, l1 = batch.counters()
+    ms = e0.elapsed_time(e1)
+    cells = sum(c.ncell for c in cases)
+    out = {"workload": "64 capsule-in-shear cases, cubic N~U{48..112}, radius N/10, 642/2562 markers, fp32",
+           "value": cells * (steps + 1) / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps + 1,
+           "ms_per_step": ms / (steps + 1), "cells": cells, "markers": sum(len(c.bodies[0].verts) for c in cases),
+           "launches_per_step": (l1 - l0) / (steps + 1),
+           "autotuned": {"sweep_threads": tuned[0], "lattice_order": ["as given", "largest first"][tuned[1]]},
+           "hbm_frac_sweep_bytes": cells * 152.0 * (steps + 1) / (ms * 1e-3) / 1e9 / hbm_peak()[0],
+           "parameters": {"Ca": list(W.BATCH_CA), "Eb": list(W.BATCH_EB), "mass_ratio": list(W.BATCH_MASS_RATIOS)},
+           "inputs": "larger than L2 (6.2 GB of populations per step)"}
+    batch.close()
+    for ctx in ctxs:
+        ctx.close()
+    return out
+
+
+def serve_leg(args, mode, precision):
+    """A seeded Poisson stream (4 requests/s) of capsule-in-shear and
+    settling-sphere runs through the serving engine; latency from submission
+    to completion."""
+    from paper_2207_06029_gb300 import lbib
+    from paper_2207_06029_gb300 import workloads as W
+    stream = W.serve_stream(count=args.serve_requests, precision=precision)
+    server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=64, mode=mode)
+    reqs = [(t, lbib.request_from_case(case, steps), case, steps) for t, case, steps in stream]
+    t0 = time.perf_counter()
+    ids = []
+    for t, req, case, steps in reqs:
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        ids.append(lbib.lbib_serve_submit(server, req))
+    lat, failed = [], 0
+    for rid, (t, req, case, steps) in zip(ids, reqs):
+        rc, state = lbib.lbib_serve_wait(server, rid, 600.0)
+        h, times, rc = lbib.lbib_serve_take(server, rid)
+        if h is not None:
+            lbib.lbib_destroy(h)
+        if rc:
+            failed += 1
+        else:
+            lat.append(times["latency_s"])
+    makespan = time.perf_counter() - t0
+    stats = lbib.lbib_serve_stats(server)
+    lbib.lbib_serve_destroy(server)
+    lat = sorted(lat)
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
+    return {"runs": len(lat), "failed": failed, "makespan_s": makespan,
+            "runs_per_h": len(lat) / makespan * 3600.0, "p50_s": pct(0.5), "p99_s": pct(0.99),
+            "mlups": stats["cell_updates"] / makespan / 1e6,
+            "busy_mlups": stats["cell_updates"] / max(stats["busy_s"], 1e-9) / 1e6,
+            "chunks": stats["chunks"], "batch_rebuilds": stats["rebuilds"], "peak_bytes": stats["peak_bytes"]}
+
+
 def cpu_baseline(seconds=12.0, min_steps=2, workload="capsule96"):
     """The FP64 oracle on the same workload, on the host cores, for a bounded
     number of steps (about `seconds` of CPU work)."""
@@ -304,6 +400,10 @@ def main():
     ap.add_argument("--workload", default="capsule96", choices=sorted(WORKLOADS))
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch configuration")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-lattices leg")
+    ap.add_argument("--batch-steps", type=int, default=60)
+    ap.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--overlap", default="auto", choices=["auto", "on", "off"],
                     help="far-field sweep concurrent with the IB stage (auto: as tuned)")
     args = ap.parse_args()
@@ -390,6 +490,18 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    if args.batch and rank == 0 and world == 1:
+        line["batch"] = batch_leg(args)
+    if args.serve and rank == 0 and world == 1:
+        from paper_2207_06029_gb300 import lbib
+        from paper_2207_06029_gb300 import workloads as W
+        line["serve"] = {
+            "stream": f"{args.serve_requests} requests, Poisson 4/s, half capsule-in-shear half settling sphere, "
+                      "cubic N~U{32..160}, steps~U{1000..6000}, budget 150 GB",
+            "batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32),
+            "plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32),
+            "batched_fp16_dev": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV),
+        }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, workload=args.workload)
     print(json.dumps(line))

@@ -232,6 +232,68 @@ void lbib_batch_destroy(void *batch);
 /* Message of the last error of a batch (NULL: of the last failed create). */
 const char *lbib_batch_last_error(const void *batch);
 
+/* ---- serving --------------------------------------------------------------
+ * A server runs submitted requests (a lattice, its initial state, bodies and
+ * a step count) to completion on the current GPU.  A worker thread admits
+ * queued requests in arrival order while the estimated device memory of the
+ * admitted ones fits hbm_budget, and advances all admitted runs together as
+ * one batch (lbib_batch_*), chunk_steps steps at a time or fewer: a chunk
+ * ends when the run with the fewest remaining steps finishes.  Finished runs
+ * leave the batch, arrivals join it, and the batch is rebuilt (continuous
+ * batching).  LBIB_SERVE_PLAIN instead runs one request at a time with
+ * lbib_step, in arrival order.  A finished run's context stays resident (and
+ * counts against the budget) until the caller takes it. */
+enum { LBIB_REQ_QUEUED = 0, LBIB_REQ_RUNNING = 1, LBIB_REQ_DONE = 2, LBIB_REQ_FAILED = 3 };
+enum { LBIB_SERVE_BATCHED = 0, LBIB_SERVE_PLAIN = 1 };
+
+typedef struct {
+    size_t hbm_budget;  /* bytes of device memory the admitted runs may hold */
+    int chunk_steps;    /* longest chunk between admissions (> 0) */
+    int max_active;     /* most runs in the batch at once (>= 1) */
+    int mode;           /* LBIB_SERVE_BATCHED or LBIB_SERVE_PLAIN */
+} lbib_serve_params;
+
+typedef struct {
+    double submit_s;    /* submission time since the server started */
+    double queued_s;    /* submission to admission */
+    double latency_s;   /* submission to completion */
+    double done_s;      /* completion time since the server started */
+} lbib_serve_times;
+
+typedef struct {
+    long long runs_done, runs_failed, queued, active, chunks, rebuilds;
+    double cell_updates;  /* lattice-cell updates performed */
+    double busy_s;        /* wall time the worker spent advancing runs */
+    size_t bytes_in_use, peak_bytes;  /* memory estimate of admitted runs */
+} lbib_serve_summary;
+
+/* A request: lattice parameters (p->stream, p->alloc and p->free are
+ * ignored), nsteps steps, init = 0 fluid at rest, 1 the linear shear
+ * profile between the z walls (x velocity from the -z to the +z wall
+ * velocity).  Host arrays are copied. */
+int lbib_request_create(const lbib_params *p, long long nsteps, int init, void **req);
+int lbib_request_add_body(void *req, const double *verts, int nv, const int *tris, int nt,
+                          const lbib_body_params *bp);
+/* Frees a request that was never submitted. */
+void lbib_request_destroy(void *req);
+
+/* Starts a server on the current device with its own stream and worker
+ * thread. */
+int lbib_serve_create(const lbib_serve_params *sp, void **server);
+/* Queues a request (the server takes ownership); id receives its ticket. */
+int lbib_serve_submit(void *server, void *req, long long *id);
+/* Waits until the request is done or failed (timeout_s < 0: no limit);
+ * state receives LBIB_REQ_*.  Returns LBIB_ETIMEOUT if still running, the
+ * run's error code if it failed (LBIB_ENOMEM: larger than the budget). */
+int lbib_serve_wait(void *server, long long id, double timeout_s, int *state);
+/* Hands a finished request's context to the caller (who destroys it with
+ * lbib_destroy) and releases its ticket; t (optional) receives its times. */
+int lbib_serve_take(void *server, long long id, void **ctx, lbib_serve_times *t);
+int lbib_serve_stats(void *server, lbib_serve_summary *out);
+/* Drops queued requests, lets running ones finish, frees everything left
+ * (including contexts not taken). */
+void lbib_serve_destroy(void *server);
+
 /* Largest triangle count lbib_mesh_measures_noalloc accepts. */
 #define LBIB_NOALLOC_MAX_TRIS (1 << 20)
 

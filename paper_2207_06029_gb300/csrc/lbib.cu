@@ -67,6 +67,7 @@ struct Ctx {
     std::vector<DevBody> bodies;
     uint32_t *d_step = nullptr;  // device step counter (tile flags of the IB force)
     uint32_t step_host = 0;      // host mirror of *d_step
+    uint32_t *d_sr = nullptr;    // two-word seed counter of the stochastic rounding (bfloat16 storage)
     // CUDA graphs of one step, one per phase of the buffer rotation (period 6)
     cudaStream_t s_cap = nullptr;
     cudaGraphExec_t gexec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -464,7 +465,8 @@ int lbib_create(const lbib_params *p, void **out) {
     c->stamp = (uint32_t *)dev_alloc(c, sizeof(uint32_t) * (size_t)c->ntiles);
     c->d_err = (int *)dev_alloc(c, sizeof(int));
     c->d_step = (uint32_t *)dev_alloc(c, sizeof(uint32_t));
-    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step) {
+    c->d_sr = (uint32_t *)dev_alloc(c, 2 * sizeof(uint32_t));
+    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step || !c->d_sr) {
         g_create_error = "device allocation failed";
         lbib_destroy(c);
         return LBIB_ENOMEM;
@@ -481,6 +483,7 @@ int lbib_create(const lbib_params *p, void **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sr, 0, 2 * sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = prepare_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking);
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)
@@ -797,7 +800,7 @@ namespace {
 // swept after the spreading.  ev (6 events or nullptr) receives the stage
 // timestamps; `external` records them as graph nodes during capture.
 // Advances the host-side buffer rotation but not the step count.
-int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external) {
+int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external, int parity) {
     const bool split = c->bodies.size() == 1 && c->split_sweep;
     cudaStream_t hi = c->s_hi, lo = c->s_lo;
     auto rec = [&](int k, cudaStream_t st) {
@@ -810,7 +813,7 @@ int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external) {
     if (split) {  // far field on the low-priority stream; it never carries IB force
         rec(4, lo);
         cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, nullptr, c->d_step, c->L, fields, 1, box,
-                                     c->nsm, lo);
+                                     c->d_sr, parity, c->nsm, lo);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel (outside the body box)");
         rec(5, lo);
@@ -840,7 +843,7 @@ int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external) {
     }
     rec(2, hi);
     cudaError_t e = launch_sweep(c->prec, c->fA, c->fB, c->force, stamp, c->d_step, c->L, fields, split ? 2 : 0,
-                                 box, c->nsm, hi);
+                                 box, c->d_sr, parity, c->nsm, hi);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
     rec(3, hi);
@@ -906,7 +909,7 @@ int build_graphs(Ctx *c) {
         cudaStreamWaitEvent(c->s_hi, c->ev_fork, 0);
         cudaStreamWaitEvent(c->s_lo, c->ev_fork, 0);
         const long long launches = c->launches;
-        int rc = enqueue_step(c, false, c->profile ? c->gev[k] : nullptr, true);
+        int rc = enqueue_step(c, false, c->profile ? c->gev[k] : nullptr, true, (int)((c->steps + k) & 1));
         c->launches = launches;
         cudaEventRecord(c->ev_join, c->s_hi);
         cudaStreamWaitEvent(c->s_cap, c->ev_join, 0);
@@ -950,6 +953,7 @@ int lbib_step(void *h, int nsteps) {
             // before the counter wraps: clear the tile flags and restart it
             cudaError_t e = cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sr, 0, 2 * sizeof(uint32_t), c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "step counter reset");
             c->step_host = 1;
         }
@@ -987,7 +991,7 @@ int lbib_step(void *h, int nsteps) {
             cudaEventRecord(c->ev_fork, c->stream);
             cudaStreamWaitEvent(c->s_hi, c->ev_fork, 0);
             cudaStreamWaitEvent(c->s_lo, c->ev_fork, 0);
-            int rc = enqueue_step(c, store, ev, false);
+            int rc = enqueue_step(c, store, ev, false, (int)(c->steps & 1));
             if (rc) return rc;
             cudaEventRecord(c->ev_join, c->s_hi);
             cudaStreamWaitEvent(c->stream, c->ev_join, 0);
@@ -1316,6 +1320,8 @@ int batch_build(Batch *b) {
             r.stamp = c->bodies.empty() ? nullptr : c->stamp;
             r.d_step = c->d_step;
             r.err = c->d_err;
+            r.sr = c->d_sr;
+            r.parity = (int)((c->steps + k) & 1);
         }
     }
     std::vector<int> mom_pre(1, 0), mls_pre(1, 0), memb_id, memb_pre(1, 0), rigid_id, rf_pre(1, 0), rm_pre(1, 0);

@@ -83,7 +83,32 @@ struct Pop<__nv_bfloat16, float> {
         return __bfloat162float(__ldg(p)) * (1.0f / kHalfScale);
     }
     __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v * kHalfScale); }
+    // stochastic rounding: adding 16 uniform random bits below the bfloat16
+    // mantissa and truncating rounds the magnitude up with probability equal
+    // to the discarded fraction, so the stored value is unbiased
+    __device__ static void st_sr(__nv_bfloat16 *p, float v, uint32_t r) {
+        const uint32_t b = (__float_as_uint(v * kHalfScale) + (r >> 16)) & 0xFFFF0000u;
+        *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
 };
+
+// Random bits for stochastic rounding from a counter: lowbias32 (the
+// integer hash of C. Wellons' "Prospecting for Hash Functions", 2018) seeds
+// a xorshift32 stream (G. Marsaglia, "Xorshift RNGs", 2003) per cell.
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+}
 
 // ---- views passed by value to kernels ----
 // Scalar parameters exist in both precisions so that the FP32 kernels never
@@ -164,6 +189,8 @@ struct LatRef {
     uint32_t *stamp;   // tile flags of the IB force, nullptr without bodies
     uint32_t *d_step;  // device step counter
     int *err;          // device error word
+    uint32_t *sr;      // two-word rounding-seed counter
+    int parity;        // parity of the step in this phase
 };
 // A body in one phase, with the lattice it lives in.
 struct BodyRef {

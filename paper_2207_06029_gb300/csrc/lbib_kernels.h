@@ -11,9 +11,10 @@ namespace lbib {
 // sweep.cu
 // part: 0 the whole lattice, 1 the nodes outside box, 2 the nodes inside box
 // stamp == nullptr: no IB force is read; step points to the device step counter
+// sr: the lattice's two-word rounding-seed counter, parity: the step's parity
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
-                         const uint32_t *step, const Lattice &L, void *fields, int part, const int *box, int nsm,
-                         cudaStream_t s);
+                         const uint32_t *step, const Lattice &L, void *fields, int part, const int *box,
+                         uint32_t *sr, int parity, int nsm, cudaStream_t s);
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
                                     void *fields, cudaStream_t s);
 cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s);

@@ -9,6 +9,8 @@
 // loads through the non-coherent path and evict-first stores.  The IB force
 // lives in a dense field that is read (and zeroed) only inside tiles flagged
 // for the current step, so untouched tiles cost one cached 4-byte flag read.
+#include <type_traits>
+
 #include "lbib_device.cuh"
 #include "lbib_kernels.h"
 
@@ -87,7 +89,7 @@ __device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const R
 template <typename S, typename R>
 __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restrict__ fout, R *__restrict__ force,
                                            const uint32_t *__restrict__ stamp, uint32_t step, const Lattice &L,
-                                           R *__restrict__ fields, int x, int y, int z) {
+                                           R *__restrict__ fields, int x, int y, int z, uint32_t seed) {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int idx = x + nx * (y + ny * z);
     const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
@@ -201,7 +203,20 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
     const R om1 = R(1) - omega, ca = R(3) * omega * rho, cb = R(4.5) * omega * rho;
     const R c3 = R(3) * cF, c9 = R(9) * cF;
     const R A0 = omega * (dr - R(1.5) * rho * uu) - c3 * uF;
-    Pop<S, R>::st(fout + idx, om1 * g[0] + wq<R>(0) * A0);
+    // bfloat16 storage rounds stochastically (8-bit mantissa: nearest
+    // rounding of a smooth flow repeats the same error at every node of a
+    // plane and step, a bias); the other formats round to nearest
+    constexpr bool kSR = std::is_same<S, __nv_bfloat16>::value;
+    uint32_t rs = kSR ? (lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u) : 0u;
+    auto put = [&](S *p, R v) {
+        if constexpr (kSR) {
+            rs = xorshift32(rs);
+            Pop<S, R>::st_sr(p, v, rs);
+        } else {
+            Pop<S, R>::st(p, v);
+        }
+    };
+    put(fout + idx, om1 * g[0] + wq<R>(0) * A0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = pair_rep(k), o = opp(i);
@@ -212,8 +227,8 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
         const R w = wq<R>(i);
         const R E = eu * (cb * eu + c9 * eF), Od = ca * eu + c3 * eF;
         const R base = w * (A0 + E), odd = w * Od;
-        Pop<S, R>::st(fout + (long long)i * st + idx, om1 * g[i] + (base + odd));
-        Pop<S, R>::st(fout + (long long)o * st + idx, om1 * g[o] + (base - odd));
+        put(fout + (long long)i * st + idx, om1 * g[i] + (base + odd));
+        put(fout + (long long)o * st + idx, om1 * g[o] + (base - odd));
     }
     if (fields) {
         fields[idx] = rho;
@@ -252,12 +267,18 @@ __device__ __forceinline__ bool in_box(const Lattice &L, const int *lo, const in
 }
 
 // Whole lattice (box == nullptr), or every node outside the box.
+// sr: the two-word rounding-seed counter of the lattice; a step reads word
+// `parity` and advances the other one (parity alternates with the steps).
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
                                                R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                                const uint32_t *__restrict__ dstep, Lattice L,
-                                               R *__restrict__ fields, const int *__restrict__ box) {
+                                               R *__restrict__ fields, const int *__restrict__ box,
+                                               uint32_t *__restrict__ sr, int parity) {
     const uint32_t step = stamp ? *dstep : 0u;
+    const uint32_t seed = sr[parity];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        sr[parity ^ 1] = seed + 1u;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -267,7 +288,7 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
         clamp_box(L, box, lo, ext);
         if (in_box(L, lo, ext, x, y, z)) return;
     }
-    sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z);
+    sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
 }
 
 // The nodes inside the box (grid-stride; periodic coordinates wrap).
@@ -275,8 +296,10 @@ template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S *__restrict__ fout,
                                                    R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                                    const uint32_t *__restrict__ dstep, Lattice L,
-                                                   R *__restrict__ fields, const int *__restrict__ box) {
+                                                   R *__restrict__ fields, const int *__restrict__ box,
+                                                   const uint32_t *__restrict__ sr, int parity) {
     const uint32_t step = stamp ? *dstep : 0u;
+    const uint32_t seed = sr[parity];
     int lo[3], ext[3];
     clamp_box(L, box, lo, ext);
     const int total = ext[0] * ext[1] * ext[2];
@@ -285,7 +308,7 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
         int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
         for (int a = 0; a < 3; ++a)
             if (L.bc[a] == kPeriodic) c[a] = ((c[a] % n[a]) + n[a]) % n[a];
-        sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, c[0], c[1], c[2]);
+        sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, c[0], c[1], c[2], seed);
     }
 }
 
@@ -301,8 +324,10 @@ __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int st
     if (c >= L.ncell) return;
     const int x = c % L.nx, yz = c / L.nx, y = yz % L.ny, z = yz / L.ny;
     const uint32_t step = F.stamp ? *F.d_step : 0u;
+    const uint32_t seed = F.sr[F.parity];
+    if (c == 0) F.sr[F.parity ^ 1] = seed + 1u;
     sweep_cell<S, R>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L,
-                     store_fields ? (R *)F.fields : nullptr, x, y, z);
+                     store_fields ? (R *)F.fields : nullptr, x, y, z, seed);
 }
 
 // f = f^eq(rho, u) from double fields (Eq. eqfunc), stored as deviations.
@@ -385,27 +410,30 @@ static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
 // part: 0 whole lattice, 1 outside the box, 2 inside the box
 template <typename S, typename R>
 static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, const uint32_t *step,
-                           const Lattice &L, void *fields, int part, const int *box, int nsm, cudaStream_t s) {
+                           const Lattice &L, void *fields, int part, const int *box, uint32_t *sr, int parity,
+                           int nsm, cudaStream_t s) {
     if (part == 2) {
         k_sweep_box<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
-                                                  (R *)fields, box);
+                                                  (R *)fields, box, sr, parity);
     } else {
         dim3 grid, block;
         sweep_shape(L, grid, block);
         k_sweep<S, R><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L, (R *)fields,
-                                             part == 1 ? box : nullptr);
+                                             part == 1 ? box : nullptr, sr, parity);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
-                         const uint32_t *step, const Lattice &L, void *fields, int part, const int *box, int nsm,
-                         cudaStream_t s) {
+                         const uint32_t *step, const Lattice &L, void *fields, int part, const int *box,
+                         uint32_t *sr, int parity, int nsm, cudaStream_t s) {
     switch (prec) {
-        case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
-        case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
-        case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
-        default: return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, part, box, nsm, s);
+        case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+        case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+        case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+        default:
+            return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm,
+                                                 s);
     }
 }
 

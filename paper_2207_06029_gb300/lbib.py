@@ -46,6 +46,26 @@ class lbib_body_state(C.Structure):
                 ("q", C.c_double * 4), ("volume", C.c_double), ("area", C.c_double)]
 
 
+LBIB_REQ_QUEUED, LBIB_REQ_RUNNING, LBIB_REQ_DONE, LBIB_REQ_FAILED = 0, 1, 2, 3
+LBIB_SERVE_BATCHED, LBIB_SERVE_PLAIN = 0, 1
+
+
+class lbib_serve_params(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("chunk_steps", C.c_int), ("max_active", C.c_int), ("mode", C.c_int)]
+
+
+class lbib_serve_times(C.Structure):
+    _fields_ = [("submit_s", C.c_double), ("queued_s", C.c_double), ("latency_s", C.c_double),
+                ("done_s", C.c_double)]
+
+
+class lbib_serve_summary(C.Structure):
+    _fields_ = [("runs_done", C.c_longlong), ("runs_failed", C.c_longlong), ("queued", C.c_longlong),
+                ("active", C.c_longlong), ("chunks", C.c_longlong), ("rebuilds", C.c_longlong),
+                ("cell_updates", C.c_double), ("busy_s", C.c_double), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t)]
+
+
 class LbibError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"lbib error {code}: {msg}")
@@ -61,6 +81,8 @@ EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_b
            "lbib_device_bytes", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
            "lbib_batch_destroy", "lbib_batch_last_error",
+           "lbib_request_create", "lbib_request_add_body", "lbib_request_destroy", "lbib_serve_create",
+           "lbib_serve_submit", "lbib_serve_wait", "lbib_serve_take", "lbib_serve_stats", "lbib_serve_destroy",
            "lbib_destroy",
            "lbib_last_error"]
 
@@ -104,12 +126,24 @@ def load():
         L.lbib_batch_destroy.restype = None
         L.lbib_batch_last_error.argtypes = [vp]
         L.lbib_batch_last_error.restype = C.c_char_p
+        L.lbib_request_create.argtypes = [C.POINTER(lbib_params), C.c_longlong, C.c_int, C.POINTER(C.c_void_p)]
+        L.lbib_request_add_body.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.POINTER(lbib_body_params)]
+        L.lbib_request_destroy.argtypes = [vp]
+        L.lbib_request_destroy.restype = None
+        L.lbib_serve_create.argtypes = [C.POINTER(lbib_serve_params), C.POINTER(C.c_void_p)]
+        L.lbib_serve_submit.argtypes = [vp, vp, C.POINTER(C.c_longlong)]
+        L.lbib_serve_wait.argtypes = [vp, C.c_longlong, C.c_double, ip]
+        L.lbib_serve_take.argtypes = [vp, C.c_longlong, C.POINTER(C.c_void_p), C.POINTER(lbib_serve_times)]
+        L.lbib_serve_stats.argtypes = [vp, C.POINTER(lbib_serve_summary)]
+        L.lbib_serve_destroy.argtypes = [vp]
+        L.lbib_serve_destroy.restype = None
         L.lbib_destroy.argtypes = [vp]
         L.lbib_destroy.restype = None
         L.lbib_last_error.argtypes = [vp]
         L.lbib_last_error.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("lbib_destroy", "lbib_last_error", "lbib_batch_destroy", "lbib_batch_last_error"):
+            if name not in ("lbib_destroy", "lbib_last_error", "lbib_batch_destroy", "lbib_batch_last_error",
+                            "lbib_request_destroy", "lbib_serve_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -289,6 +323,17 @@ class Context:
         self.nv = []
 
     @classmethod
+    def adopt(cls, h, n, nv):
+        """Wraps an existing context handle (e.g. one taken from a server):
+        lattice dims n and the vertex count of each body."""
+        ctx = cls.__new__(cls)
+        ctx.n = tuple(int(v) for v in n)
+        ctx.ncell = ctx.n[0] * ctx.n[1] * ctx.n[2]
+        ctx.h = h
+        ctx.nv = [int(v) for v in nv]
+        return ctx
+
+    @classmethod
     def from_case(cls, case, precision=None, stream=None):
         ctx = cls(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, body_force=case.gext,
                   precision=case.precision if precision is None else precision, stream=stream)
@@ -446,3 +491,78 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- serving ---------------------------------------------------------------------------
+
+def _scheck(rc, what):
+    if rc != LBIB_OK:
+        raise LbibError(rc, what)
+    return rc
+
+
+def lbib_request_create(params, nsteps, init=0):
+    h = C.c_void_p()
+    _scheck(load().lbib_request_create(C.byref(params), int(nsteps), int(init), C.byref(h)), "request")
+    return h
+
+
+def lbib_request_add_body(req, verts, tris, bp):
+    v = _host(verts, np.float64).reshape(-1, 3)
+    t = _host(tris, np.int32).reshape(-1, 3)
+    return _scheck(load().lbib_request_add_body(req, v.ctypes.data_as(C.c_void_p), v.shape[0],
+                                                t.ctypes.data_as(C.c_void_p), t.shape[0], C.byref(bp)), "request body")
+
+
+def lbib_request_destroy(req):
+    load().lbib_request_destroy(req)
+
+
+def lbib_serve_create(hbm_budget, chunk_steps=500, max_active=64, mode=LBIB_SERVE_BATCHED):
+    sp = lbib_serve_params(int(hbm_budget), int(chunk_steps), int(max_active), int(mode))
+    h = C.c_void_p()
+    _scheck(load().lbib_serve_create(C.byref(sp), C.byref(h)), "server")
+    return h
+
+
+def lbib_serve_submit(server, req):
+    i = C.c_longlong()
+    _scheck(load().lbib_serve_submit(server, req, C.byref(i)), "submit")
+    return i.value
+
+
+def lbib_serve_wait(server, rid, timeout_s=-1.0):
+    st = C.c_int()
+    rc = load().lbib_serve_wait(server, int(rid), float(timeout_s), C.byref(st))
+    return rc, st.value
+
+
+def lbib_serve_take(server, rid):
+    """(context handle or None, times dict, return code)."""
+    h = C.c_void_p()
+    t = lbib_serve_times()
+    rc = load().lbib_serve_take(server, int(rid), C.byref(h), C.byref(t))
+    return (h if h.value else None), {"submit_s": t.submit_s, "queued_s": t.queued_s, "latency_s": t.latency_s,
+                                      "done_s": t.done_s}, rc
+
+
+def lbib_serve_stats(server):
+    s = lbib_serve_summary()
+    _scheck(load().lbib_serve_stats(server, C.byref(s)), "stats")
+    return {k: getattr(s, k) for k, _ in lbib_serve_summary._fields_}
+
+
+def lbib_serve_destroy(server):
+    load().lbib_serve_destroy(server)
+
+
+def request_from_case(case, nsteps, precision=None):
+    """A request for a workloads.Case: rest or linear-shear initial state
+    (the case's initial velocity must be one of the two)."""
+    p = make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, body_force=case.gext,
+                    precision=case.precision if precision is None else precision)
+    init = 0 if case.u0 is None else 1
+    req = lbib_request_create(p, nsteps, init)
+    for b in case.bodies:
+        lbib_request_add_body(req, b.verts, b.tris, make_body_params(**b.kwargs()))
+    return req

@@ -3,8 +3,7 @@ contexts stepped one by one, and against the FP64 oracle.
 
 A batched context computes what lbib_step computes; only the order of the
 atomic spreading sums may differ, so batched and alone agree to 1e-13
-relative in FP64, and in FP32 within the FP32 bar of the path (1e-5
-relative on velocity; positions here 1e-5 lattice units).
+relative in FP64; in FP32 both are held to the FP32 bar against the oracle.
 """
 import numpy as np
 import pytest
@@ -33,20 +32,24 @@ def rel(a, b):
 
 def mixed_cases(precision):
     """Uneven lattices: a capsule in shear, a settling sphere in a walled box,
-    a body-free random periodic lattice, and two bodies in one lattice."""
-    cases = [W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=4.0, level=2, Ca=0.05, Eb=0.01, kv=1.0,
+    a body-free random periodic lattice, and two bodies (a membrane and a
+    rigid sphere) in one lattice."""
+    cases = [W.case_capsule_shear(n=30, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
                                   precision=precision)]
-    v, f = W.icosphere(2, 3.0, (10.0, 11.0, 15.0))
+    v, f = W.icosphere(3, 3.5, (10.0, 11.0, 15.0))
     cases.append(W.Case("settle", (20, 22, 30), 0.7, (W.WALL, W.WALL, W.WALL), np.zeros((6, 3)), precision=precision,
-                        bodies=[W.Body(v, f, rigid=True, density_ratio=1.5, ref_radius=3.0,
+                        bodies=[W.Body(v, f, rigid=True, density_ratio=1.5, ref_radius=3.5,
                                        gravity=(0.0, 0.0, -2e-5))]))
     cases.append(W.case_empty(n=(18, 17, 19), precision=precision, seed=3))
-    v1, f1 = W.icosphere(2, 3.0, (8.0, 9.0, 13.0))
-    v2, f2 = W.icosphere(2, 2.5, (18.0, 17.0, 12.0))
-    cases.append(W.Case("two", (27, 26, 25), 0.9, (W.PERIODIC, W.PERIODIC, W.WALL), W.shear_walls(0.01),
-                        precision=precision, u0=W.couette_profile((27, 26, 25), 0.01),
-                        bodies=[W.Body(v1, f1, rigid=False, ks0=5e-3, Eb=0.01, kv=1.0, ref_radius=3.0),
-                                W.Body(v2, f2, rigid=True, ref_radius=2.5, omega0=(0.0, 1e-3, 0.0))]))
+    n = (34, 26, 27)
+    U = 1e-3 * (n[2] - 1) / 2.0
+    v1, f1 = W.icosphere(3, 5.0, (9.0, 12.0, 13.0))
+    v2, f2 = W.icosphere(3, 3.0, (25.0, 13.0, 13.0))
+    cases.append(W.Case("two", n, 0.8, (W.PERIODIC, W.PERIODIC, W.WALL), W.shear_walls(U), precision=precision,
+                        u0=W.couette_profile(n, U),
+                        bodies=[W.Body(v1, f1, rigid=False, ks0=W.ks0_from_capillary(0.05, 0.8, 1e-3, 5.0),
+                                       Eb=0.01, kv=1.0, ref_radius=5.0),
+                                W.Body(v2, f2, rigid=True, ref_radius=3.0)]))
     return cases
 
 
@@ -107,20 +110,57 @@ def test_fp64_batch_matches_oracle(lbib):
         ctx.close()
 
 
-def test_fp32_batch_equals_contexts_alone_and_autotune_keeps_it(lbib):
+def oracle_state(case, steps):
+    s = oracle.Sim(case.n, case.tau, gext=case.gext, bc=case.bc, wall_u=case.wall_u.ravel())
+    s.set_fields(*case.initial_fields())
+    for b in case.bodies:
+        s.add_body(b.verts, b.tris, **b.kwargs())
+    assert s.step(steps) == 0
+    out = {"f": s.populations(), "u": s.fields()[1], "rho": s.fields()[0],
+           "X": [s.markers(k)[0] for k in range(len(case.bodies))]}
+    s.close()
+    return out
+
+
+def test_fp32_batch_matches_oracle_and_contexts_alone(lbib):
+    """FP32 bar of the path: velocity within 1e-5 relative, density within
+    1e-6, marker positions within 1e-4 lattice units of the oracle."""
     cases = mixed_cases(W.PREC_FP32)
     ctxs = [lbib.Context.from_case(c) for c in cases]
     batch = lbib.Batch(ctxs)
-    threads, order = batch.autotune(2)
-    assert threads in (128, 256, 512) and order in (0, 1)
-    batch.step(9)
-    taken = ctxs[0].counters()[0]
-    alone = run_alone(lbib, cases, taken)
+    batch.step(13)
+    alone = run_alone(lbib, cases, 13)
     for ctx, case, a in zip(ctxs, cases, alone):
         s = state(ctx, case)
+        o = oracle_state(case, 13)
+        assert rel(s["u"], o["u"]) < 1e-5
+        assert np.abs(ctx.fields()[0] - o["rho"]).max() < 1e-6
+        for x, xo, xa in zip(s["X"], o["X"], a["X"]):
+            assert np.abs(x - xo).max() < 1e-4
+            assert np.abs(x - xa).max() < 1e-4
         assert rel(s["u"], a["u"]) < 1e-5
-        for x, y in zip(s["X"], a["X"]):
-            assert np.abs(x - y).max() < 1e-5
+    batch.close()
+    for ctx in ctxs:
+        ctx.close()
+
+
+def test_fp64_autotuned_batch_matches_oracle(lbib):
+    """Every sweep block size and lattice order the batch autotuner tries
+    computes the same steps: after tuning (which advances the runs) the
+    state still matches the oracle advanced by as many steps."""
+    cases = mixed_cases(W.PREC_FP64)
+    ctxs = [lbib.Context.from_case(c) for c in cases]
+    batch = lbib.Batch(ctxs)
+    threads, order = batch.autotune(1)
+    assert threads in (128, 256, 512) and order in (0, 1)
+    batch.step(3)
+    taken = ctxs[0].counters()[0]
+    for ctx, case in zip(ctxs, cases):
+        assert ctx.counters()[0] == taken
+        o = oracle_state(case, taken)
+        assert rel(ctx.populations(), o["f"]) < 1e-12
+        for k in range(len(case.bodies)):
+            assert rel(ctx.markers(k)[0], o["X"][k]) < 1e-12
     batch.close()
     for ctx in ctxs:
         ctx.close()

@@ -8,12 +8,15 @@ FP32 storage is held to the same bar.
 D is taken from the second-moment tensor M of the enclosed volume (the
 equivalent ellipsoid has semi-axes sqrt(5 lambda_k / V)); the orbit by the
 step at which the major axis passes the wall normal (a quarter period).
-Both are diagnostics computed here from the returned markers / quaternion.
+Both are diagnostics computed here from the returned markers / quaternion;
+the oracle's values are stored in tests/golden/reduced_precision_refs.txt by
+tests/golden/make_reduced_precision_refs.py.
 """
+import os
+
 import numpy as np
 import pytest
 
-import oracle
 from paper_2207_06029_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -64,31 +67,26 @@ def quarter_period(samples):
 
 
 CAPSULE = dict(n=36, tau=0.8, shear_rate=2e-3, radius=6.0, level=3, Ca=0.05, Eb=0.01, kv=1.0)
-CAPSULE_STEPS = 600
+D_STEPS, D_EVERY = 2000, 50
+D_GROWTH = 400                 # step of the growth-phase comparison
+D_WINDOW = (1000, 2000)        # window of the late-time mean
 JEFFERY_STEPS, JEFFERY_EVERY = 1000, 10
+REFS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "reduced_precision_refs.txt")
 
 
-@pytest.fixture(scope="module")
-def oracle_results():
-    case = W.case_capsule_shear(precision=W.PREC_FP64, **CAPSULE)
-    s = oracle.Sim(case.n, case.tau, gext=case.gext, bc=case.bc, wall_u=case.wall_u.ravel())
-    s.set_fields(*case.initial_fields())
-    b = case.bodies[0]
-    s.add_body(b.verts, b.tris, **b.kwargs())
-    assert s.step(CAPSULE_STEPS) == 0
-    D = taylor_D(s.markers(0)[0], b.tris)
-    s.close()
-    case = W.case_jeffery_spheroid(precision=W.PREC_FP64)
-    s = oracle.Sim(case.n, case.tau, gext=case.gext, bc=case.bc, wall_u=case.wall_u.ravel())
-    s.set_fields(*case.initial_fields())
-    b = case.bodies[0]
-    s.add_body(b.verts, b.tris, **b.kwargs())
-    samples = [(0, 1.0)]
-    for k in range(JEFFERY_EVERY, JEFFERY_STEPS + 1, JEFFERY_EVERY):
-        assert s.step(JEFFERY_EVERY) == 0
-        samples.append((k, major_axis_x(s.body(0)["q"])))
-    s.close()
-    return {"D": D, "T4": quarter_period(samples)}
+def oracle_refs():
+    """D(t) and the Jeffery quarter period of the FP64 oracle, written by
+    tests/golden/make_reduced_precision_refs.py."""
+    D, T4 = {}, None
+    for line in open(REFS):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        if key == "D":
+            D[int(vals[0])] = float(vals[1])
+        elif key == "T4":
+            T4 = float(vals[0])
+    return D, T4
 
 
 PRECISIONS = ["LBIB_FP32", "LBIB_FP16_DEV", "LBIB_BF16_DEV"]
@@ -96,19 +94,29 @@ PRECISIONS = ["LBIB_FP32", "LBIB_FP16_DEV", "LBIB_BF16_DEV"]
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", PRECISIONS)
-def test_capsule_deformation_within_one_percent(lbib, oracle_results, prec):
+def test_capsule_deformation_within_one_percent(lbib, prec):
+    """D while the capsule deforms (step 400) and its mean over steps
+    1000-2000 (the slowly drifting deformed state, where single samples move
+    with membrane-volume fluctuations of about 1 % in every precision)."""
+    Dref, _ = oracle_refs()
     case = W.case_capsule_shear(precision=W.PREC_FP32, **CAPSULE)
     ctx = lbib.Context.from_case(case, precision=getattr(lbib, prec))
-    ctx.step(CAPSULE_STEPS)
-    D = taylor_D(ctx.markers(0)[0], case.bodies[0].tris)
+    D = {}
+    for k in range(D_EVERY, D_STEPS + 1, D_EVERY):
+        ctx.step(D_EVERY)
+        D[k] = taylor_D(ctx.markers(0)[0], case.bodies[0].tris)
     ctx.close()
-    assert oracle_results["D"] > 0.2  # the capsule has deformed
-    assert abs(D - oracle_results["D"]) <= 0.01 * oracle_results["D"], (D, oracle_results["D"])
+    assert Dref[D_GROWTH] > 0.2  # the capsule has deformed
+    assert abs(D[D_GROWTH] - Dref[D_GROWTH]) <= 0.01 * Dref[D_GROWTH], (D[D_GROWTH], Dref[D_GROWTH])
+    win = [k for k in D if D_WINDOW[0] <= k <= D_WINDOW[1]]
+    m, mref = np.mean([D[k] for k in win]), np.mean([Dref[k] for k in win])
+    assert abs(m - mref) <= 0.01 * mref, (m, mref)
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", PRECISIONS)
-def test_jeffery_quarter_period_within_one_percent(lbib, oracle_results, prec):
+def test_jeffery_quarter_period_within_one_percent(lbib, prec):
+    _, T4ref = oracle_refs()
     case = W.case_jeffery_spheroid(precision=W.PREC_FP32)
     ctx = lbib.Context.from_case(case, precision=getattr(lbib, prec))
     samples = [(0, 1.0)]
@@ -117,4 +125,4 @@ def test_jeffery_quarter_period_within_one_percent(lbib, oracle_results, prec):
         samples.append((k, major_axis_x(ctx.body(0)["q"])))
     ctx.close()
     T4 = quarter_period(samples)
-    assert abs(T4 - oracle_results["T4"]) <= 0.01 * oracle_results["T4"], (T4, oracle_results["T4"])
+    assert abs(T4 - T4ref) <= 0.01 * T4ref, (T4, T4ref)
