@@ -347,14 +347,14 @@ def serve_leg(args, mode, precision):
         if t > now:
             time.sleep(t - now)
         ids.append(lbib.lbib_serve_submit(server, req))
-    lat, failed = [], 0
+    lat, failed = [], []
     for rid, (t, req, case, steps) in zip(ids, reqs):
         rc, state = lbib.lbib_serve_wait(server, rid, 600.0)
         h, times, rc = lbib.lbib_serve_take(server, rid)
         if h is not None:
             lbib.lbib_destroy(h)
         if rc:
-            failed += 1
+            failed.append({"request": case.name, "steps": steps, "code": rc})
         else:
             lat.append(times["latency_s"])
     makespan = time.perf_counter() - t0

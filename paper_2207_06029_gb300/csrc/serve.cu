@@ -199,8 +199,10 @@ void worker_loop(Server *s) {
         for (Request *r : act) chunk = std::min(chunk, r->remaining);
         const auto t_a = Clock::now();
         int brc = LBIB_OK;
+        bool advanced = false;  // the chunk's steps were enqueued for every run
         if (s->sp.mode == LBIB_SERVE_PLAIN) {
             brc = lbib_step(act[0]->ctx, (int)chunk);
+            advanced = brc == LBIB_OK;
             if (!brc) brc = lbib_sync(act[0]->ctx);
         } else {
             if (stale || act != members) {
@@ -213,7 +215,10 @@ void worker_loop(Server *s) {
                 stale = false;
                 ++s->rebuilds;
             }
-            if (!brc) brc = lbib_batch_step(batch, (int)chunk);
+            if (!brc) {
+                brc = lbib_batch_step(batch, (int)chunk);
+                advanced = brc == LBIB_OK;
+            }
             if (!brc) brc = lbib_batch_sync(batch);
         }
         const auto t_b = Clock::now();
@@ -229,7 +234,7 @@ void worker_loop(Server *s) {
                 stale = true;
                 continue;
             }
-            if (!brc) {
+            if (advanced) {
                 r->remaining -= chunk;
                 s->cell_updates += (double)chunk * r->p.nx * r->p.ny * r->p.nz;
             }

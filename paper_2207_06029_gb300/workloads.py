@@ -277,7 +277,7 @@ def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000
     """A seeded Poisson arrival stream (mean `rate` requests per second) of
     capsule-in-shear and settling-sphere runs, half each: cubic lattices
     N ~ U{n_range}, steps ~ U{step_range}, capsule parameters drawn as in
-    case_batch, settling spheres of radius N/10 (icosphere level 3 or 4) at
+    case_batch (radius max(N/10, 5)), settling spheres of radius N/10 (icosphere level 3 or 4) at
     density ratio U[1.1, 1.5] with gravity for a terminal Re U[1, 20] (capped
     so that the sphere stays clear of the floor for its steps).
     Returns [(arrival_s, case, steps)]."""
@@ -288,9 +288,13 @@ def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000
         n = int(rng.integers(n_range[0], n_range[1] + 1))
         steps = int(rng.integers(step_range[0], step_range[1] + 1))
         radius = n / 10.0
-        level = 3 if radius <= 7.0 else 4
         c = (n - 1) / 2.0
         if k % 2 == 0:
+            # capsules no smaller than radius 5 (level 3 below radius 4.8 puts
+            # markers closer than 0.6 lattice units, where the explicit update
+            # of A11 loses stability)
+            radius = max(radius, 5.0)
+            level = 3 if radius <= 7.0 else 4
             Ca = float(np.exp(rng.uniform(np.log(Ca_range[0]), np.log(Ca_range[1]))))
             Eb = float(rng.uniform(*Eb_range))
             mr = float(rng.choice(mass_ratios))
@@ -301,6 +305,7 @@ def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000
             case = Case(f"serve_capsule_{k}_n{n}", (n, n, n), 0.8, (PERIODIC, PERIODIC, WALL), shear_walls(ws),
                         precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), ws))
         else:
+            level = 3 if radius <= 7.0 else 4
             gamma = float(rng.uniform(1.1, 1.5))
             # terminal Re drawn in [1, 20], capped so that the sphere falls at
             # most 0.3 N during its steps (it starts 0.7 N above the floor)
