@@ -289,7 +289,7 @@ def batch_leg(args):
 
     from paper_2207_06029_gb300 import lbib
     from paper_2207_06029_gb300 import workloads as W
-    cases, params = W.case_batch(precision=W.PREC_FP32)
+    cases, params = W.case_batch(count=args.batch_count, precision=W.PREC_FP32)
     stream = torch.cuda.current_stream()
     ctxs = []
     for case in cases:
@@ -317,7 +317,8 @@ def batch_leg(args):
     _, l1 = batch.counters()
     ms = e0.elapsed_time(e1)
     cells = sum(c.ncell for c in cases)
-    out = {"workload": "64 capsule-in-shear cases, cubic N~U{48..112}, radius N/10, 642/2562 markers, fp32",
+    out = {"workload": f"{len(cases)} capsule-in-shear cases, cubic N~U{{48..112}}, radius N/10, 642/2562 markers, "
+                       "fp32",
            "value": cells * (steps + 1) / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps + 1,
            "ms_per_step": ms / (steps + 1), "cells": cells, "markers": sum(len(c.bodies[0].verts) for c in cases),
            "launches_per_step": (l1 - l0) / (steps + 1),
@@ -402,6 +403,7 @@ def main():
                     help="keep the default launch configuration")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-lattices leg")
     ap.add_argument("--batch-steps", type=int, default=60)
+    ap.add_argument("--batch-count", type=int, default=64, help="lattices in the batched leg")
     ap.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving leg")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--overlap", default="auto", choices=["auto", "on", "off"],

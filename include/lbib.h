@@ -87,6 +87,9 @@ typedef struct {
     double gravity[3];       /* rigid: gravity acceleration (adds (rho_s - rho_f) V g) */
     double u0[3], omega0[3]; /* rigid: initial linear and angular velocity */
     int bend_variant;        /* 0: k_b [1 - cos(theta - theta0)]; 1: k_b/2 (theta - theta0)^2 */
+    int kinematic;           /* membrane: 1 advects the markers with the interpolated fluid velocity
+                              * (the kinematic IB of Sec. 3.4) and spreads the internal forces
+                              * alone; 0 the dynamic IB (Newton + Verlet) */
 } lbib_body_params;
 
 typedef struct {

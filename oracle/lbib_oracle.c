@@ -575,6 +575,7 @@ typedef struct {
     double ks0, Eb, kv, thickness, density_ratio, ref_radius;
     double gravity[3], u0[3], omega0[3];
     int bend_variant;
+    int kinematic; /* membrane: markers advected with the fluid (kinematic IB) */
 } orc_body_params;
 
 typedef struct {
@@ -906,9 +907,10 @@ static int body_step(orc_sim *s, orc_body *b) {
         orc_spring_forces(b->X, b->nh, b->edge, b->ks, b->l0, Ftot);
         orc_bend_forces(b->X, b->nh, b->hinge, b->kb, b->theta0, b->p.bend_variant, Ftot);
         orc_volume_forces(b->X, nt, b->tri, b->p.kv, b->V0, Ftot);
-        for (int t = 0; t < nt; ++t)
-            for (int q = 0; q < 3; ++q)
-                for (int a = 0; a < 3; ++a) Ftot[3 * b->tri[3 * t + q] + a] += Ftri[3 * t + a] / 3.0;
+        if (!b->p.kinematic)
+            for (int t = 0; t < nt; ++t)
+                for (int q = 0; q < 3; ++q)
+                    for (int a = 0; a < 3; ++a) Ftot[3 * b->tri[3 * t + q] + a] += Ftri[3 * t + a] / 3.0;
         /* (4) Verlet with the interpolated velocity as tentative velocity
          * (Eqs. verletPos, verletVel) moves the vertices.  reading: the
          * boundary velocity imposed by the IB force is the tentative
@@ -920,7 +922,15 @@ static int body_step(orc_sim *s, orc_body *b) {
         for (int l = 0; l < nv; ++l) {
             double acc[3], xn[3], ubdf[3];
             for (int a = 0; a < 3; ++a) acc[a] = Ftot[3 * l + a] / b->mv;
-            orc_verlet(&b->X[3 * l], &b->Xprev[3 * l], &b->U[3 * l], acc, xn, ubdf);
+            if (b->p.kinematic) {
+                /* kinematic IB (the variant of Sec. 3.4): the vertices are
+                 * advected with the interpolated fluid velocity, X += U dt;
+                 * the fluid feels the membrane's internal forces alone (the
+                 * element hydrodynamic stresses are the fluid's own) */
+                for (int a = 0; a < 3; ++a) xn[a] = b->X[3 * l + a] + b->U[3 * l + a];
+            } else {
+                orc_verlet(&b->X[3 * l], &b->Xprev[3 * l], &b->U[3 * l], acc, xn, ubdf);
+            }
             for (int a = 0; a < 3; ++a) {
                 Xnew[3 * l + a] = xn[a];
                 Ub[3 * l + a] = b->U[3 * l + a] + acc[a];

@@ -540,8 +540,11 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
     const uint32_t step = *dstep;
     __shared__ R s_cv;
     __shared__ BlockBox sbox;
-    const int lane = threadIdx.x & 31;
-    const int v = (vb * blockDim.x + threadIdx.x) >> 5;
+    __shared__ R s_F[8][4];   // per vertex warp: total force (3) and vertex area
+    __shared__ R s_Fl[8][3];  // per vertex warp: Lagrangian force
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v0 = vb * (blockDim.x >> 5);  // first vertex of the block
+    const int v = v0 + warp;
     // the spreading lanes fetch their node and weight first
     int snode = 0;
     R sphi = R(0);
@@ -617,36 +620,48 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
         const int t = B.vt_list[q] / 3;
         const R *tg = (const R *)B.tri_geo + 8 * t;
         Al += tg[3] / R(3);
-        R Fh[3];
-        tri_hydro<R>(B, t, Fh);
+        R Fh[3] = {R(0), R(0), R(0)};
+        if (!B.kinematic) tri_hydro<R>(B, t, Fh);  // kinematic IB: the fluid's stresses stay in the fluid
         for (int a = 0; a < 3; ++a) F[a] += (cv * tg[a] * tg[3] + Fh[a]) / R(3);
     }
     for (int a = 0; a < 3; ++a) F[a] = warp_sum(F[a]);
     Al = warp_sum(Al);
+    if (lane == 0) {
+        s_F[warp][0] = F[0];
+        s_F[warp][1] = F[1];
+        s_F[warp][2] = F[2];
+        s_F[warp][3] = Al;
+    }
+    }
+    __syncthreads();
     // Newton (Eq. newtonSoft) and Verlet (Eqs. verletPos, verletVel), dt = 1,
-    // lane a < 3 integrates component a in FP64
-    R fl = R(0);
-    if (lane < 3) {
-        const int a = lane;
-        const double acc = (double)(a == 0 ? F[0] : a == 1 ? F[1] : F[2]) * B.inv_mv;
-        const double U = B.U[3 * v + a];
+    // in FP64 for the block's 8 vertices at once: lane 3 j + a of one warp
+    // integrates component a of vertex j (FP64 issues per warp-instruction;
+    // the warp rotates over the SM sub-partitions from block to block)
+    if (warp == (vb & 7) && lane < 24 && v0 + lane / 3 < B.nv) {
+        const int j = lane / 3, a = lane % 3, vj = v0 + j;
+        const double acc = (double)s_F[j][a] * B.inv_mv;
+        const double U = B.U[3 * vj + a];
         const double Ub = U + acc;
         const double Fla = Ub - U;
-        const double x = B.X[3 * v + a], xp = B.Xprev[3 * v + a];
-        const double xt = x + U + 0.5 * acc;
-        const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
-        const double xn = x + ubdf + 0.5 * acc;
-        B.Xnew[3 * v + a] = xn;
-        ((R *)B.Xrel_next)[3 * v + a] = R(xn - B.origin[a]);
-        B.Ub[3 * v + a] = Ub;
-        B.Fl[3 * v + a] = Fla;
+        const double x = B.X[3 * vj + a], xp = B.Xprev[3 * vj + a];
+        double xn;
+        if (B.kinematic) {
+            xn = x + U;  // kinematic IB: advected with the interpolated fluid velocity
+        } else {
+            const double xt = x + U + 0.5 * acc;
+            const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
+            xn = x + ubdf + 0.5 * acc;
+        }
+        B.Xnew[3 * vj + a] = xn;
+        ((R *)B.Xrel_next)[3 * vj + a] = R(xn - B.origin[a]);
+        B.Ub[3 * vj + a] = Ub;
+        B.Fl[3 * vj + a] = Fla;
         sbox.add(a, xn);
-        fl = R(Fla);
+        s_Fl[j][a] = R(Fla);
     }
-    const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
-                     __shfl_sync(0xffffffffu, fl, 2)};
-    spread_node<R>(L, lane, snode, Al * sphi, Fl, force, stamp, step);
-    }
+    __syncthreads();
+    if (v < B.nv) spread_node<R>(L, lane, snode, s_F[warp][3] * sphi, s_Fl[warp], force, stamp, step);
     __syncthreads();
     sbox.flush(B.bbox_next);
 }
@@ -844,37 +859,41 @@ __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyV
                                                    const uint32_t *__restrict__ dstep, const int vb) {
     const uint32_t step = *dstep;
     __shared__ BlockBox sbox;
-    const int lane = threadIdx.x & 31;
-    const int v = (vb * blockDim.x + threadIdx.x) >> 5;
+    __shared__ R s_Al[8];
+    __shared__ R s_Fl[8][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v0 = vb * (blockDim.x >> 5);
+    const int v = v0 + warp;
     sbox.init();
-    __syncthreads();
     if (v < B.nv) {
-    const double *S = B.rstate;
-    R Al = R(0);
-    for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32)
-        Al += ((const R *)B.tri_geo)[8 * (B.vt_list[q] / 3) + 3] / R(3);
-    Al = warp_sum(Al);
-    R fl = R(0);
-    if (lane < 3) {
-        const int a = lane, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        R Al = R(0);
+        for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32)
+            Al += ((const R *)B.tri_geo)[8 * (B.vt_list[q] / 3) + 3] / R(3);
+        Al = warp_sum(Al);
+        if (lane == 0) s_Al[warp] = Al;
+    }
+    __syncthreads();
+    // FP64 for the block's 8 markers at once: lane 3 j + a of one warp
+    // handles component a of marker j
+    if (warp == (vb & 7) && lane < 24 && v0 + lane / 3 < B.nv) {
+        const int j = lane / 3, a = lane % 3, vj = v0 + j, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        const double *S = B.rstate;
         const double *un = S + RigidState::U, *wn = S + RigidState::W, *xo = S + RigidState::XC_OLD;
         const double *xc = S + RigidState::XC, *Rn = S + RigidState::ROT;
-        const double r1 = B.X[3 * v + a1] - xo[a1], r2 = B.X[3 * v + a2] - xo[a2];
+        const double r1 = B.X[3 * vj + a1] - xo[a1], r2 = B.X[3 * vj + a2] - xo[a2];
         const double ub = un[a] + (wn[a1] * r2 - wn[a2] * r1);  // (w x r)_a
-        const double Fla = ub - B.U[3 * v + a];
-        B.Ub[3 * v + a] = ub;
-        B.Fl[3 * v + a] = Fla;
-        const double *xb = B.Xbody + 3 * v;
+        const double Fla = ub - B.U[3 * vj + a];
+        B.Ub[3 * vj + a] = ub;
+        B.Fl[3 * vj + a] = Fla;
+        const double *xb = B.Xbody + 3 * vj;
         const double xn = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
-        B.Xnew[3 * v + a] = xn;
-        ((R *)B.Xrel_next)[3 * v + a] = R(xn - B.origin[a]);
+        B.Xnew[3 * vj + a] = xn;
+        ((R *)B.Xrel_next)[3 * vj + a] = R(xn - B.origin[a]);
         sbox.add(a, xn);
-        fl = R(Fla);
+        s_Fl[j][a] = R(Fla);
     }
-    const R Fl[3] = {__shfl_sync(0xffffffffu, fl, 0), __shfl_sync(0xffffffffu, fl, 1),
-                     __shfl_sync(0xffffffffu, fl, 2)};
-    spread_warp<R>(L, B, v, lane, Al, Fl, force, stamp, step);
-    }
+    __syncthreads();
+    if (v < B.nv) spread_warp<R>(L, B, v, lane, s_Al[warp], s_Fl[warp], force, stamp, step);
     __syncthreads();
     sbox.flush(B.bbox_next);
 }
@@ -888,7 +907,7 @@ __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R 
 // ---- batch kernels: the bodies of all lattices of a batch per launch ----
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) kb_moments(BatchTables T, int phase) {
-    const int j = batch_item(T.mom_pre, T.nb, blockIdx.x);
+    const int j = __ldg(T.mom_blk + blockIdx.x);
     const int vb = blockIdx.x - __ldg(T.mom_pre + j), nvb = __ldg(T.mom_pre + j + 1) - __ldg(T.mom_pre + j);
     const BodyRef &br = T.body[phase * T.nb + j];
     const LatRef &F = T.ref[phase * T.nl + br.lat];
@@ -899,7 +918,7 @@ __global__ void __launch_bounds__(256) kb_moments(BatchTables T, int phase) {
 template <typename R>
 __global__ void __launch_bounds__(kMlsThreads) kb_mls(BatchTables T, int phase) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int j = batch_item(T.mls_pre, T.nb, blockIdx.x);
+    const int j = __ldg(T.mls_blk + blockIdx.x);
     const int vb = blockIdx.x - __ldg(T.mls_pre + j), nvb = __ldg(T.mls_pre + j + 1) - __ldg(T.mls_pre + j);
     const BodyRef &br = T.body[phase * T.nb + j];
     const LatRef &F = T.ref[phase * T.nl + br.lat];
@@ -908,7 +927,7 @@ __global__ void __launch_bounds__(kMlsThreads) kb_mls(BatchTables T, int phase) 
 
 template <typename R>
 __global__ void __launch_bounds__(256) kb_membrane(BatchTables T, int phase) {
-    const int m = batch_item(T.memb_pre, T.nmemb, blockIdx.x);
+    const int m = __ldg(T.memb_blk + blockIdx.x);
     const BodyRef &br = T.body[phase * T.nb + __ldg(T.memb_id + m)];
     const LatRef &F = T.ref[phase * T.nl + br.lat];
     membrane_body<R>(T.lat[br.lat], br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.memb_pre + m));
@@ -916,7 +935,7 @@ __global__ void __launch_bounds__(256) kb_membrane(BatchTables T, int phase) {
 
 template <typename R>
 __global__ void __launch_bounds__(256) kb_rigid_forces(BatchTables T, int phase) {
-    const int m = batch_item(T.rf_pre, T.nrigid, blockIdx.x);
+    const int m = __ldg(T.rf_blk + blockIdx.x);
     const BodyRef &br = T.body[phase * T.nb + __ldg(T.rigid_id + m)];
     const int b0 = __ldg(T.rf_pre + m);
     rigid_forces_body<R>(br.v, blockIdx.x - b0, __ldg(T.rf_pre + m + 1) - b0);
@@ -924,7 +943,7 @@ __global__ void __launch_bounds__(256) kb_rigid_forces(BatchTables T, int phase)
 
 template <typename R>
 __global__ void __launch_bounds__(256) kb_rigid_markers(BatchTables T, int phase) {
-    const int m = batch_item(T.rm_pre, T.nrigid, blockIdx.x);
+    const int m = __ldg(T.rm_blk + blockIdx.x);
     const BodyRef &br = T.body[phase * T.nb + __ldg(T.rigid_id + m)];
     const LatRef &F = T.ref[phase * T.nl + br.lat];
     rigid_markers_body<R>(T.lat[br.lat], br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.rm_pre + m));

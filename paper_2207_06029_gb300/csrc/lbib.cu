@@ -283,6 +283,7 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.kv = b.p.kv;
     for (int a = 0; a < 3; ++a) v.origin[a] = b.origin[a];
     v.bend_variant = b.p.bend_variant;
+    v.kinematic = b.p.kinematic;
     v.Xbody = b.Xbody;
     v.rstate = b.rstate;
     v.bbox = b.bbox[b.bcur];
@@ -1360,6 +1361,16 @@ int batch_build(Batch *b) {
     std::vector<int> sweep_pre(1, 0);
     for (int i = 0; i < nl; ++i)
         sweep_pre.push_back(sweep_pre.back() + (lat[order[i]].ncell + b->sweep_threads - 1) / b->sweep_threads);
+    // block -> item maps
+    auto blocks_of = [](const std::vector<int> &pre) {
+        std::vector<int> blk(pre.back() > 0 ? pre.back() : 1, 0);
+        for (size_t i = 0; i + 1 < pre.size(); ++i)
+            for (int q = pre[i]; q < pre[i + 1]; ++q) blk[q] = (int)i;
+        return blk;
+    };
+    const std::vector<int> sweep_blk = blocks_of(sweep_pre), mom_blk = blocks_of(mom_pre),
+                           mls_blk = blocks_of(mls_pre), memb_blk = blocks_of(memb_pre), rf_blk = blocks_of(rf_pre),
+                           rm_blk = blocks_of(rm_pre);
     // one device block for all tables
     size_t off = 0;
     auto place = [&](size_t bytes) {
@@ -1372,7 +1383,10 @@ int batch_build(Batch *b) {
                  o_spre = place(sizeof(int) * sweep_pre.size()), o_mom = place(sizeof(int) * mom_pre.size()),
                  o_mls = place(sizeof(int) * mls_pre.size()), o_mid = place(sizeof(int) * memb_id.size()),
                  o_mpre = place(sizeof(int) * memb_pre.size()), o_rid = place(sizeof(int) * rigid_id.size()),
-                 o_rf = place(sizeof(int) * rf_pre.size()), o_rm = place(sizeof(int) * rm_pre.size());
+                 o_rf = place(sizeof(int) * rf_pre.size()), o_rm = place(sizeof(int) * rm_pre.size()),
+                 o_bs = place(sizeof(int) * sweep_blk.size()), o_bmo = place(sizeof(int) * mom_blk.size()),
+                 o_bml = place(sizeof(int) * mls_blk.size()), o_bme = place(sizeof(int) * memb_blk.size()),
+                 o_brf = place(sizeof(int) * rf_blk.size()), o_brm = place(sizeof(int) * rm_blk.size());
     cudaError_t e = cudaMalloc(&b->dmem, off);
     if (e != cudaSuccess) {
         b->dmem = nullptr;
@@ -1394,6 +1408,12 @@ int batch_build(Batch *b) {
     put(o_rid, rigid_id.data(), sizeof(int) * rigid_id.size());
     put(o_rf, rf_pre.data(), sizeof(int) * rf_pre.size());
     put(o_rm, rm_pre.data(), sizeof(int) * rm_pre.size());
+    put(o_bs, sweep_blk.data(), sizeof(int) * sweep_blk.size());
+    put(o_bmo, mom_blk.data(), sizeof(int) * mom_blk.size());
+    put(o_bml, mls_blk.data(), sizeof(int) * mls_blk.size());
+    put(o_bme, memb_blk.data(), sizeof(int) * memb_blk.size());
+    put(o_brf, rf_blk.data(), sizeof(int) * rf_blk.size());
+    put(o_brm, rm_blk.data(), sizeof(int) * rm_blk.size());
     e = cudaMemcpy(b->dmem, host.data(), off, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bcuda(b, e, "batch tables upload");
     unsigned char *d = static_cast<unsigned char *>(b->dmem);
@@ -1414,6 +1434,12 @@ int batch_build(Batch *b) {
     T.rigid_id = reinterpret_cast<const int *>(d + o_rid);
     T.rf_pre = reinterpret_cast<const int *>(d + o_rf);
     T.rm_pre = reinterpret_cast<const int *>(d + o_rm);
+    T.sweep_blk = reinterpret_cast<const int *>(d + o_bs);
+    T.mom_blk = reinterpret_cast<const int *>(d + o_bmo);
+    T.mls_blk = reinterpret_cast<const int *>(d + o_bml);
+    T.memb_blk = reinterpret_cast<const int *>(d + o_bme);
+    T.rf_blk = reinterpret_cast<const int *>(d + o_brf);
+    T.rm_blk = reinterpret_cast<const int *>(d + o_brm);
     T.sweep_threads = b->sweep_threads;
     b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back()};
     b->steps = 0;

@@ -169,6 +169,7 @@ struct BodyView {
     double inv_mv, inv_6V0; // 1/m_v, 1/(6 V0)
     double origin[3];       // reference point of relative positions and of the volume sum
     int bend_variant;
+    int kinematic;          // membrane markers advected with the fluid (kinematic IB)
     // rigid body
     const double *Xbody;    // [3nv] rest coordinates about the centre
     double *rstate;         // rigid state block, see RigidState
@@ -199,7 +200,8 @@ struct BodyRef {
     int inc_step;  // the first body of its lattice advances the step counter
 };
 // Launch tables (device pointers).  The blocks of a batch launch are split
-// over its items by prefix sums of per-item block counts.
+// over its items by prefix sums of per-item block counts; *_blk maps each
+// block to its item directly (one cached load instead of a search).
 struct BatchTables {
     int nl, nb, nmemb, nrigid;
     const Lattice *lat;    // [nl]
@@ -214,21 +216,9 @@ struct BatchTables {
     const int *rigid_id;   // [nrigid] rigid bodies
     const int *rf_pre;     // [nrigid + 1] triangle blocks of the force reduction
     const int *rm_pre;     // [nrigid + 1] blocks of 8 marker warps
+    const int *sweep_blk, *mom_blk, *mls_blk, *memb_blk, *rf_blk, *rm_blk;  // item of each block
     int sweep_threads;     // threads per sweep block
 };
-
-// Item of block b: the largest i with pre[i] <= b (pre[0] = 0, increasing).
-__device__ __forceinline__ int batch_item(const int *pre, int n, int b) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(pre + mid) <= b)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
 
 // Layout of the rigid-body state block (doubles).
 struct RigidState {

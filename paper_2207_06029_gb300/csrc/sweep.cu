@@ -312,11 +312,11 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
     }
 }
 
-// All lattices of a batch: block b belongs to sweep slot batch_item(b); its
+// All lattices of a batch: block b belongs to sweep slot sweep_blk[b]; its
 // threads take consecutive cells of that lattice (x fastest).
 template <typename S, typename R>
 __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int store_fields) {
-    const int slot = batch_item(T.sweep_pre, T.nl, blockIdx.x);
+    const int slot = __ldg(T.sweep_blk + blockIdx.x);
     const int l = __ldg(T.sweep_lat + slot);
     const Lattice &L = T.lat[l];
     const LatRef &F = T.ref[phase * T.nl + l];

@@ -148,11 +148,12 @@ class Body:
     u0: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     omega0: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     bend_variant: int = 0
+    kinematic: int = 0
 
     def kwargs(self):
         return dict(rigid=self.rigid, ks0=self.ks0, Eb=self.Eb, kv=self.kv, thickness=self.thickness,
                     density_ratio=self.density_ratio, ref_radius=self.ref_radius, gravity=self.gravity,
-                    u0=self.u0, omega0=self.omega0, bend_variant=self.bend_variant)
+                    u0=self.u0, omega0=self.omega0, bend_variant=self.bend_variant, kinematic=self.kinematic)
 
 
 @dataclasses.dataclass
@@ -317,6 +318,25 @@ def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000
                         precision=precision, steps=steps, bodies=[body])
         out.append((t, case, steps))
     return out
+
+
+def case_cavity(n=25, Re=10.0, tau=0.8, precision=PREC_FP32, sphere=False, steps=None):
+    """Lid-driven cubic cavity (Sec. 3.1): walls on every face, the +y face
+    moving along +z at u_lid = Re nu / (n - 1) (diffusive scaling: fixed tau,
+    u_lid ~ 1/n).  With sphere=True a neutrally buoyant rigid sphere of
+    radius n/8 (icosphere level 3) sits at (0.5, 0.35, 0.5) L."""
+    u_lid = Re * viscosity(tau) / (n - 1)
+    wall_u = np.zeros((6, 3))
+    wall_u[3, 2] = u_lid  # +y face moves along z
+    bodies = []
+    if sphere:
+        L = n - 1
+        v, f = icosphere(3, n / 8.0, (0.5 * L, 0.35 * L, 0.5 * L))
+        bodies.append(Body(v, f, rigid=True, density_ratio=1.0, ref_radius=n / 8.0))
+    if steps is None:
+        steps = int(2.0 * (n - 1) ** 2 / viscosity(tau))
+    return Case(f"cavity_{n}_Re{Re:g}", (n, n, n), tau, (WALL, WALL, WALL), wall_u, precision=precision,
+                steps=steps, bodies=bodies)
 
 
 def case_settling(nx=160, ny=160, nz=480, tau=0.7, radius=8.0, level=5, Re=5.0, gamma=1.3, steps=50000,

@@ -144,6 +144,17 @@ def test_fp64_capsule_in_shear(lbib, bend_variant):
     check_fp64(g, o)
 
 
+def test_fp64_kinematic_capsule_in_shear(lbib):
+    """Kinematic-IB variant (markers advected with the interpolated fluid
+    velocity, internal forces spread), 28^3, 25 steps."""
+    case = W.case_capsule_shear(n=28, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
+                                precision=W.PREC_FP64)
+    case.bodies[0].kinematic = 1
+    g = run_gpu(lbib, case, 25)
+    o = run_oracle(case, 25)
+    check_fp64(g, o)
+
+
 def test_fp64_two_bodies_and_gravity_periodic(lbib):
     """Two bodies in one periodic lattice: a settling rigid sphere and a
     capsule (shared force field, several spreads per step)."""
