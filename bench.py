@@ -178,10 +178,10 @@ def run_gpu(args, rank, world):
     if args.autotune:
         tuned = lbib.lbib_autotune(h, 20)  # launch configuration (untimed; advances the run)
     else:
-        tuned = (0, 0, 1)
+        tuned = (0, 0, 1, 0)
     if args.overlap != "auto":
         lbib.lbib_set_overlap(h, 1 if args.overlap == "on" else 0)
-        tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0)
+        tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0, tuned[3])
     lbib.lbib_sync(h)
     lbib.lbib_set_output(h, -1)  # no macroscopic-field output inside the timed loop
     # L2 flush between timed steps: write a buffer larger than the 129 MB L2,
@@ -332,14 +332,14 @@ def batch_leg(args):
     return out
 
 
-def serve_leg(args, mode, precision):
+def serve_leg(args, mode, precision, max_active=64):
     """A seeded Poisson stream (4 requests/s) of capsule-in-shear and
     settling-sphere runs through the serving engine; latency from submission
     to completion."""
     from paper_2207_06029_gb300 import lbib
     from paper_2207_06029_gb300 import workloads as W
     stream = W.serve_stream(count=args.serve_requests, precision=precision)
-    server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=64, mode=mode)
+    server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=max_active, mode=mode)
     reqs = [(t, lbib.request_from_case(case, steps), case, steps) for t, case, steps in stream]
     t0 = time.perf_counter()
     ids = []
@@ -472,10 +472,13 @@ def main():
         "config": {"workload": WORKLOADS[args.workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
                    "fields_output": "off in the timed loop (e2e reads them)",
-                   "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2])},
+                   "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
+                                 "sweep_row_tiles": bool(r["tuned"][3])},
                    "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(), "kernel": "k_sweep<float,float>",
+                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "kernel": ("k_sweep_tile<float,float> (shared-memory row tiles, 128-bit loads/stores)"
+                                if r["tuned"][3] else "k_sweep<float,float>"),
                      "peak_source": peak_kind, "sweep_us": r["iso_sweep_us"],
                      "sweep_in_step_us": 1e6 * concurrent_s,
                      "sweep_in_step_frac": bytes_per_launch / concurrent_s / 1e9 / peak,
@@ -501,6 +504,7 @@ def main():
             "stream": f"{args.serve_requests} requests, Poisson 4/s, half capsule-in-shear half settling sphere, "
                       "cubic N~U{32..160}, steps~U{1000..6000}, budget 150 GB",
             "batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32),
+            "batched_fp32_max4": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, max_active=4),
             "plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32),
             "batched_fp16_dev": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV),
         }

@@ -164,12 +164,21 @@ int lbib_profile(void *ctx, int enable);
 int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
 
 /* Times the step in several launch configurations and keeps the fastest:
- * the block shape of the whole-lattice sweep, then (single-body contexts)
- * the overlap of the far-field sweep with the IB stage.  Each trial runs
+ * the sweep kernel and its block shape (the 4-wide FP32 kernel with 128-bit
+ * loads and stores where nx is a multiple of 4, or the one-node kernel in
+ * several shapes), then (single-body contexts) the overlap of the far-field
+ * sweep with the IB stage.  Each trial runs
  * 1 + 2 * `steps` real time steps, so the simulation advances by about
- * 16 * `steps` steps.  choice (optional, 3 ints) receives block x, block y (0, 0: whole
- * x-rows) and the overlap flag. */
+ * 16 * `steps` steps.  choice (optional, 4 ints) receives block x, block y (0, 0: whole
+ * x-rows), the overlap flag and the 4-wide flag. */
 int lbib_autotune(void *ctx, int steps, int *choice);
+
+/* Sets the sweep launch configuration (what lbib_autotune chooses):
+ * row_tiles = 1 selects the row-tile kernel (x-rows staged in shared memory
+ * with 128-bit loads and stores; FP32/FP64 with nx a multiple of 4, else
+ * ignored), 0 the one-node kernel with blocks of block_x * block_y threads
+ * (0, 0: whole x-rows).  Results are the same in every configuration. */
+int lbib_set_sweep_config(void *ctx, int row_tiles, int block_x, int block_y);
 
 /* With a single body, the sweep of the nodes outside the body's support
  * box runs on a second stream concurrently with the IB stage (default 1);

@@ -907,30 +907,38 @@ __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R 
 // ---- batch kernels: the bodies of all lattices of a batch per launch ----
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) kb_moments(BatchTables T, int phase) {
+    __shared__ Lattice L;
     const int j = __ldg(T.mom_blk + blockIdx.x);
     const int vb = blockIdx.x - __ldg(T.mom_pre + j), nvb = __ldg(T.mom_pre + j + 1) - __ldg(T.mom_pre + j);
     const BodyRef &br = T.body[phase * T.nb + j];
+    stage_shared(L, T.lat + br.lat);
     const LatRef &F = T.ref[phase * T.nl + br.lat];
-    moments_body<S, R>((const S *)F.fin, T.lat[br.lat], br.v.bbox, br.v.bbox_next, (R *)F.mom,
-                       br.inc_step ? F.d_step : nullptr, vb, nvb);
+    moments_body<S, R>((const S *)F.fin, L, br.v.bbox, br.v.bbox_next, (R *)F.mom, br.inc_step ? F.d_step : nullptr,
+                       vb, nvb);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kMlsThreads) kb_mls(BatchTables T, int phase) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Lattice L;
+    __shared__ BodyRef br;
     const int j = __ldg(T.mls_blk + blockIdx.x);
     const int vb = blockIdx.x - __ldg(T.mls_pre + j), nvb = __ldg(T.mls_pre + j + 1) - __ldg(T.mls_pre + j);
-    const BodyRef &br = T.body[phase * T.nb + j];
+    stage_shared(br, T.body + phase * T.nb + j);
+    stage_shared(L, T.lat + br.lat);
     const LatRef &F = T.ref[phase * T.nl + br.lat];
-    mls_body<R>((const R *)F.mom, T.lat[br.lat], br.v, F.err, *reinterpret_cast<MlsSmem<R> *>(smem_raw), vb, nvb);
+    mls_body<R>((const R *)F.mom, L, br.v, F.err, *reinterpret_cast<MlsSmem<R> *>(smem_raw), vb, nvb);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256) kb_membrane(BatchTables T, int phase) {
+    __shared__ Lattice L;
+    __shared__ BodyRef br;
     const int m = __ldg(T.memb_blk + blockIdx.x);
-    const BodyRef &br = T.body[phase * T.nb + __ldg(T.memb_id + m)];
+    stage_shared(br, T.body + phase * T.nb + __ldg(T.memb_id + m));
+    stage_shared(L, T.lat + br.lat);
     const LatRef &F = T.ref[phase * T.nl + br.lat];
-    membrane_body<R>(T.lat[br.lat], br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.memb_pre + m));
+    membrane_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.memb_pre + m));
 }
 
 template <typename R>
@@ -943,10 +951,13 @@ __global__ void __launch_bounds__(256) kb_rigid_forces(BatchTables T, int phase)
 
 template <typename R>
 __global__ void __launch_bounds__(256) kb_rigid_markers(BatchTables T, int phase) {
+    __shared__ Lattice L;
+    __shared__ BodyRef br;
     const int m = __ldg(T.rm_blk + blockIdx.x);
-    const BodyRef &br = T.body[phase * T.nb + __ldg(T.rigid_id + m)];
+    stage_shared(br, T.body + phase * T.nb + __ldg(T.rigid_id + m));
+    stage_shared(L, T.lat + br.lat);
     const LatRef &F = T.ref[phase * T.nl + br.lat];
-    rigid_markers_body<R>(T.lat[br.lat], br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.rm_pre + m));
+    rigid_markers_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.rm_pre + m));
 }
 
 template <typename S, typename R>

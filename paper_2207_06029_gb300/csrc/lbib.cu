@@ -386,6 +386,7 @@ int lbib_create(const lbib_params *p, void **out) {
     L.ntz = (n[2] + kTile - 1) / kTile;
     L.ncell = (int)ncell;
     L.stride = (ncell + 63) / 64 * 64;
+    L.sweep_vec = 0;  // the one-node sweep; the autotuner may pick the row-tile kernel
     for (int a = 0; a < 3; ++a) {
         L.bc[a] = p->bc[a];
         L.gext[a] = p->body_force[a];
@@ -486,6 +487,7 @@ int lbib_create(const lbib_params *p, void **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sr, 0, 2 * sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = prepare_kernels();
+    if (e == cudaSuccess) e = prepare_sweep_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking);
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)
         for (int j = 0; j < 6 && e == cudaSuccess; ++j) e = cudaEventCreate(&c->gev[k][j]);
@@ -1181,16 +1183,25 @@ int lbib_autotune(void *h, int steps, int *choice) {
         }
         return sync_ctx(c);
     };
-    // sweep block shapes: whole x-rows (default), then fixed 2D shapes
-    const int shapes[][2] = {{0, 0}, {32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}};
+    // sweep launch shapes: the row-tile kernel (where it applies), whole
+    // x-rows of the one-node kernel, then fixed 2D shapes
+    const int shapes[][3] = {{0, 0, 0}, {0, 0, 1}, {32, 8, 0}, {64, 4, 0}, {128, 2, 0}, {256, 1, 0}, {32, 4, 0},
+                             {64, 2, 0}};
+    const int esz = c->prec == LBIB_FP64 ? 8 : 4;
+    const bool vec_ok = (c->prec == LBIB_FP32 || c->prec == LBIB_FP64) && (c->L.nx & 3) == 0 &&
+                        (c->L.nx * esz) % 16 == 0 &&
+                        19LL * std::max(1, std::min(256 / c->L.nx, c->L.ny)) * c->L.nx * esz <= 160 * 1024 &&
+                        c->L.nx <= 512;
     const bool saved_split = c->split_sweep;
     c->split_sweep = false;
     float best = 1e30f;
     int best_shape = 0, rc = 0;
     for (int k = 0; k < (int)(sizeof(shapes) / sizeof(shapes[0])); ++k) {
+        if (shapes[k][2] && !vec_ok) continue;
         if (shapes[k][0] > 0 && shapes[k][0] > (c->L.nx + 31) / 32 * 32) continue;
         c->L.sweep_bx = shapes[k][0];
         c->L.sweep_by = shapes[k][1];
+        c->L.sweep_vec = shapes[k][2];
         invalidate_graphs(c);
         float ms = 0.f;
         if ((rc = trial(&ms))) break;
@@ -1201,6 +1212,7 @@ int lbib_autotune(void *h, int steps, int *choice) {
     }
     c->L.sweep_bx = shapes[best_shape][0];
     c->L.sweep_by = shapes[best_shape][1];
+    c->L.sweep_vec = shapes[best_shape][2];
     invalidate_graphs(c);
     // overlap of the far-field sweep with the IB stage
     int overlap = 0;
@@ -1220,8 +1232,22 @@ int lbib_autotune(void *h, int steps, int *choice) {
         choice[0] = c->L.sweep_bx;
         choice[1] = c->L.sweep_by;
         choice[2] = overlap;
+        choice[3] = c->L.sweep_vec;
     }
     return rc;
+}
+
+int lbib_set_sweep_config(void *h, int row_tiles, int block_x, int block_y) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (row_tiles < 0 || row_tiles > 1 || block_x < 0 || block_y < 0 || (block_x == 0) != (block_y == 0) ||
+        block_x * block_y > 1024)
+        return fail(c, LBIB_EINVAL, "bad sweep configuration");
+    c->L.sweep_vec = row_tiles;
+    c->L.sweep_bx = block_x;
+    c->L.sweep_by = block_y;
+    invalidate_graphs(c);
+    return LBIB_OK;
 }
 
 int lbib_set_overlap(void *h, int enable) {

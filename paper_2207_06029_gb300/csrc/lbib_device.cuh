@@ -66,16 +66,22 @@ template <>
 struct Pop<double, double> {
     __device__ static double ld(const double *p) { return __ldg(p); }
     __device__ static void st(double *p, double v) { __stcs(p, v); }
+    __device__ static double from(double v) { return v; }
+    __device__ static double to(double v) { return v; }
 };
 template <>
 struct Pop<float, float> {
     __device__ static float ld(const float *p) { return __ldg(p); }
     __device__ static void st(float *p, float v) { __stcs(p, v); }
+    __device__ static float from(float v) { return v; }
+    __device__ static float to(float v) { return v; }
 };
 template <>
 struct Pop<__half, float> {
     __device__ static float ld(const __half *p) { return __half2float(__ldg(p)) * (1.0f / kHalfScale); }
     __device__ static void st(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
+    __device__ static float from(__half v) { return __half2float(v) * (1.0f / kHalfScale); }
+    __device__ static __half to(float v) { return __float2half_rn(v * kHalfScale); }
 };
 template <>
 struct Pop<__nv_bfloat16, float> {
@@ -83,6 +89,8 @@ struct Pop<__nv_bfloat16, float> {
         return __bfloat162float(__ldg(p)) * (1.0f / kHalfScale);
     }
     __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v * kHalfScale); }
+    __device__ static float from(__nv_bfloat16 v) { return __bfloat162float(v) * (1.0f / kHalfScale); }
+    __device__ static __nv_bfloat16 to(float v) { return __float2bfloat16_rn(v * kHalfScale); }
     // stochastic rounding: adding 16 uniform random bits below the bfloat16
     // mantissa and truncating rounds the magnitude up with probability equal
     // to the discarded fraction, so the stored value is unbiased
@@ -124,6 +132,7 @@ struct Lattice {
     double wall_u[6][3];
     double dist2_cut;       // largest |X - x_k|^2 whose MLS weight is non-zero
     int sweep_bx, sweep_by; // block shape of the whole-lattice sweep (0: default)
+    int sweep_vec;          // 1: row-tile sweep (shared-memory staging, 128-bit loads/stores) where it applies
     // derived, double and float copies
     double omega_d, cF_d, nu_d, gext_d[3], uw_d[27][3];
     float omega_f, cF_f, nu_f, gext_f[3], uw_f[27][3], dist2_cut_f;
@@ -219,6 +228,18 @@ struct BatchTables {
     const int *sweep_blk, *mom_blk, *mls_blk, *memb_blk, *rf_blk, *rm_blk;  // item of each block
     int sweep_threads;     // threads per sweep block
 };
+
+// Copies a table entry into shared memory with the whole block (the batch
+// kernels then read lattice and body parameters at shared-memory latency
+// instead of chasing them through global memory).  Ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void stage_shared(T &dst, const T *src) {
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += blockDim.x) d[w] = __ldg(s + w);
+    __syncthreads();
+}
 
 // Layout of the rigid-body state block (doubles).
 struct RigidState {

@@ -15,6 +15,7 @@ namespace lbib {
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
                          const uint32_t *step, const Lattice &L, void *fields, int part, const int *box,
                          uint32_t *sr, int parity, int nsm, cudaStream_t s);
+cudaError_t prepare_sweep_kernels();
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
                                     void *fields, cudaStream_t s);
 cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s);

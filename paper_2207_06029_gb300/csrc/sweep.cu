@@ -85,38 +85,16 @@ __device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const R
     }
 }
 
-// Stream, walls and collision of node (x, y, z).
-template <typename S, typename R>
-__device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restrict__ fout, R *__restrict__ force,
-                                           const uint32_t *__restrict__ stamp, uint32_t step, const Lattice &L,
-                                           R *__restrict__ fields, int x, int y, int z, uint32_t seed) {
+// Walls, moments, body force and BGK/Guo collision of node (x, y, z) whose
+// streamed populations are g (Eqs. evoleq, eqfunc, forcing; Zou-He walls);
+// on return g holds the post-collision populations and rho, u the moments
+// of the collision (stored as the macroscopic fields).
+template <typename R>
+__device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, const uint32_t *__restrict__ stamp,
+                                             uint32_t step, const Lattice &L, int x, int y, int z, long long idx,
+                                             R &rho_o, R &ux_o, R &uy_o, R &uz_o) {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int idx = x + nx * (y + ny * z);
-    const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
-    // neighbour coordinates; on walled axes an outside source is clamped to
-    // the node itself (its value is unused: the wall rule overwrites it)
-    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
-    if (xm < 0) xm = px ? nx - 1 : 0;
-    if (xp >= nx) xp = px ? 0 : nx - 1;
-    if (ym < 0) ym = py ? ny - 1 : 0;
-    if (yp >= ny) yp = py ? 0 : ny - 1;
-    if (zm < 0) zm = pz ? nz - 1 : 0;
-    if (zp >= nz) zp = pz ? 0 : nz - 1;
-    const int nxy = nx * ny;
-    const int oy_m = ym * nx, oy_0 = y * nx, oy_p = yp * nx;
-    const int oz_m = zm * nxy, oz_0 = z * nxy, oz_p = zp * nxy;
     const long long st = L.stride;
-
-    // pull: f_i(x) = f*_i(x - e_i)
-    R g[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
-        const int sy = ey(i) > 0 ? oy_m : ey(i) < 0 ? oy_p : oy_0;
-        const int sz = ez(i) > 0 ? oz_m : ez(i) < 0 ? oz_p : oz_0;
-        g[i] = Pop<S, R>::ld(fin + (long long)i * st + (sx + sy + sz));
-    }
-
     // walls (faces -x,+x,-y,+y,-z,+z; the index-0 face has inward normal +)
     int nf = 0, fa = 0, fs = 0, code[3] = {0, 0, 0};
     unsigned unknown = 0;
@@ -203,6 +181,62 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
     const R om1 = R(1) - omega, ca = R(3) * omega * rho, cb = R(4.5) * omega * rho;
     const R c3 = R(3) * cF, c9 = R(9) * cF;
     const R A0 = omega * (dr - R(1.5) * rho * uu) - c3 * uF;
+    const R g0 = om1 * g[0] + wq<R>(0) * A0;
+    g[0] = g0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = pair_rep(k), o = opp(i);
+        R eu = R(0), eF = R(0);
+        if (ex(i)) { eu += R(ex(i)) * ux; eF += R(ex(i)) * F0; }
+        if (ey(i)) { eu += R(ey(i)) * uy; eF += R(ey(i)) * F1; }
+        if (ez(i)) { eu += R(ez(i)) * uz; eF += R(ez(i)) * F2; }
+        const R w = wq<R>(i);
+        const R E = eu * (cb * eu + c9 * eF), Od = ca * eu + c3 * eF;
+        const R base = w * (A0 + E), odd = w * Od;
+        const R gi = om1 * g[i] + (base + odd), go = om1 * g[o] + (base - odd);
+        g[i] = gi;
+        g[o] = go;
+    }
+    rho_o = rho;
+    ux_o = ux;
+    uy_o = uy;
+    uz_o = uz;
+}
+
+// Stream, walls and collision of node (x, y, z).
+template <typename S, typename R>
+__device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restrict__ fout, R *__restrict__ force,
+                                           const uint32_t *__restrict__ stamp, uint32_t step, const Lattice &L,
+                                           R *__restrict__ fields, int x, int y, int z, uint32_t seed) {
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int idx = x + nx * (y + ny * z);
+    const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
+    // neighbour coordinates; on walled axes an outside source is clamped to
+    // the node itself (its value is unused: the wall rule overwrites it)
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    if (xm < 0) xm = px ? nx - 1 : 0;
+    if (xp >= nx) xp = px ? 0 : nx - 1;
+    if (ym < 0) ym = py ? ny - 1 : 0;
+    if (yp >= ny) yp = py ? 0 : ny - 1;
+    if (zm < 0) zm = pz ? nz - 1 : 0;
+    if (zp >= nz) zp = pz ? 0 : nz - 1;
+    const int nxy = nx * ny;
+    const int oy_m = ym * nx, oy_0 = y * nx, oy_p = yp * nx;
+    const int oz_m = zm * nxy, oz_0 = z * nxy, oz_p = zp * nxy;
+    const long long st = L.stride;
+
+    // pull: f_i(x) = f*_i(x - e_i)
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
+        const int sy = ey(i) > 0 ? oy_m : ey(i) < 0 ? oy_p : oy_0;
+        const int sz = ez(i) > 0 ? oz_m : ez(i) < 0 ? oz_p : oz_0;
+        g[i] = Pop<S, R>::ld(fin + (long long)i * st + (sx + sy + sz));
+    }
+
+    R rho, ux, uy, uz;
+    collide_node<R>(g, force, stamp, step, L, x, y, z, idx, rho, ux, uy, uz);
     // bfloat16 storage rounds stochastically (8-bit mantissa: nearest
     // rounding of a smooth flow repeats the same error at every node of a
     // plane and step, a bias); the other formats round to nearest
@@ -216,19 +250,12 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
             Pop<S, R>::st(p, v);
         }
     };
-    put(fout + idx, om1 * g[0] + wq<R>(0) * A0);
+    put(fout + idx, g[0]);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = pair_rep(k), o = opp(i);
-        R eu = R(0), eF = R(0);
-        if (ex(i)) { eu += R(ex(i)) * ux; eF += R(ex(i)) * F0; }
-        if (ey(i)) { eu += R(ey(i)) * uy; eF += R(ey(i)) * F1; }
-        if (ez(i)) { eu += R(ez(i)) * uz; eF += R(ez(i)) * F2; }
-        const R w = wq<R>(i);
-        const R E = eu * (cb * eu + c9 * eF), Od = ca * eu + c3 * eF;
-        const R base = w * (A0 + E), odd = w * Od;
-        put(fout + (long long)i * st + idx, om1 * g[i] + (base + odd));
-        put(fout + (long long)o * st + idx, om1 * g[o] + (base - odd));
+        put(fout + (long long)i * st + idx, g[i]);
+        put(fout + (long long)o * st + idx, g[o]);
     }
     if (fields) {
         fields[idx] = rho;
@@ -244,6 +271,12 @@ __device__ __forceinline__ void clamp_box(const Lattice &L, const int *box, int 
     const int n[3] = {L.nx, L.ny, L.nz};
     for (int a = 0; a < 3; ++a) {
         long long l = box[a], h = box[3 + a];
+        if (a == 0 && (L.nx & 3) == 0 && h >= l) {
+            // whole groups of 4 along x, so that the 4-wide sweep never
+            // splits a group between the far-field and the box sweeps
+            l &= ~3LL;  // down to a multiple of 4 (two's complement: also below 0)
+            h |= 3LL;   // up to the last node of its group
+        }
         if (L.bc[a] == kWall) {
             l = l < 0 ? 0 : l;
             h = h > n[a] - 1 ? n[a] - 1 : h;
@@ -291,6 +324,93 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
     sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
 }
 
+// Row-tile sweep with shared-memory staging: a block takes `rows`
+// consecutive x-rows of one z-plane.  It first copies, for every direction
+// i, the source rows (y - e_iy, z - e_iz) into shared memory with 128-bit
+// coalesced loads; each thread then pulls its node's 19 values from shared
+// memory (the x shift and its periodic or walled wrap stay inside the row),
+// collides, writes the results back over the staged rows, and the block
+// stores them with 128-bit coalesced stores.  Needs rows of whole 16-byte
+// vectors (nx * sizeof(S) a multiple of 16); with a body box, the box holds
+// whole groups of 4 nodes along x, so no vector straddles it.
+template <typename S, typename R>
+__global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S *__restrict__ fout,
+                                                     R *__restrict__ force, const uint32_t *__restrict__ stamp,
+                                                     const uint32_t *__restrict__ dstep, Lattice L,
+                                                     R *__restrict__ fields, const int *__restrict__ box,
+                                                     uint32_t *__restrict__ sr, int parity, int rows) {
+    extern __shared__ uint4 tile_raw[];
+    S *sm = reinterpret_cast<S *>(tile_raw);  // [Q][rows][nx]
+    constexpr int V = 16 / sizeof(S);         // nodes per 16-byte vector
+    const uint32_t step = stamp ? *dstep : 0u;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) sr[parity ^ 1] = sr[parity] + 1u;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny;
+    const int z = blockIdx.y, y0 = blockIdx.x * rows;
+    const int nrows = min(rows, ny - y0);
+    const int nvec = nx / V;  // vectors per row
+    const long long st = L.stride;
+    const bool px = L.bc[0] == kPeriodic, py = L.bc[1] == kPeriodic, pz = L.bc[2] == kPeriodic;
+    int lo[3] = {0, 0, 0}, ext[3] = {0, 0, 0};
+    if (box) clamp_box(L, box, lo, ext);
+
+    // stage the source rows: a thread keeps one (row, vector) slot and
+    // takes every G-th direction, so no division sits in the loops
+    const int nslot = nrows * nvec, G = blockDim.x / nslot;  // blockDim >= nslot: rows * nx >= rows * nvec
+    const int slot = threadIdx.x % nslot, grp = threadIdx.x / nslot;
+    const int sr_ = slot / nvec, sq = slot - sr_ * nvec;
+    if (grp < G) {
+        const int yr = y0 + sr_;
+        int ym = yr - 1, yp = yr + 1, zm = z - 1, zp = z + 1;
+        if (ym < 0) ym = py ? ny - 1 : 0;
+        if (yp >= ny) yp = py ? 0 : ny - 1;
+        if (zm < 0) zm = pz ? nz - 1 : 0;
+        if (zp >= nz) zp = pz ? 0 : nz - 1;
+        for (int i = grp; i < Q; i += G) {
+            const int eyi = ey(i), ezi = ez(i);
+            const int sy = eyi > 0 ? ym : eyi < 0 ? yp : yr;
+            const int sz = ezi > 0 ? zm : ezi < 0 ? zp : z;
+            const S *src = fin + (long long)i * st + ((long long)sy * nx + (long long)sz * nxy) + sq * V;
+            reinterpret_cast<uint4 *>(sm + (i * rows + sr_) * nx)[sq] = __ldg(reinterpret_cast<const uint4 *>(src));
+        }
+    }
+    __syncthreads();
+
+    const int r = threadIdx.x / nx, x = threadIdx.x - r * nx, y = y0 + r;
+    const bool mine = r < nrows && !(box && in_box(L, lo, ext, x, y, z));
+    R g[Q];
+    if (mine) {
+        int xm = x - 1, xp = x + 1;
+        if (xm < 0) xm = px ? nx - 1 : 0;
+        if (xp >= nx) xp = px ? 0 : nx - 1;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
+            g[i] = Pop<S, R>::from(sm[(i * rows + r) * nx + sx]);
+        }
+        const long long idx = x + (long long)y * nx + (long long)z * nxy;
+        R rho, ux, uy, uz;
+        collide_node<R>(g, force, stamp, step, L, x, y, z, idx, rho, ux, uy, uz);
+        if (fields) {
+            fields[idx] = rho;
+            fields[st + idx] = ux;
+            fields[2 * st + idx] = uy;
+            fields[3 * st + idx] = uz;
+        }
+    }
+    __syncthreads();  // every staged value has been read
+    if (mine) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sm[(i * rows + r) * nx + x] = Pop<S, R>::to(g[i]);
+    }
+    __syncthreads();
+    if (grp < G && !(box && in_box(L, lo, ext, sq * V, y0 + sr_, z))) {  // not the box sweep's nodes
+        S *dst = fout + ((long long)(y0 + sr_) * nx + (long long)z * nxy) + sq * V;
+        for (int i = grp; i < Q; i += G)
+            __stcs(reinterpret_cast<uint4 *>(dst + (long long)i * st),
+                   reinterpret_cast<const uint4 *>(sm + (i * rows + sr_) * nx)[sq]);
+    }
+}
+
 // The nodes inside the box (grid-stride; periodic coordinates wrap).
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S *__restrict__ fout,
@@ -316,9 +436,10 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
 // threads take consecutive cells of that lattice (x fastest).
 template <typename S, typename R>
 __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int store_fields) {
+    __shared__ Lattice L;
     const int slot = __ldg(T.sweep_blk + blockIdx.x);
     const int l = __ldg(T.sweep_lat + slot);
-    const Lattice &L = T.lat[l];
+    stage_shared(L, T.lat + l);
     const LatRef &F = T.ref[phase * T.nl + l];
     const int c = (blockIdx.x - __ldg(T.sweep_pre + slot)) * blockDim.x + threadIdx.x;
     if (c >= L.ncell) return;
@@ -393,6 +514,25 @@ static inline unsigned grid_for(int n, int b) { return (unsigned)((n + b - 1) / 
 
 // Block of whole x-rows: bx = nx rounded up to a warp (at most 256), by rows
 // so that a block holds about 256 threads; one z-plane per grid layer.
+// Row-tile sweep: rows of whole 16-byte vectors, about 256 nodes a block,
+// staged rows within kTileSmem bytes.
+constexpr int kTileSmem = 160 * 1024;
+
+template <typename S>
+static int tile_rows(const Lattice &L) {
+    // nx a multiple of 4 also keeps every vector on one side of a body box
+    if (!L.sweep_vec || (L.nx & 3) != 0 || (L.nx * (int)sizeof(S)) % 16 != 0 ||
+        (L.stride * (long long)sizeof(S)) % 16 != 0)
+        return 0;
+    if (!(std::is_same<S, float>::value || std::is_same<S, double>::value)) return 0;
+    int rows = 256 / L.nx;
+    if (rows < 1) rows = 1;
+    if (rows > L.ny) rows = L.ny;
+    if (rows * L.nx > 512) return 0;
+    if ((size_t)Q * rows * L.nx * sizeof(S) > (size_t)kTileSmem) return 0;
+    return rows;
+}
+
 static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
     int bx = (L.nx + 31) / 32 * 32;
     if (bx > 256) bx = 256;
@@ -415,6 +555,12 @@ static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint3
     if (part == 2) {
         k_sweep_box<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
                                                   (R *)fields, box, sr, parity);
+    } else if (const int rows = tile_rows<S>(L)) {
+        const dim3 grid((L.ny + rows - 1) / rows, L.nz);
+        const size_t smem = (size_t)Q * rows * L.nx * sizeof(S);
+        k_sweep_tile<S, R><<<grid, rows * L.nx, smem, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
+                                                           (R *)fields, part == 1 ? box : nullptr, sr, parity,
+                                                           rows);
     } else {
         dim3 grid, block;
         sweep_shape(L, grid, block);
@@ -451,6 +597,16 @@ cudaError_t launch_batch_sweep(int prec, const BatchTables &T, const BatchGrid &
         case 2: return batch_sweep_t<__half, float>(T, G, phase, store_fields, s);
         default: return batch_sweep_t<__nv_bfloat16, float>(T, G, phase, store_fields, s);
     }
+}
+
+// Kernel attributes set once before any launch or capture.
+cudaError_t prepare_sweep_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_tile<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTileSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_tile<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kTileSmem);
+    return e;
 }
 
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,

@@ -77,7 +77,7 @@ _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
-           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_autotune",
+           "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
            "lbib_device_bytes", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
            "lbib_batch_destroy", "lbib_batch_last_error",
@@ -114,6 +114,7 @@ def load():
         L.lbib_set_output.argtypes = [vp, C.c_int]
         L.lbib_set_overlap.argtypes = [vp, C.c_int]
         L.lbib_set_graphs.argtypes = [vp, C.c_int]
+        L.lbib_set_sweep_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_mesh_measures_noalloc.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
@@ -246,14 +247,18 @@ def lbib_get_profile(ctx):
 
 
 def lbib_autotune(ctx, steps):
-    """Returns (block_x, block_y, overlap) chosen; advances the run by several times `steps`."""
-    ch = (C.c_int * 3)()
+    """Returns (block_x, block_y, overlap, vec4) chosen; advances the run by several times `steps`."""
+    ch = (C.c_int * 4)()
     _check(ctx, load().lbib_autotune(ctx, int(steps), ch))
-    return ch[0], ch[1], ch[2]
+    return ch[0], ch[1], ch[2], ch[3]
 
 
 def lbib_set_overlap(ctx, enable):
     return _check(ctx, load().lbib_set_overlap(ctx, int(enable)))
+
+
+def lbib_set_sweep_config(ctx, row_tiles, block_x=0, block_y=0):
+    return _check(ctx, load().lbib_set_sweep_config(ctx, int(row_tiles), int(block_x), int(block_y)))
 
 
 def lbib_set_graphs(ctx, enable):

@@ -245,6 +245,35 @@ def test_graph_steps_match_enqueued_steps(lbib, overlap):
     assert rel(out[0][0], o["f"]) < 1e-12
 
 
+@pytest.mark.parametrize("config", [(1, 0, 0), (0, 32, 4), (0, 128, 2)])
+@pytest.mark.parametrize("overlap", [1, 0])
+def test_sweep_kernels_and_shapes_match_oracle(lbib, config, overlap):
+    """The row-tile sweep (x-rows staged in shared memory, 128-bit loads
+    and stores) and the one-node sweep in several block shapes compute the
+    same steps (FP64, 28^3 capsule in shear, with and without the far-field
+    sweep running beside the IB stage)."""
+    case = W.case_capsule_shear(n=28, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
+                                precision=W.PREC_FP64)
+    ctx = lbib.Context.from_case(case)
+    lbib.lbib_set_sweep_config(ctx.h, *config)
+    lbib.lbib_set_overlap(ctx.h, overlap)
+    ctx.step(20)
+    g = {"f": ctx.populations(), "fields": ctx.fields(), "markers": [ctx.markers(0)]}
+    ctx.close()
+    check_fp64(g, run_oracle(case, 20))
+
+
+def test_fp32_row_tile_sweep_full_size(lbib):
+    """The row-tile kernel on the 96^3 FP32 capsule case against the oracle."""
+    case = W.case_capsule_shear(Ca=0.05, Eb=0.01, kv=1.0)
+    ctx = lbib.Context.from_case(case)
+    lbib.lbib_set_sweep_config(ctx.h, 1, 0, 0)
+    ctx.step(30)
+    g = {"fields": ctx.fields(), "markers": [ctx.markers(0)]}
+    ctx.close()
+    check_fp32(g, run_oracle(case, 30))
+
+
 def test_autotuned_launch_configurations_keep_parity(lbib):
     """Every block shape and overlap mode the autotuner tries computes the
     same step: after tuning (which advances the run) the state still matches
