@@ -90,6 +90,10 @@ typedef struct {
     int kinematic;           /* membrane: 1 advects the markers with the interpolated fluid velocity
                               * (the kinematic IB of Sec. 3.4) and spreads the internal forces
                               * alone; 0 the dynamic IB (Newton + Verlet) */
+    int rigid_force;         /* rigid: 0 the hydrodynamic force and moment of the probe stress jumps
+                              * (Eqs. hydroForP, hydroForNu, as printed); 1 momentum exchange: minus
+                              * the previous step's IB force sum_l A_l F_l (and its moment) plus the
+                              * inertia of the fluid inside the body, rho_f V du/dt and I_f dw/dt */
 } lbib_body_params;
 
 typedef struct {
@@ -136,6 +140,11 @@ int lbib_sync(void *ctx);
 /* Density and velocity u = (sum f e + f_lb/2)/rho of the last collision
  * (Sec. 2.1): rho[ncell], u[3*ncell]; either may be NULL.  Synchronises. */
 int lbib_get_fields(void *ctx, double *rho, double *u, int on_device);
+
+/* Global mass and momentum of the post-collision populations, reduced on
+ * the GPU in FP64 in a fixed order: out[0] = sum over nodes of sum_i f_i,
+ * out[1..3] = sum over nodes of sum_i f_i e_i (host doubles).  Synchronises. */
+int lbib_get_totals(void *ctx, double *out);
 
 /* Post-collision populations, f[ncell*19] doubles.  Synchronises. */
 int lbib_get_populations(void *ctx, double *f, int on_device);

@@ -576,6 +576,7 @@ typedef struct {
     double gravity[3], u0[3], omega0[3];
     int bend_variant;
     int kinematic; /* membrane: markers advected with the fluid (kinematic IB) */
+    int rigid_force; /* rigid: 0 probe stress jump (as printed), 1 momentum exchange */
 } orc_body_params;
 
 typedef struct {
@@ -940,13 +941,45 @@ static int body_step(orc_sim *s, orc_body *b) {
         /* (3') rigid body: total force and moment of the element stresses,
          * plus reading: gravity minus buoyancy (rho_s - rho_f) V g. */
         double F[3] = {0, 0, 0}, M[3] = {0, 0, 0};
-        for (int t = 0; t < nt; ++t) {
-            double r[3], rxF[3];
-            sub3(&cen[3 * t], b->xc, r);
-            cross3(r, &Ftri[3 * t], rxF);
+        if (!b->p.rigid_force) {
+            for (int t = 0; t < nt; ++t) {
+                double r[3], rxF[3];
+                sub3(&cen[3 * t], b->xc, r);
+                cross3(r, &Ftri[3 * t], rxF);
+                for (int a = 0; a < 3; ++a) {
+                    F[a] += Ftri[3 * t + a];
+                    M[a] += rxF[a];
+                }
+            }
+        } else {
+            /* reading (momentum exchange, the alternative to the printed
+             * stress jump): the fluid pushes back with minus the IB force it
+             * received in the previous step, -sum_l A_l F_l and its moment,
+             * plus the rate of change of the momentum of the fluid inside the
+             * body moving with it, rho_f V du/dt and I_f dw/dt (backward
+             * differences, I_f the body's world-frame inertia scaled by
+             * rho_f / rho_s) */
+            for (int l = 0; l < nv; ++l) {
+                double r[3], f[3], rxf[3];
+                sub3(&b->X[3 * l], b->xc, r);
+                for (int a = 0; a < 3; ++a) f[a] = -Av[l] * b->Fl[3 * l + a];
+                cross3(r, f, rxf);
+                for (int a = 0; a < 3; ++a) {
+                    F[a] += f[a];
+                    M[a] += rxf[a];
+                }
+            }
+            double Rq[9], dw_body[3], Idw[3];
+            quat_to_R(b->q, Rq);
+            /* I_world (w - wp) = R I_b R^T (w - wp) */
+            for (int i = 0; i < 3; ++i)
+                dw_body[i] = Rq[i] * (b->w[0] - b->wp[0]) + Rq[3 + i] * (b->w[1] - b->wp[1]) +
+                             Rq[6 + i] * (b->w[2] - b->wp[2]);
+            for (int i = 0; i < 3; ++i)
+                Idw[i] = b->Ib[3 * i] * dw_body[0] + b->Ib[3 * i + 1] * dw_body[1] + b->Ib[3 * i + 2] * dw_body[2];
             for (int a = 0; a < 3; ++a) {
-                F[a] += Ftri[3 * t + a];
-                M[a] += rxF[a];
+                F[a] += b->Vb * (b->u[a] - b->up[a]);
+                M[a] += (Rq[3 * a] * Idw[0] + Rq[3 * a + 1] * Idw[1] + Rq[3 * a + 2] * Idw[2]) / b->p.density_ratio;
             }
         }
         for (int a = 0; a < 3; ++a) F[a] += (b->p.density_ratio - 1.0) * b->Vb * b->p.gravity[a];

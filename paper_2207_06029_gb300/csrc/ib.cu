@@ -692,7 +692,7 @@ __device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int v
                      R(S[RigidState::XC + 2] - B.origin[2])};
     R f[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const int t = vb * blockDim.x + threadIdx.x;
-    if (t < B.nt) {
+    if (t < B.nt && !B.rigid_force) {
         R Fh[3];
         tri_hydro<R>(B, t, Fh);
         const R *tg = (const R *)B.tri_geo + 8 * t;
@@ -703,6 +703,23 @@ __device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int v
         f[3] = r[1] * Fh[2] - r[2] * Fh[1];
         f[4] = r[2] * Fh[0] - r[0] * Fh[2];
         f[5] = r[0] * Fh[1] - r[1] * Fh[0];
+    } else if (t < B.nt) {
+        // momentum exchange: minus the IB force of the previous step, each
+        // corner carrying a third of the triangle's area (sum_l A_l F_l)
+        const R *tg = (const R *)B.tri_geo + 8 * t;
+        const R c = -tg[3] / R(3);
+        const R *Xr = (const R *)B.Xrel;
+        for (int q = 0; q < 3; ++q) {
+            const int v = B.tri[3 * t + q];
+            const R Fv[3] = {c * R(B.Fl[3 * v]), c * R(B.Fl[3 * v + 1]), c * R(B.Fl[3 * v + 2])};
+            const R r[3] = {Xr[3 * v] - xc[0], Xr[3 * v + 1] - xc[1], Xr[3 * v + 2] - xc[2]};
+            f[0] += Fv[0];
+            f[1] += Fv[1];
+            f[2] += Fv[2];
+            f[3] += r[1] * Fv[2] - r[2] * Fv[1];
+            f[4] += r[2] * Fv[0] - r[0] * Fv[2];
+            f[5] += r[0] * Fv[1] - r[1] * Fv[0];
+        }
     }
     for (int q = 0; q < 6; ++q) {
         const R w = warp_sum(f[q]);
@@ -727,6 +744,9 @@ __device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int v
         double acc = 0.0;
         for (int b = 0; b < nvb; ++b) acc += __ldcg(B.vol_part + 6 * b + lane);
         if (lane < 3) acc += (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + lane];
+        // momentum exchange: the fluid inside moves with the body, rho_f V du/dt
+        if (lane < 3 && B.rigid_force)
+            acc += S[RigidState::VOL] * (S[RigidState::U + lane] - S[RigidState::UP + lane]);
         sF[lane] = acc;
     }
     if (lane == 0) *B.vol_count = 0u;
@@ -752,6 +772,26 @@ __device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int v
     }
     __syncwarp();
     // dw/dt = I_world^-1 M = R I_b^-1 R^T M, lanes 0..2
+    if (B.rigid_force) {
+        // and I_f dw/dt = R I_b R^T (w - wp) rho_f / rho_s
+        if (lane < 3) {
+            const double *w = S + RigidState::W, *wp = S + RigidState::WP;
+            sY[lane] = sR[lane] * (w[0] - wp[0]) + sR[3 + lane] * (w[1] - wp[1]) + sR[6 + lane] * (w[2] - wp[2]);
+        }
+        __syncwarp();
+        double iy = 0.0;
+        if (lane < 3) {
+            const double *Ib = S + RigidState::IB + 3 * lane;
+            iy = Ib[0] * sY[0] + Ib[1] * sY[1] + Ib[2] * sY[2];
+        }
+        __syncwarp();
+        if (lane < 3) sY[lane] = iy;
+        __syncwarp();
+        if (lane < 3)
+            sF[3 + lane] += (sR[3 * lane] * sY[0] + sR[3 * lane + 1] * sY[1] + sR[3 * lane + 2] * sY[2]) /
+                            S[RigidState::DENS];
+        __syncwarp();
+    }
     if (lane < 3) sY[lane] = sR[lane] * sF[3] + sR[3 + lane] * sF[4] + sR[6 + lane] * sF[5];  // R^T M
     __syncwarp();
     double zl = 0.0;

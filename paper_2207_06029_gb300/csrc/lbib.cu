@@ -68,6 +68,7 @@ struct Ctx {
     uint32_t *d_step = nullptr;  // device step counter (tile flags of the IB force)
     uint32_t step_host = 0;      // host mirror of *d_step
     uint32_t *d_sr = nullptr;    // two-word seed counter of the stochastic rounding (bfloat16 storage)
+    double *d_tot = nullptr;     // partials, counter and result of the FP64 mass/momentum totals
     // CUDA graphs of one step, one per phase of the buffer rotation (period 6)
     cudaStream_t s_cap = nullptr;
     cudaGraphExec_t gexec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -284,6 +285,7 @@ BodyView make_view(Ctx *c, DevBody &b) {
     for (int a = 0; a < 3; ++a) v.origin[a] = b.origin[a];
     v.bend_variant = b.p.bend_variant;
     v.kinematic = b.p.kinematic;
+    v.rigid_force = b.p.rigid_force;
     v.Xbody = b.Xbody;
     v.rstate = b.rstate;
     v.bbox = b.bbox[b.bcur];
@@ -468,7 +470,8 @@ int lbib_create(const lbib_params *p, void **out) {
     c->d_err = (int *)dev_alloc(c, sizeof(int));
     c->d_step = (uint32_t *)dev_alloc(c, sizeof(uint32_t));
     c->d_sr = (uint32_t *)dev_alloc(c, 2 * sizeof(uint32_t));
-    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step || !c->d_sr) {
+    c->d_tot = (double *)dev_alloc(c, sizeof(double) * (size_t)totals_scratch_doubles());
+    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step || !c->d_sr || !c->d_tot) {
         g_create_error = "device allocation failed";
         lbib_destroy(c);
         return LBIB_ENOMEM;
@@ -957,6 +960,8 @@ int lbib_step(void *h, int nsteps) {
             cudaError_t e = cudaMemsetAsync(c->stamp, 0, sizeof(uint32_t) * (size_t)c->ntiles, c->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sr, 0, 2 * sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->d_tot, 0, sizeof(double) * (size_t)totals_scratch_doubles(), c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "step counter reset");
             c->step_host = 1;
         }
@@ -1033,6 +1038,22 @@ int lbib_get_fields(void *h, double *rho, double *u, int on_device) {
     }
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fields sync");
+    return rc;
+}
+
+int lbib_get_totals(void *h, double *out) {
+    Ctx *c = as_ctx(h);
+    if (!c || !out) return LBIB_EINVAL;
+    int rc = sync_ctx(c);
+    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    const int n = totals_scratch_doubles();
+    double *part = c->d_tot, *res = c->d_tot + (n - 8);
+    unsigned int *count = reinterpret_cast<unsigned int *>(c->d_tot + (n - 4));
+    cudaError_t e = launch_totals(c->prec, c->fA, c->L, part, count, res, c->stream);
+    c->launches++;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "totals");
     return rc;
 }
 

@@ -179,6 +179,7 @@ struct BodyView {
     double origin[3];       // reference point of relative positions and of the volume sum
     int bend_variant;
     int kinematic;          // membrane markers advected with the fluid (kinematic IB)
+    int rigid_force;        // rigid: 0 probe stress jump, 1 momentum exchange
     // rigid body
     const double *Xbody;    // [3nv] rest coordinates about the centre
     double *rstate;         // rigid state block, see RigidState

@@ -16,6 +16,11 @@ cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, con
                          const uint32_t *step, const Lattice &L, void *fields, int part, const int *box,
                          uint32_t *sr, int parity, int nsm, cudaStream_t s);
 cudaError_t prepare_sweep_kernels();
+// global mass and momentum (FP64): part holds totals_scratch_doubles() doubles,
+// count one word that starts (and is left) at zero, out 4 doubles
+cudaError_t launch_totals(int prec, const void *fin, const Lattice &L, double *part, unsigned int *count,
+                          double *out, cudaStream_t s);
+int totals_scratch_doubles();
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
                                     void *fields, cudaStream_t s);
 cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s);

@@ -599,6 +599,80 @@ cudaError_t launch_batch_sweep(int prec, const BatchTables &T, const BatchGrid &
     }
 }
 
+// Global mass and momentum of the populations in FP64: sum over nodes of
+// sum_i f_i and sum_i f_i e_i.  Each node's 19 deviations are summed in the
+// arithmetic precision, the nodes in FP64 (the resting weights add 1 per node
+// to the mass and nothing to the momentum).  Fixed-order block partials; the
+// last block to finish sums them in block order, so the result does not
+// depend on scheduling.
+constexpr int kTotBlocks = 512;
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_totals(const S *__restrict__ fin, Lattice L, double *__restrict__ part,
+                                                unsigned int *__restrict__ count, double *__restrict__ out) {
+    __shared__ double red[4][256];
+    __shared__ bool last;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long st = L.stride;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.ncell; idx += gridDim.x * blockDim.x) {
+        R m = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R gi = Pop<S, R>::ld(fin + (long long)i * st + idx);
+            m += gi;
+            if (ex(i)) jx += R(ex(i)) * gi;
+            if (ey(i)) jy += R(ey(i)) * gi;
+            if (ez(i)) jz += R(ez(i)) * gi;
+        }
+        acc[0] += (double)m;
+        acc[1] += (double)jx;
+        acc[2] += (double)jy;
+        acc[3] += (double)jz;
+    }
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = red[q][0];
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + 4 * b + threadIdx.x);
+        out[threadIdx.x] = threadIdx.x == 0 ? t + (double)L.ncell : t;
+    }
+    if (threadIdx.x == 0) *count = 0u;
+}
+
+template <typename S, typename R>
+static cudaError_t totals_t(const void *fin, const Lattice &L, double *part, unsigned int *count, double *out,
+                            cudaStream_t s) {
+    int g = (L.ncell + 255) / 256;
+    if (g > kTotBlocks) g = kTotBlocks;
+    k_totals<S, R><<<g, 256, 0, s>>>((const S *)fin, L, part, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(int prec, const void *fin, const Lattice &L, double *part, unsigned int *count,
+                          double *out, cudaStream_t s) {
+    switch (prec) {
+        case 0: return totals_t<double, double>(fin, L, part, count, out, s);
+        case 1: return totals_t<float, float>(fin, L, part, count, out, s);
+        case 2: return totals_t<__half, float>(fin, L, part, count, out, s);
+        default: return totals_t<__nv_bfloat16, float>(fin, L, part, count, out, s);
+    }
+}
+
+int totals_scratch_doubles() { return 4 * kTotBlocks + 8; }
+
 // Kernel attributes set once before any launch or capture.
 cudaError_t prepare_sweep_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_sweep_tile<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

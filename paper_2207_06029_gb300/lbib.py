@@ -38,7 +38,7 @@ class lbib_body_params(C.Structure):
     _fields_ = [("rigid", C.c_int), ("ks0", C.c_double), ("Eb", C.c_double), ("kv", C.c_double),
                 ("thickness", C.c_double), ("density_ratio", C.c_double), ("ref_radius", C.c_double),
                 ("gravity", C.c_double * 3), ("u0", C.c_double * 3), ("omega0", C.c_double * 3),
-                ("bend_variant", C.c_int), ("kinematic", C.c_int)]
+                ("bend_variant", C.c_int), ("kinematic", C.c_int), ("rigid_force", C.c_int)]
 
 
 class lbib_body_state(C.Structure):
@@ -76,7 +76,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
-           "lbib_get_fields", "lbib_get_populations", "lbib_get_markers", "lbib_get_body", "lbib_counters",
+           "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
            "lbib_device_bytes", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
@@ -106,6 +106,7 @@ def load():
         L.lbib_sync.argtypes = [vp]
         L.lbib_get_fields.argtypes = [vp, vp, vp, C.c_int]
         L.lbib_get_populations.argtypes = [vp, vp, C.c_int]
+        L.lbib_get_totals.argtypes = [vp, dp]
         L.lbib_get_markers.argtypes = [vp, C.c_int, vp, vp, vp]
         L.lbib_get_body.argtypes = [vp, C.c_int, C.POINTER(lbib_body_state)]
         L.lbib_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
@@ -213,6 +214,13 @@ def lbib_get_fields(ctx, rho, u):
     return _check(ctx, load().lbib_get_fields(ctx, pr, pu, max(dev, dev2)))
 
 
+def lbib_get_totals(ctx):
+    """(mass, momentum[3]) of the populations, reduced on the GPU in FP64."""
+    out = (C.c_double * 4)()
+    _check(ctx, load().lbib_get_totals(ctx, out))
+    return out[0], np.array(out[1:4])
+
+
 def lbib_get_populations(ctx, f):
     pf, dev = _ptr(f)
     return _check(ctx, load().lbib_get_populations(ctx, pf, dev))
@@ -303,7 +311,7 @@ def make_params(n, tau, *, bc=(0, 0, 0), wall_u=None, body_force=(0, 0, 0), prec
 
 
 def make_body_params(*, rigid=False, ks0=0.0, Eb=0.0, kv=0.0, thickness=1.0, density_ratio=1.0, ref_radius=1.0,
-                     gravity=(0, 0, 0), u0=(0, 0, 0), omega0=(0, 0, 0), bend_variant=0, kinematic=0):
+                     gravity=(0, 0, 0), u0=(0, 0, 0), omega0=(0, 0, 0), bend_variant=0, kinematic=0, rigid_force=0):
     bp = lbib_body_params()
     bp.rigid = int(rigid)
     bp.ks0, bp.Eb, bp.kv = float(ks0), float(Eb), float(kv)
@@ -314,6 +322,7 @@ def make_body_params(*, rigid=False, ks0=0.0, Eb=0.0, kv=0.0, thickness=1.0, den
         bp.omega0[a] = float(omega0[a])
     bp.bend_variant = int(bend_variant)
     bp.kinematic = int(kinematic)
+    bp.rigid_force = int(rigid_force)
     return bp
 
 

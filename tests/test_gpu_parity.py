@@ -155,6 +155,21 @@ def test_fp64_kinematic_capsule_in_shear(lbib):
     check_fp64(g, o)
 
 
+def test_fp64_momentum_exchange_rigid_bodies(lbib):
+    """Momentum-exchange rigid-body force variant: a heavy sphere settling in
+    a walled box and a free sphere in Couette flow, 30 steps."""
+    v, f = W.icosphere(3, 3.5, (10.0, 11.0, 17.0))
+    settle = W.Case("settle_mx", (20, 22, 30), 0.7, (W.WALL, W.WALL, W.WALL), np.zeros((6, 3)),
+                    precision=W.PREC_FP64, bodies=[W.Body(v, f, rigid=True, density_ratio=1.5, ref_radius=3.5,
+                                                          gravity=(0.0, 0.0, -2e-5), rigid_force=1)])
+    couette = W.case_couette_sphere()
+    couette.bodies[0].rigid_force = 1
+    for case in (settle, couette):
+        g = run_gpu(lbib, case, 30)
+        o = run_oracle(case, 30)
+        check_fp64(g, o)
+
+
 def test_fp64_two_bodies_and_gravity_periodic(lbib):
     """Two bodies in one periodic lattice: a settling rigid sphere and a
     capsule (shared force field, several spreads per step)."""
@@ -294,6 +309,30 @@ def test_autotuned_launch_configurations_keep_parity(lbib):
 # ---------------------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [(W.PREC_FP64, 1e-12), (W.PREC_FP32, 2e-6)])
+def test_fp64_totals_conservation_and_forcing(lbib, prec, tol, paper_e):
+    """The GPU's FP64 mass/momentum reduction: on a periodic lattice the
+    mass is constant and the momentum grows by exactly ncell * g_ext per step
+    (streaming conserves both; the Guo collision adds the force, Eq.
+    forcing), and at the end both equal the sums over the oracle's
+    populations.  FP32 storage: within its rounding."""
+    g = np.array([2e-6, -1e-6, 5e-7])
+    case = W.case_empty(n=(33, 17, 12), tau=0.7, gext=tuple(g), precision=prec, seed=11)
+    ctx = lbib.Context.from_case(case)
+    m0, p0 = lbib.lbib_get_totals(ctx.h)
+    nc = case.ncell
+    for k in range(1, 4):
+        ctx.step(5)
+        m, p = lbib.lbib_get_totals(ctx.h)
+        assert abs(m - m0) <= tol * nc
+        assert np.abs(p - p0 - 5 * k * nc * g).max() <= tol * nc * 1e-2
+    f = ctx.populations()
+    ctx.close()
+    o = run_oracle(case, 15)["f"]
+    assert abs(m - o.sum()) <= tol * nc
+    assert np.abs(p - (o @ paper_e).sum(axis=0)).max() <= tol * nc * 1e-2
+
 
 def test_zero_steps_and_empty_lattice(lbib):
     case = W.case_empty(n=(5, 4, 3), precision=W.PREC_FP64, seed=7)

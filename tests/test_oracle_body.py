@@ -168,3 +168,23 @@ def test_kinematic_membrane_is_carried_by_a_uniform_flow():
     rho, u = s.fields()
     assert np.abs(u - u0).max() < 1e-13 and np.abs(rho - 1.0).max() < 1e-13
     s.close()
+
+
+def test_momentum_exchange_sphere_spins_at_half_shear_rate():
+    """The momentum-exchange rigid-body force (minus the IB force given to
+    the fluid, plus the inertia of the enclosed fluid) gives the same Stokes
+    rotation omega = shear_rate/2 of a free neutrally buoyant sphere as the
+    printed stress-jump force (same 32^3 Couette cell, 200 steps)."""
+    case = W.case_couette_sphere(steps=200)
+    s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
+    s.set_fields(*case.initial_fields())
+    b = case.bodies[0]
+    kw = b.kwargs()
+    kw["rigid_force"] = 1
+    s.add_body(b.verts, b.tris, **kw)
+    assert s.step(200) == 0
+    st = s.body(0)
+    gamma = 0.02 / 31.0
+    assert abs(st["omega"][1] / (gamma / 2) - 1.0) < 0.02
+    assert np.abs(st["xc"] - 15.5).max() < 1e-10
+    s.close()
