@@ -302,7 +302,7 @@ def batch_leg(args):
         ctxs.append(ctx)
     torch.cuda.synchronize()
     batch = lbib.Batch(ctxs, stream=stream.cuda_stream)
-    tuned = batch.autotune(6) if args.autotune else (256, 0)
+    tuned = batch.autotune(6) if args.autotune else (256, 0, 4)
     batch.step(12)
     batch.sync()
     steps = max(6, (args.batch_steps // 6) * 6)
@@ -322,7 +322,8 @@ def batch_leg(args):
            "value": cells * (steps + 1) / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps + 1,
            "ms_per_step": ms / (steps + 1), "cells": cells, "markers": sum(len(c.bodies[0].verts) for c in cases),
            "launches_per_step": (l1 - l0) / (steps + 1),
-           "autotuned": {"sweep_threads": tuned[0], "lattice_order": ["as given", "largest first"][tuned[1]]},
+           "autotuned": {"sweep_threads": tuned[0], "lattice_order": ["as given", "largest first"][tuned[1]],
+                         "cells_per_thread": tuned[2]},
            "hbm_frac_sweep_bytes": cells * 152.0 * (steps + 1) / (ms * 1e-3) / 1e9 / hbm_peak()[0],
            "parameters": {"Ca": list(W.BATCH_CA), "Eb": list(W.BATCH_EB), "mass_ratio": list(W.BATCH_MASS_RATIOS)},
            "inputs": "larger than L2 (6.2 GB of populations per step)"}

@@ -241,10 +241,11 @@ int lbib_batch_sync(void *batch);
 /* Steps taken through the batch and kernels launched by it. */
 int lbib_batch_counters(void *batch, long long *steps, long long *launches);
 
-/* Times `steps` steps for each sweep block size (128, 256, 512 threads) and
- * lattice order in the sweep launch (as given; largest lattice first) and
- * keeps the fastest; the contexts advance by about 14 + 12 * steps steps.
- * choice (optional, 2 ints): threads, order. */
+/* Times `steps` steps for each sweep block size (128, 256, 512 threads),
+ * cells per sweep thread (1, 4) and lattice order in the sweep launch (as
+ * given; largest lattice first) and keeps the fastest; the contexts advance
+ * by about 12 * (7 + 2 * steps) steps.  choice (optional, 3 ints): threads,
+ * order, cells per thread. */
 int lbib_batch_autotune(void *batch, int steps, int *choice);
 
 /* Releases the batch (not its contexts). */

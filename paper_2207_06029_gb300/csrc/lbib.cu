@@ -1314,7 +1314,7 @@ struct Batch {
     BatchTables T{};
     BatchGrid G{};
     long long steps = 0;  // steps since the last table build (phase origin)
-    int sweep_threads = 256, order = 0;
+    int sweep_threads = 256, order = 0, sweep_cpt = 4;
     cudaGraphExec_t g6 = nullptr;
     long long launches = 0, total_steps = 0;
     std::string msg;
@@ -1407,7 +1407,8 @@ int batch_build(Batch *b) {
                          [&](int x, int y) { return lat[x].ncell > lat[y].ncell; });
     std::vector<int> sweep_pre(1, 0);
     for (int i = 0; i < nl; ++i)
-        sweep_pre.push_back(sweep_pre.back() + (lat[order[i]].ncell + b->sweep_threads - 1) / b->sweep_threads);
+        sweep_pre.push_back(sweep_pre.back() + (lat[order[i]].ncell + b->sweep_threads * b->sweep_cpt - 1) /
+                                                   (b->sweep_threads * b->sweep_cpt));
     // block -> item maps
     auto blocks_of = [](const std::vector<int> &pre) {
         std::vector<int> blk(pre.back() > 0 ? pre.back() : 1, 0);
@@ -1488,6 +1489,7 @@ int batch_build(Batch *b) {
     T.rf_blk = reinterpret_cast<const int *>(d + o_brf);
     T.rm_blk = reinterpret_cast<const int *>(d + o_brm);
     T.sweep_threads = b->sweep_threads;
+    T.sweep_cpt = b->sweep_cpt;
     b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back()};
     b->steps = 0;
     for (int i = 0; i < nl; ++i) b->base[i] = b->ctx[i]->steps;
@@ -1678,40 +1680,45 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bcuda(b, cudaGetLastError(), "autotune events");
-    const int threads[] = {128, 256, 512};
+    const int threads[] = {128, 256, 512}, cpts[] = {1, 4};
     float best = 1e30f;
-    int best_t = b->sweep_threads, best_o = b->order, rc = LBIB_OK;
+    int best_t = b->sweep_threads, best_o = b->order, best_c = b->sweep_cpt, rc = LBIB_OK;
     for (int o = 0; o < 2 && !rc; ++o)
-        for (int t : threads) {
-            b->sweep_threads = t;
-            b->order = o;
-            if ((rc = batch_build(b))) break;
-            if ((rc = lbib_batch_step(h, 7))) break;  // captures the graph, untimed
-            float ms = 1e30f;
-            for (int rep = 0; rep < 2 && !rc; ++rep) {
-                cudaEventRecord(e0, b->stream);
-                rc = lbib_batch_step(h, steps);
-                cudaEventRecord(e1, b->stream);
-                cudaEventSynchronize(e1);
-                float t_ms = 0.f;
-                cudaEventElapsedTime(&t_ms, e0, e1);
-                if (t_ms < ms) ms = t_ms;
+        for (int cp : cpts)
+            for (int t : threads) {
+                b->sweep_threads = t;
+                b->order = o;
+                b->sweep_cpt = cp;
+                if ((rc = batch_build(b))) break;
+                if ((rc = lbib_batch_step(h, 7))) break;  // captures the graph, untimed
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2 && !rc; ++rep) {
+                    cudaEventRecord(e0, b->stream);
+                    rc = lbib_batch_step(h, steps);
+                    cudaEventRecord(e1, b->stream);
+                    cudaEventSynchronize(e1);
+                    float t_ms = 0.f;
+                    cudaEventElapsedTime(&t_ms, e0, e1);
+                    if (t_ms < ms) ms = t_ms;
+                }
+                if (rc) break;
+                if (ms < best) {
+                    best = ms;
+                    best_t = t;
+                    best_o = o;
+                    best_c = cp;
+                }
             }
-            if (rc) break;
-            if (ms < best) {
-                best = ms;
-                best_t = t;
-                best_o = o;
-            }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->sweep_threads = best_t;
     b->order = best_o;
+    b->sweep_cpt = best_c;
     int rc2 = batch_build(b);
     if (choice) {
         choice[0] = best_t;
         choice[1] = best_o;
+        choice[2] = best_c;
     }
     return rc ? rc : rc2;
 }

@@ -228,6 +228,7 @@ struct BatchTables {
     const int *rm_pre;     // [nrigid + 1] blocks of 8 marker warps
     const int *sweep_blk, *mom_blk, *mls_blk, *memb_blk, *rf_blk, *rm_blk;  // item of each block
     int sweep_threads;     // threads per sweep block
+    int sweep_cpt;         // cells per sweep thread (blocks per lattice = cells / (threads * cpt))
 };
 
 // Copies a table entry into shared memory with the whole block (the batch

@@ -432,8 +432,10 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
     }
 }
 
-// All lattices of a batch: block b belongs to sweep slot sweep_blk[b]; its
-// threads take consecutive cells of that lattice (x fastest).
+// All lattices of a batch: block b belongs to sweep slot sweep_blk[b]; the
+// blocks of a lattice stride over its cells (x fastest), a few cells per
+// thread so that the per-block set-up (the lattice entry staged in shared
+// memory) is amortised.
 template <typename S, typename R>
 __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int store_fields) {
     __shared__ Lattice L;
@@ -441,14 +443,15 @@ __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int st
     const int l = __ldg(T.sweep_lat + slot);
     stage_shared(L, T.lat + l);
     const LatRef &F = T.ref[phase * T.nl + l];
-    const int c = (blockIdx.x - __ldg(T.sweep_pre + slot)) * blockDim.x + threadIdx.x;
-    if (c >= L.ncell) return;
-    const int x = c % L.nx, yz = c / L.nx, y = yz % L.ny, z = yz / L.ny;
+    const int b0 = __ldg(T.sweep_pre + slot), nb = __ldg(T.sweep_pre + slot + 1) - b0;
     const uint32_t step = F.stamp ? *F.d_step : 0u;
     const uint32_t seed = F.sr[F.parity];
-    if (c == 0) F.sr[F.parity ^ 1] = seed + 1u;
-    sweep_cell<S, R>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L,
-                     store_fields ? (R *)F.fields : nullptr, x, y, z, seed);
+    if (blockIdx.x == b0 && threadIdx.x == 0) F.sr[F.parity ^ 1] = seed + 1u;
+    R *fields = store_fields ? (R *)F.fields : nullptr;
+    for (int c = (blockIdx.x - b0) * blockDim.x + threadIdx.x; c < L.ncell; c += nb * blockDim.x) {
+        const int x = c % L.nx, yz = c / L.nx, y = yz % L.ny, z = yz / L.ny;
+        sweep_cell<S, R>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L, fields, x, y, z, seed);
+    }
 }
 
 // f = f^eq(rho, u) from double fields (Eq. eqfunc), stored as deviations.

@@ -463,7 +463,8 @@ def lbib_batch_counters(batch):
 
 
 def lbib_batch_autotune(batch, steps):
-    ch = (C.c_int * 2)()
+    """(threads per sweep block, lattice order, cells per sweep thread) chosen."""
+    ch = (C.c_int * 3)()
     _bcheck(batch, load().lbib_batch_autotune(batch, int(steps), ch))
     return tuple(ch)
 
