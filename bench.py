@@ -333,14 +333,19 @@ def batch_leg(args):
     return out
 
 
-def serve_leg(args, mode, precision, max_active=64):
+def serve_leg(args, mode, precision, max_active=64, batch_cells=0, small=False):
     """A seeded Poisson stream (4 requests/s) of capsule-in-shear and
     settling-sphere runs through the serving engine; latency from submission
     to completion."""
     from paper_2207_06029_gb300 import lbib
     from paper_2207_06029_gb300 import workloads as W
-    stream = W.serve_stream(count=args.serve_requests, precision=precision)
-    server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=max_active, mode=mode)
+    if small:
+        stream = W.serve_stream(count=64, seed=9, rate=40.0, n_range=(32, 64), step_range=(500, 2000),
+                                precision=precision)
+    else:
+        stream = W.serve_stream(count=args.serve_requests, precision=precision)
+    server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=max_active, mode=mode,
+                                    batch_cells=batch_cells)
     reqs = [(t, lbib.request_from_case(case, steps), case, steps) for t, case, steps in stream]
     t0 = time.perf_counter()
     ids = []
@@ -356,7 +361,7 @@ def serve_leg(args, mode, precision, max_active=64):
         if h is not None:
             lbib.lbib_destroy(h)
         if rc:
-            failed.append({"request": case.name, "steps": steps, "code": rc})
+            failed.append({"request": case.name, "steps": steps, "code": rc, "error": times["error"]})
         else:
             lat.append(times["latency_s"])
     makespan = time.perf_counter() - t0
@@ -503,11 +508,16 @@ def main():
         from paper_2207_06029_gb300 import workloads as W
         line["serve"] = {
             "stream": f"{args.serve_requests} requests, Poisson 4/s, half capsule-in-shear half settling sphere, "
-                      "cubic N~U{32..160}, steps~U{1000..6000}, budget 150 GB",
+                      "cubic N~U{32..160} (capsules N>=48), steps~U{1000..6000}, budget 150 GB",
             "batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32),
-            "batched_fp32_max4": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, max_active=4),
+            "batched_fp32_srpt_8M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, batch_cells=8 << 20),
             "plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32),
-            "batched_fp16_dev": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV),
+            "batched_fp16_dev_srpt_8M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV,
+                                                  batch_cells=8 << 20),
+            "small_stream": "64 requests, Poisson 40/s, same mix, cubic N~U{32..64} (capsules 48..64), "
+                            "steps~U{500..2000}",
+            "small_batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, small=True),
+            "small_plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32, small=True),
         }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, workload=args.workload)

@@ -273,6 +273,9 @@ typedef struct {
     int chunk_steps;    /* longest chunk between admissions (> 0) */
     int max_active;     /* most runs in the batch at once (>= 1) */
     int mode;           /* LBIB_SERVE_BATCHED or LBIB_SERVE_PLAIN */
+    long long batch_cells; /* batched mode: 0 advances every admitted run in each chunk; > 0 advances
+                            * the runs with the least remaining work (cells x steps) up to this many
+                            * lattice cells (at least one run), the others waiting resident */
 } lbib_serve_params;
 
 typedef struct {
@@ -280,6 +283,7 @@ typedef struct {
     double queued_s;    /* submission to admission */
     double latency_s;   /* submission to completion */
     double done_s;      /* completion time since the server started */
+    char error[160];    /* message of a failed run ("" otherwise) */
 } lbib_serve_times;
 
 typedef struct {

@@ -1309,6 +1309,7 @@ struct Batch {
     int prec = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t s_cap = nullptr;  // private capture stream: the batch stream is never in capture mode
     cudaEvent_t done = nullptr;
     void *dmem = nullptr;
     BatchTables T{};
@@ -1496,9 +1497,9 @@ int batch_build(Batch *b) {
     return LBIB_OK;
 }
 
-int batch_enqueue(Batch *b, int phase, bool store) {
-    cudaError_t e = launch_batch_ib(b->prec, b->T, b->G, phase, b->stream);
-    if (e == cudaSuccess) e = launch_batch_sweep(b->prec, b->T, b->G, phase, store ? 1 : 0, b->stream);
+int batch_enqueue(Batch *b, int phase, bool store, cudaStream_t st) {
+    cudaError_t e = launch_batch_ib(b->prec, b->T, b->G, phase, st);
+    if (e == cudaSuccess) e = launch_batch_sweep(b->prec, b->T, b->G, phase, store ? 1 : 0, st);
     if (e != cudaSuccess) return bcuda(b, e, "batch launch");
     return LBIB_OK;
 }
@@ -1510,12 +1511,12 @@ int batch_launches_per_step(const Batch *b) {
 }
 
 int batch_capture6(Batch *b) {
-    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(b->s_cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "batch capture");
     int rc = LBIB_OK;
-    for (int k = 0; k < 6 && rc == LBIB_OK; ++k) rc = batch_enqueue(b, k, false);
+    for (int k = 0; k < 6 && rc == LBIB_OK; ++k) rc = batch_enqueue(b, k, false, b->s_cap);
     cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(b->stream, &g);
+    e = cudaStreamEndCapture(b->s_cap, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -1589,6 +1590,7 @@ int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out) {
         e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         b->own_stream = e == cudaSuccess;
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->s_cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     b->ctx_ev.assign(n, nullptr);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ctx_ev[i], cudaEventDisableTiming);
@@ -1638,7 +1640,7 @@ int lbib_batch_step(void *h, int nsteps) {
             remaining -= 6;
             b->launches += 6 * batch_launches_per_step(b);
         } else {
-            int rc = batch_enqueue(b, phase, remaining == 1);
+            int rc = batch_enqueue(b, phase, remaining == 1, b->stream);
             if (rc) return rc;
             b->steps += 1;
             remaining -= 1;
@@ -1731,6 +1733,7 @@ void lbib_batch_destroy(void *h) {
     for (cudaEvent_t ev : b->ctx_ev)
         if (ev) cudaEventDestroy(ev);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->s_cap) cudaStreamDestroy(b->s_cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -48,6 +49,7 @@ struct Request {
     size_t bytes = 0;
     int state = LBIB_REQ_QUEUED;
     int err = 0;
+    std::string msg;  // why a failed run failed
     Clock::time_point t_submit, t_admit, t_done;
 };
 
@@ -125,11 +127,17 @@ int start_request(Server *s, Request *r) {
     return LBIB_OK;
 }
 
-void finish(Server *s, Request *r, int err) {
+void finish(Server *s, Request *r, int err, const char *why = nullptr) {
     r->t_done = Clock::now();
     r->err = err;
     r->state = err ? LBIB_REQ_FAILED : LBIB_REQ_DONE;
     if (err) {
+        if (why)
+            r->msg = why;
+        else if (r->ctx)
+            r->msg = lbib_last_error(r->ctx);
+        else
+            r->msg = lbib_last_error(nullptr);
         if (r->ctx) lbib_destroy(r->ctx);
         r->ctx = nullptr;
         s->bytes_in_use -= r->bytes;
@@ -157,7 +165,7 @@ void worker_loop(Server *s) {
                 if (need > s->sp.hbm_budget) {  // can never fit
                     s->queue.pop_front();
                     r->t_admit = Clock::now();
-                    finish(s, r, LBIB_ENOMEM);
+                    finish(s, r, LBIB_ENOMEM, "the run's memory estimate exceeds the budget");
                     s->cv_done.notify_all();
                     continue;
                 }
@@ -195,6 +203,24 @@ void worker_loop(Server *s) {
             act = s->active;
         }
         if (act.empty()) continue;
+        if (s->sp.mode == LBIB_SERVE_BATCHED && s->sp.batch_cells > 0 && act.size() > 1) {
+            // shortest remaining work first: the runs with the least
+            // remaining cell updates, up to batch_cells lattice cells (at
+            // least one run); the others stay resident and wait
+            std::stable_sort(act.begin(), act.end(), [](const Request *a, const Request *b) {
+                const double wa = (double)a->remaining * a->p.nx * a->p.ny * a->p.nz;
+                const double wb = (double)b->remaining * b->p.nx * b->p.ny * b->p.nz;
+                return wa < wb;
+            });
+            long long cells = 0;
+            size_t k = 0;
+            for (; k < act.size(); ++k) {
+                const long long c = (long long)act[k]->p.nx * act[k]->p.ny * act[k]->p.nz;
+                if (k > 0 && cells + c > s->sp.batch_cells) break;
+                cells += c;
+            }
+            act.resize(k);
+        }
         long long chunk = s->sp.chunk_steps > 0 ? s->sp.chunk_steps : 500;
         for (Request *r : act) chunk = std::min(chunk, r->remaining);
         const auto t_a = Clock::now();
@@ -226,6 +252,9 @@ void worker_loop(Server *s) {
         s->busy_s += seconds(t_a, t_b);
         ++s->chunks;
         std::vector<Request *> keep;
+        for (Request *r : s->active)  // runs that waited this chunk
+            if (std::find(act.begin(), act.end(), r) == act.end()) keep.push_back(r);
+        const size_t waited = keep.size();
         for (Request *r : act) {
             int rc = LBIB_OK;
             if (brc) rc = lbib_sync(r->ctx);  // which run failed
@@ -245,10 +274,11 @@ void worker_loop(Server *s) {
                 keep.push_back(r);
             }
         }
-        if (brc && keep.size() == act.size()) {
+        if (brc && keep.size() - waited == act.size()) {
             // a batch-level failure no single context reports: fail them all
-            for (Request *r : keep) finish(s, r, brc);
-            keep.clear();
+            const std::string why = batch ? lbib_batch_last_error(batch) : lbib_batch_last_error(nullptr);
+            for (size_t k = waited; k < keep.size(); ++k) finish(s, keep[k], brc, why.c_str());
+            keep.resize(waited);
             stale = true;
         }
         s->active = keep;
@@ -353,6 +383,7 @@ int lbib_serve_take(void *h, long long id, void **ctx, lbib_serve_times *t) {
         t->latency_s = seconds(r->t_submit, r->t_done);
         t->submit_s = seconds(s->t0, r->t_submit);
         t->done_s = seconds(s->t0, r->t_done);
+        std::snprintf(t->error, sizeof(t->error), "%s", r->msg.c_str());
     }
     const int err = r->state == LBIB_REQ_FAILED ? r->err : LBIB_OK;
     *ctx = r->ctx;

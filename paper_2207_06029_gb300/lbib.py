@@ -51,12 +51,13 @@ LBIB_SERVE_BATCHED, LBIB_SERVE_PLAIN = 0, 1
 
 
 class lbib_serve_params(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("chunk_steps", C.c_int), ("max_active", C.c_int), ("mode", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("chunk_steps", C.c_int), ("max_active", C.c_int), ("mode", C.c_int),
+                ("batch_cells", C.c_longlong)]
 
 
 class lbib_serve_times(C.Structure):
     _fields_ = [("submit_s", C.c_double), ("queued_s", C.c_double), ("latency_s", C.c_double),
-                ("done_s", C.c_double)]
+                ("done_s", C.c_double), ("error", C.c_char * 160)]
 
 
 class lbib_serve_summary(C.Structure):
@@ -534,8 +535,8 @@ def lbib_request_destroy(req):
     load().lbib_request_destroy(req)
 
 
-def lbib_serve_create(hbm_budget, chunk_steps=500, max_active=64, mode=LBIB_SERVE_BATCHED):
-    sp = lbib_serve_params(int(hbm_budget), int(chunk_steps), int(max_active), int(mode))
+def lbib_serve_create(hbm_budget, chunk_steps=500, max_active=64, mode=LBIB_SERVE_BATCHED, batch_cells=0):
+    sp = lbib_serve_params(int(hbm_budget), int(chunk_steps), int(max_active), int(mode), int(batch_cells))
     h = C.c_void_p()
     _scheck(load().lbib_serve_create(C.byref(sp), C.byref(h)), "server")
     return h
@@ -559,7 +560,7 @@ def lbib_serve_take(server, rid):
     t = lbib_serve_times()
     rc = load().lbib_serve_take(server, int(rid), C.byref(h), C.byref(t))
     return (h if h.value else None), {"submit_s": t.submit_s, "queued_s": t.queued_s, "latency_s": t.latency_s,
-                                      "done_s": t.done_s}, rc
+                                      "done_s": t.done_s, "error": t.error.decode(errors="replace")}, rc
 
 
 def lbib_serve_stats(server):

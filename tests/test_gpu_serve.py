@@ -66,9 +66,13 @@ def take(L, server, rid, case):
     return out, times
 
 
-def test_each_result_is_the_same_alone_and_in_the_mix(lbib):
+@pytest.mark.parametrize("batch_cells", [0, 40000])
+def test_each_result_is_the_same_alone_and_in_the_mix(lbib, batch_cells):
+    """batch_cells = 0: every admitted run in every chunk; 40000: the runs
+    with the least remaining work, about one lattice per chunk, the others
+    waiting resident."""
     reqs = requests(W.PREC_FP64)
-    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=16, max_active=8)
+    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=16, max_active=8, batch_cells=batch_cells)
     ids = []
     for k, (case, steps) in enumerate(reqs):
         ids.append(lbib.lbib_serve_submit(server, lbib.request_from_case(case, steps)))
@@ -116,3 +120,27 @@ def test_memory_budget_limits_admission(lbib):
     lbib.lbib_serve_destroy(server)
     assert stats["peak_bytes"] <= one
     assert stats["runs_done"] == len(reqs)
+
+
+def test_taking_and_destroying_results_while_the_server_runs(lbib):
+    """Results are taken and destroyed on the caller's thread while the
+    worker keeps admitting, rebuilding and capturing batches: no run fails."""
+    rng = np.random.default_rng(5)
+    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=20, max_active=16)
+    ids, cases = [], []
+    for k in range(14):
+        n = int(rng.integers(24, 41))
+        case = W.case_capsule_shear(n=n, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.1, Eb=0.005, kv=1.0,
+                                    precision=W.PREC_FP32)
+        ids.append(lbib.lbib_serve_submit(server, lbib.request_from_case(case, int(rng.integers(30, 90)))))
+        cases.append(case)
+        if k % 3 == 2:
+            time.sleep(0.01)
+    for rid in ids:
+        rc, state = lbib.lbib_serve_wait(server, rid, WAIT_S)
+        h, times, rc = lbib.lbib_serve_take(server, rid)
+        assert rc == lbib.LBIB_OK, times["error"]
+        lbib.lbib_destroy(h)
+    stats = lbib.lbib_serve_stats(server)
+    lbib.lbib_serve_destroy(server)
+    assert stats["runs_done"] == len(ids) and stats["runs_failed"] == 0
