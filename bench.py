@@ -322,8 +322,9 @@ def batch_leg(args):
            "value": cells * (steps + 1) / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps + 1,
            "ms_per_step": ms / (steps + 1), "cells": cells, "markers": sum(len(c.bodies[0].verts) for c in cases),
            "launches_per_step": (l1 - l0) / (steps + 1),
-           "autotuned": {"sweep_threads": tuned[0], "lattice_order": ["as given", "largest first"][tuned[1]],
-                         "cells_per_thread": tuned[2]},
+           "autotuned": {"sweep": ("one launch per lattice" if tuned[0] == 0 else
+                                   f"batched, {tuned[0]} threads, {tuned[2]} cells per thread"),
+                         "lattice_order": ["as given", "largest first"][tuned[1]]},
            "hbm_frac_sweep_bytes": cells * 152.0 * (steps + 1) / (ms * 1e-3) / 1e9 / hbm_peak()[0],
            "parameters": {"Ca": list(W.BATCH_CA), "Eb": list(W.BATCH_EB), "mass_ratio": list(W.BATCH_MASS_RATIOS)},
            "inputs": "larger than L2 (6.2 GB of populations per step)"}

@@ -241,11 +241,12 @@ int lbib_batch_sync(void *batch);
 /* Steps taken through the batch and kernels launched by it. */
 int lbib_batch_counters(void *batch, long long *steps, long long *launches);
 
-/* Times `steps` steps for each sweep block size (128, 256, 512 threads),
- * cells per sweep thread (1, 4) and lattice order in the sweep launch (as
- * given; largest lattice first) and keeps the fastest; the contexts advance
- * by about 12 * (7 + 2 * steps) steps.  choice (optional, 3 ints): threads,
- * order, cells per thread. */
+/* Times `steps` steps for each sweep configuration and keeps the fastest:
+ * the batched sweep with 128, 256 or 512 threads a block and 1 or 4 cells a
+ * thread, or one one-lattice sweep launch per lattice spread over side
+ * streams, each with the lattices as given or largest first; the contexts
+ * advance by about 14 * (7 + 2 * steps) steps.  choice (optional, 3 ints):
+ * threads (0: one launch per lattice), order, cells per thread. */
 int lbib_batch_autotune(void *batch, int steps, int *choice);
 
 /* Releases the batch (not its contexts). */

@@ -1311,6 +1311,15 @@ struct Batch {
     bool own_stream = false;
     cudaStream_t s_cap = nullptr;  // private capture stream: the batch stream is never in capture mode
     cudaEvent_t done = nullptr;
+    // sweep of each lattice as its own launch (the one-lattice kernel with its
+    // parameters in the constant bank), spread over side streams
+    int sweep_split = 0;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_ev;  // [0] fork, [1..] joins
+    std::vector<Lattice> lat_h;        // host copies of the launch tables
+    std::vector<LatRef> ref_h;
+    std::vector<int> order_h;
+    int nsm = 1;
     void *dmem = nullptr;
     BatchTables T{};
     BatchGrid G{};
@@ -1492,6 +1501,9 @@ int batch_build(Batch *b) {
     T.sweep_threads = b->sweep_threads;
     T.sweep_cpt = b->sweep_cpt;
     b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back()};
+    b->lat_h = lat;
+    b->ref_h = ref;
+    b->order_h = order;
     b->steps = 0;
     for (int i = 0; i < nl; ++i) b->base[i] = b->ctx[i]->steps;
     return LBIB_OK;
@@ -1499,15 +1511,32 @@ int batch_build(Batch *b) {
 
 int batch_enqueue(Batch *b, int phase, bool store, cudaStream_t st) {
     cudaError_t e = launch_batch_ib(b->prec, b->T, b->G, phase, st);
-    if (e == cudaSuccess) e = launch_batch_sweep(b->prec, b->T, b->G, phase, store ? 1 : 0, st);
+    if (e == cudaSuccess && !b->sweep_split) e = launch_batch_sweep(b->prec, b->T, b->G, phase, store ? 1 : 0, st);
+    if (e == cudaSuccess && b->sweep_split) {
+        // fork the side streams from st, one one-lattice sweep per lattice
+        // (largest first, round robin), join back into st
+        const int ns = (int)b->side.size(), nl = (int)b->lat_h.size();
+        e = cudaEventRecord(b->side_ev[0], st);
+        for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->side_ev[0], 0);
+        for (int q = 0; q < nl && e == cudaSuccess; ++q) {
+            const int i = b->order_h[q];
+            const LatRef &r = b->ref_h[(size_t)phase * nl + i];
+            e = launch_sweep(b->prec, r.fin, r.fout, r.force, r.stamp, r.d_step, b->lat_h[i], store ? r.fields : nullptr,
+                             0, nullptr, r.sr, r.parity, b->nsm, b->side[q % ns]);
+        }
+        for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(b->side_ev[1 + k], b->side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->side_ev[1 + k], 0);
+        }
+    }
     if (e != cudaSuccess) return bcuda(b, e, "batch launch");
     return LBIB_OK;
 }
 
 int batch_launches_per_step(const Batch *b) {
     int n = 0;
-    for (int v : {b->G.sweep, b->G.mom, b->G.mls, b->G.memb, b->G.rf, b->G.rm}) n += v > 0;
-    return n;
+    for (int v : {b->G.mom, b->G.mls, b->G.memb, b->G.rf, b->G.rm}) n += v > 0;
+    return n + (b->sweep_split ? (int)b->lat_h.size() : (b->G.sweep > 0));
 }
 
 int batch_capture6(Batch *b) {
@@ -1591,6 +1620,17 @@ int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out) {
         b->own_stream = e == cudaSuccess;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->s_cap, cudaStreamNonBlocking);
+    b->side.assign(8, nullptr);
+    b->side_ev.assign(9, nullptr);
+    for (auto &st : b->side)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (auto &ev : b->side_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) b->nsm = 1;
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     b->ctx_ev.assign(n, nullptr);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ctx_ev[i], cudaEventDisableTiming);
@@ -1682,12 +1722,17 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bcuda(b, cudaGetLastError(), "autotune events");
-    const int threads[] = {128, 256, 512}, cpts[] = {1, 4};
+    // candidates: the batched sweep in (threads, cells per thread) shapes, or
+    // one one-lattice sweep launch per lattice (threads = 0), each with the
+    // lattices as given or largest first
+    const int shapes[][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 4}, {256, 4}, {512, 4}, {0, 0}};
     float best = 1e30f;
-    int best_t = b->sweep_threads, best_o = b->order, best_c = b->sweep_cpt, rc = LBIB_OK;
+    int best_t = b->sweep_threads, best_o = b->order, best_c = b->sweep_cpt, best_split = b->sweep_split;
+    int rc = LBIB_OK;
     for (int o = 0; o < 2 && !rc; ++o)
-        for (int cp : cpts)
-            for (int t : threads) {
+        for (const auto &shape : shapes) {
+                const int t = shape[0] ? shape[0] : 256, cp = shape[0] ? shape[1] : 4;
+                b->sweep_split = shape[0] == 0;
                 b->sweep_threads = t;
                 b->order = o;
                 b->sweep_cpt = cp;
@@ -1709,6 +1754,7 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
                     best_t = t;
                     best_o = o;
                     best_c = cp;
+                    best_split = b->sweep_split;
                 }
             }
     cudaEventDestroy(e0);
@@ -1716,9 +1762,10 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
     b->sweep_threads = best_t;
     b->order = best_o;
     b->sweep_cpt = best_c;
+    b->sweep_split = best_split;
     int rc2 = batch_build(b);
     if (choice) {
-        choice[0] = best_t;
+        choice[0] = best_split ? 0 : best_t;
         choice[1] = best_o;
         choice[2] = best_c;
     }
@@ -1734,6 +1781,10 @@ void lbib_batch_destroy(void *h) {
         if (ev) cudaEventDestroy(ev);
     if (b->done) cudaEventDestroy(b->done);
     if (b->s_cap) cudaStreamDestroy(b->s_cap);
+    for (auto st : b->side)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : b->side_ev)
+        if (ev) cudaEventDestroy(ev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -152,7 +152,7 @@ def test_fp64_autotuned_batch_matches_oracle(lbib):
     ctxs = [lbib.Context.from_case(c) for c in cases]
     batch = lbib.Batch(ctxs)
     threads, order, cpt = batch.autotune(1)
-    assert threads in (128, 256, 512) and order in (0, 1) and cpt in (1, 4)
+    assert threads in (0, 128, 256, 512) and order in (0, 1) and cpt in (1, 4)
     batch.step(3)
     taken = ctxs[0].counters()[0]
     for ctx, case in zip(ctxs, cases):
