@@ -178,10 +178,10 @@ def run_gpu(args, rank, world):
     if args.autotune:
         tuned = lbib.lbib_autotune(h, 20)  # launch configuration (untimed; advances the run)
     else:
-        tuned = (0, 0, 1, 0)
+        tuned = (0, 0, 1, 0, 0)
     if args.overlap != "auto":
         lbib.lbib_set_overlap(h, 1 if args.overlap == "on" else 0)
-        tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0, tuned[3])
+        tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0, tuned[3], tuned[4])
     lbib.lbib_sync(h)
     lbib.lbib_set_output(h, -1)  # no macroscopic-field output inside the timed loop
     # L2 flush between timed steps: write a buffer larger than the 129 MB L2,
@@ -492,7 +492,7 @@ def main():
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
                    "fields_output": "off in the timed loop (e2e reads them)",
                    "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
-                                 "sweep_row_tiles": bool(r["tuned"][3])},
+                                 "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
                    "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(),

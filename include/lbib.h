@@ -178,16 +178,20 @@ int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
  * several shapes), then (single-body contexts) the overlap of the far-field
  * sweep with the IB stage.  Each trial runs
  * 1 + 2 * `steps` real time steps, so the simulation advances by about
- * 16 * `steps` steps.  choice (optional, 4 ints) receives block x, block y (0, 0: whole
- * x-rows), the overlap flag and the 4-wide flag. */
+ * 16 * `steps` steps.  choice (optional, 5 ints) receives block x, block y (0, 0: whole
+ * x-rows), the overlap flag, the row-tile flag and the far-field blocks per
+ * SM (0: full grid). */
 int lbib_autotune(void *ctx, int steps, int *choice);
 
 /* Sets the sweep launch configuration (what lbib_autotune chooses):
  * row_tiles = 1 selects the row-tile kernel (x-rows staged in shared memory
  * with 128-bit loads and stores; FP32/FP64 with nx a multiple of 4, else
  * ignored), 0 the one-node kernel with blocks of block_x * block_y threads
- * (0, 0: whole x-rows).  Results are the same in every configuration. */
-int lbib_set_sweep_config(void *ctx, int row_tiles, int block_x, int block_y);
+ * (0, 0: whole x-rows); far_per_sm > 0 runs the far-field sweep (overlap
+ * on) with that many resident blocks per SM striding over the lattice, so
+ * that the IB kernels beside it find free SMs, 0 on its full grid.  Results
+ * are the same in every configuration. */
+int lbib_set_sweep_config(void *ctx, int row_tiles, int block_x, int block_y, int far_per_sm);
 
 /* With a single body, the sweep of the nodes outside the body's support
  * box runs on a second stream concurrently with the IB stage (default 1);

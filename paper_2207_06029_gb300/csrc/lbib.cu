@@ -1235,16 +1235,26 @@ int lbib_autotune(void *h, int steps, int *choice) {
     c->L.sweep_by = shapes[best_shape][1];
     c->L.sweep_vec = shapes[best_shape][2];
     invalidate_graphs(c);
-    // overlap of the far-field sweep with the IB stage
-    int overlap = 0;
+    // overlap of the far-field sweep with the IB stage, the far-field sweep
+    // on its full grid or on a few resident blocks per SM
+    int overlap = 0, far = 0;
     if (!rc && c->bodies.size() == 1) {
-        float ms = 0.f;
         c->split_sweep = true;
-        invalidate_graphs(c);
-        if (!(rc = trial(&ms)) && ms < best) overlap = 1;
+        for (int fps : {0, 1, 2, 3}) {
+            float ms = 0.f;
+            c->L.far_per_sm = fps;
+            invalidate_graphs(c);
+            if ((rc = trial(&ms))) break;
+            if (ms < best) {
+                best = ms;
+                overlap = 1;
+                far = fps;
+            }
+        }
     } else {
         (void)saved_split;
     }
+    c->L.far_per_sm = far;
     c->split_sweep = overlap != 0;
     invalidate_graphs(c);
     cudaEventDestroy(e0);
@@ -1254,17 +1264,19 @@ int lbib_autotune(void *h, int steps, int *choice) {
         choice[1] = c->L.sweep_by;
         choice[2] = overlap;
         choice[3] = c->L.sweep_vec;
+        choice[4] = c->L.far_per_sm;
     }
     return rc;
 }
 
-int lbib_set_sweep_config(void *h, int row_tiles, int block_x, int block_y) {
+int lbib_set_sweep_config(void *h, int row_tiles, int block_x, int block_y, int far_per_sm) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;
     if (row_tiles < 0 || row_tiles > 1 || block_x < 0 || block_y < 0 || (block_x == 0) != (block_y == 0) ||
-        block_x * block_y > 1024)
+        block_x * block_y > 1024 || far_per_sm < 0 || far_per_sm > 64)
         return fail(c, LBIB_EINVAL, "bad sweep configuration");
     c->L.sweep_vec = row_tiles;
+    c->L.far_per_sm = far_per_sm;
     c->L.sweep_bx = block_x;
     c->L.sweep_by = block_y;
     invalidate_graphs(c);

@@ -133,6 +133,7 @@ struct Lattice {
     double dist2_cut;       // largest |X - x_k|^2 whose MLS weight is non-zero
     int sweep_bx, sweep_by; // block shape of the whole-lattice sweep (0: default)
     int sweep_vec;          // 1: row-tile sweep (shared-memory staging, 128-bit loads/stores) where it applies
+    int far_per_sm;         // > 0: the far-field sweep keeps this many blocks per SM (grid-stride)
     // derived, double and float copies
     double omega_d, cF_d, nu_d, gext_d[3], uw_d[27][3];
     float omega_f, cF_f, nu_f, gext_f[3], uw_f[27][3], dist2_cut_f;

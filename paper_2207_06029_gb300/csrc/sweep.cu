@@ -324,6 +324,31 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
     sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
 }
 
+// The far field (nodes outside the body box) with a bounded number of
+// resident blocks: each block strides over the (x-tile, y-tile, z) tiles of
+// the lattice, so that SM resources stay free for the IB kernels running
+// beside it (the block scheduler cannot take resources back from blocks
+// already resident).
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_sweep_far(const S *__restrict__ fin, S *__restrict__ fout,
+                                                   R *__restrict__ force, const uint32_t *__restrict__ stamp,
+                                                   const uint32_t *__restrict__ dstep, Lattice L,
+                                                   R *__restrict__ fields, const int *__restrict__ box,
+                                                   uint32_t *__restrict__ sr, int parity, int gx, int gy) {
+    const uint32_t step = stamp ? *dstep : 0u;
+    const uint32_t seed = sr[parity];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) sr[parity ^ 1] = seed + 1u;
+    int lo[3], ext[3];
+    clamp_box(L, box, lo, ext);
+    const int ntile = gx * gy * L.nz;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int tx = t % gx, ty = (t / gx) % gy, z = t / (gx * gy);
+        const int x = tx * blockDim.x + threadIdx.x, y = ty * blockDim.y + threadIdx.y;
+        if (x >= L.nx || y >= L.ny || in_box(L, lo, ext, x, y, z)) continue;
+        sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
+    }
+}
+
 // Row-tile sweep with shared-memory staging: a block takes `rows`
 // consecutive x-rows of one z-plane.  It first copies, for every direction
 // i, the source rows (y - e_iy, z - e_iz) into shared memory with 128-bit
@@ -564,6 +589,12 @@ static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint3
         k_sweep_tile<S, R><<<grid, rows * L.nx, smem, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
                                                            (R *)fields, part == 1 ? box : nullptr, sr, parity,
                                                            rows);
+    } else if (part == 1 && L.far_per_sm > 0) {
+        dim3 grid, block;
+        sweep_shape(L, grid, block);
+        k_sweep_far<S, R><<<L.far_per_sm * nsm, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step,
+                                                               L, (R *)fields, box, sr, parity, (int)grid.x,
+                                                               (int)grid.y);
     } else {
         dim3 grid, block;
         sweep_shape(L, grid, block);

@@ -116,7 +116,7 @@ def load():
         L.lbib_set_output.argtypes = [vp, C.c_int]
         L.lbib_set_overlap.argtypes = [vp, C.c_int]
         L.lbib_set_graphs.argtypes = [vp, C.c_int]
-        L.lbib_set_sweep_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.lbib_set_sweep_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_mesh_measures_noalloc.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
@@ -256,18 +256,20 @@ def lbib_get_profile(ctx):
 
 
 def lbib_autotune(ctx, steps):
-    """Returns (block_x, block_y, overlap, vec4) chosen; advances the run by several times `steps`."""
-    ch = (C.c_int * 4)()
+    """Returns (block_x, block_y, overlap, row_tiles, far_per_sm) chosen; advances the run by several
+    times `steps`."""
+    ch = (C.c_int * 5)()
     _check(ctx, load().lbib_autotune(ctx, int(steps), ch))
-    return ch[0], ch[1], ch[2], ch[3]
+    return tuple(ch)
 
 
 def lbib_set_overlap(ctx, enable):
     return _check(ctx, load().lbib_set_overlap(ctx, int(enable)))
 
 
-def lbib_set_sweep_config(ctx, row_tiles, block_x=0, block_y=0):
-    return _check(ctx, load().lbib_set_sweep_config(ctx, int(row_tiles), int(block_x), int(block_y)))
+def lbib_set_sweep_config(ctx, row_tiles, block_x=0, block_y=0, far_per_sm=0):
+    return _check(ctx, load().lbib_set_sweep_config(ctx, int(row_tiles), int(block_x), int(block_y),
+                                                    int(far_per_sm)))
 
 
 def lbib_set_graphs(ctx, enable):

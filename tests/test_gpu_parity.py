@@ -260,7 +260,7 @@ def test_graph_steps_match_enqueued_steps(lbib, overlap):
     assert rel(out[0][0], o["f"]) < 1e-12
 
 
-@pytest.mark.parametrize("config", [(1, 0, 0), (0, 32, 4), (0, 128, 2)])
+@pytest.mark.parametrize("config", [(1, 0, 0, 0), (0, 32, 4, 0), (0, 128, 2, 0), (0, 0, 0, 1), (0, 32, 4, 2)])
 @pytest.mark.parametrize("overlap", [1, 0])
 def test_sweep_kernels_and_shapes_match_oracle(lbib, config, overlap):
     """The row-tile sweep (x-rows staged in shared memory, 128-bit loads
@@ -282,7 +282,7 @@ def test_fp32_row_tile_sweep_full_size(lbib):
     """The row-tile kernel on the 96^3 FP32 capsule case against the oracle."""
     case = W.case_capsule_shear(Ca=0.05, Eb=0.01, kv=1.0)
     ctx = lbib.Context.from_case(case)
-    lbib.lbib_set_sweep_config(ctx.h, 1, 0, 0)
+    lbib.lbib_set_sweep_config(ctx.h, 1, 0, 0, 2)
     ctx.step(30)
     g = {"fields": ctx.fields(), "markers": [ctx.markers(0)]}
     ctx.close()
