@@ -212,6 +212,20 @@ int lbib_set_graphs(void *ctx, int enable);
  * returns the fields of the last step that wrote them). */
 int lbib_set_output(void *ctx, int fields_every);
 
+/* Checkpoint: the context's device state (populations, IB force and its
+ * tile flags, fields, bodies' positions, velocities, forces, transfer
+ * weights and rigid states, counters) and its step counters, into a host
+ * buffer.  buf == NULL: *size receives the bytes needed.  Otherwise *size is
+ * the buffer's capacity on entry and the bytes written on return.
+ * Synchronises. */
+int lbib_save(void *ctx, void *buf, size_t *size);
+
+/* Restores a checkpoint into a context set up the same way (same lattice,
+ * precision and bodies added in the same order); the run continues exactly
+ * where the saved one stood.  Clears a sticky error.  LBIB_EINVAL for a
+ * buffer from a differently set-up context (nothing is changed then). */
+int lbib_load(void *ctx, const void *buf, size_t size);
+
 /* Bytes of device memory held by the context. */
 int lbib_device_bytes(void *ctx, size_t *bytes);
 

@@ -83,6 +83,7 @@ struct Ctx {
     std::string msg;
     size_t bytes = 0;
     std::vector<std::pair<void *, size_t>> allocs;
+    std::vector<void *> transient;  // allocations a checkpoint leaves out (scratch, support moments)
     bool profile = false;
     std::vector<cudaEvent_t> events;  // per step: begin, after MLS, after structure, after sweep
     size_t nev = 0;
@@ -323,6 +324,7 @@ int sync_ctx(Ctx *c) {
 double *get_scratch(Ctx *c, size_t bytes) {
     if (c->scratch_bytes >= bytes) return c->scratch;
     c->scratch = (double *)dev_alloc(c, bytes);
+    if (c->scratch) c->transient.push_back(c->scratch);
     c->scratch_bytes = c->scratch ? bytes : 0;
     return c->scratch;
 }
@@ -458,6 +460,7 @@ int lbib_create(const lbib_params *p, void **out) {
     c->force = dev_alloc(c, 3 * (size_t)L.stride * c->relem);
     c->fields = dev_alloc(c, 4 * (size_t)L.stride * c->relem);
     c->mom = dev_alloc(c, 4 * (size_t)L.stride * c->relem);
+    c->transient.push_back(c->mom);
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1799,6 +1802,154 @@ void lbib_batch_destroy(void *h) {
         if (ev) cudaEventDestroy(ev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the device state of a context (every allocation except the
+// scratch and the support moments) and its step counters, restored into a
+// context set up the same way (same parameters, same bodies in the same
+// order, hence the same allocations).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkpHeader {
+    char magic[8];
+    int32_t version, prec, nx, ny, nz, nbodies, fa_index, nsaved;
+    uint32_t step_host;
+    int64_t steps, launches;
+};
+
+bool persistent(const Ctx *c, size_t k) {
+    return std::find(c->transient.begin(), c->transient.end(), c->allocs[k].first) == c->transient.end();
+}
+
+size_t checkpoint_size(const Ctx *c) {
+    size_t n = sizeof(CkpHeader) + c->bodies.size() * 4 * sizeof(int32_t);
+    for (size_t k = 0; k < c->allocs.size(); ++k)
+        if (persistent(c, k)) n += sizeof(uint64_t) + c->allocs[k].second;
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbib_save(void *h, void *buf, size_t *size) {
+    Ctx *c = as_ctx(h);
+    if (!c || !size) return LBIB_EINVAL;
+    const size_t need = checkpoint_size(c);
+    if (!buf) {
+        *size = need;
+        return LBIB_OK;
+    }
+    if (*size < need) return fail(c, LBIB_EINVAL, "checkpoint buffer too small (%zu < %zu bytes)", *size, need);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_hi);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_lo);
+    if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint sync");
+    unsigned char *out = static_cast<unsigned char *>(buf);
+    CkpHeader hd{};
+    std::memcpy(hd.magic, "LBIBCKP1", 8);
+    hd.version = 1;
+    hd.prec = c->prec;
+    hd.nx = c->L.nx;
+    hd.ny = c->L.ny;
+    hd.nz = c->L.nz;
+    hd.nbodies = (int32_t)c->bodies.size();
+    hd.fa_index = -1;
+    hd.nsaved = 0;
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (c->allocs[k].first == c->fA) hd.fa_index = (int32_t)k;
+        if (persistent(c, k)) ++hd.nsaved;
+    }
+    hd.step_host = c->step_host;
+    hd.steps = c->steps;
+    hd.launches = c->launches;
+    std::memcpy(out, &hd, sizeof(hd));
+    size_t off = sizeof(hd);
+    for (const DevBody &b : c->bodies) {
+        const int32_t v[4] = {b.cur, b.bcur, b.nv, b.nt};
+        std::memcpy(out + off, v, sizeof(v));
+        off += sizeof(v);
+    }
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (!persistent(c, k)) continue;
+        const uint64_t n = c->allocs[k].second;
+        std::memcpy(out + off, &n, sizeof(n));
+        off += sizeof(n);
+        e = cudaMemcpy(out + off, c->allocs[k].first, n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+        off += n;
+    }
+    *size = off;
+    return LBIB_OK;
+}
+
+int lbib_load(void *h, const void *buf, size_t size) {
+    Ctx *c = as_ctx(h);
+    if (!c || !buf) return LBIB_EINVAL;
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    CkpHeader hd{};
+    if (size < sizeof(hd)) return fail(c, LBIB_EINVAL, "checkpoint too short");
+    std::memcpy(&hd, in, sizeof(hd));
+    if (std::memcmp(hd.magic, "LBIBCKP1", 8) != 0 || hd.version != 1)
+        return fail(c, LBIB_EINVAL, "not a checkpoint of this library");
+    if (hd.prec != c->prec || hd.nx != c->L.nx || hd.ny != c->L.ny || hd.nz != c->L.nz ||
+        hd.nbodies != (int32_t)c->bodies.size())
+        return fail(c, LBIB_EINVAL, "checkpoint of a differently set-up context (lattice, precision or bodies)");
+    size_t off = sizeof(hd);
+    std::vector<int32_t> bs(4 * c->bodies.size());
+    if (size < off + bs.size() * sizeof(int32_t)) return fail(c, LBIB_EINVAL, "checkpoint too short");
+    std::memcpy(bs.data(), in + off, bs.size() * sizeof(int32_t));
+    off += bs.size() * sizeof(int32_t);
+    for (size_t j = 0; j < c->bodies.size(); ++j)
+        if (bs[4 * j + 2] != c->bodies[j].nv || bs[4 * j + 3] != c->bodies[j].nt ||
+            bs[4 * j] < 0 || bs[4 * j] > 2 || bs[4 * j + 1] < 0 || bs[4 * j + 1] > 1)
+            return fail(c, LBIB_EINVAL, "checkpoint bodies differ from the context's");
+    int32_t nsaved = 0;
+    for (size_t k = 0; k < c->allocs.size(); ++k) nsaved += persistent(c, k);
+    if (nsaved != hd.nsaved || hd.fa_index < 0 || hd.fa_index >= (int32_t)c->allocs.size())
+        return fail(c, LBIB_EINVAL, "checkpoint buffers differ from the context's");
+    // check every size before copying anything
+    size_t o = off;
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (!persistent(c, k)) continue;
+        uint64_t n = 0;
+        if (size < o + sizeof(n)) return fail(c, LBIB_EINVAL, "checkpoint too short");
+        std::memcpy(&n, in + o, sizeof(n));
+        if (n != c->allocs[k].second || size < o + sizeof(n) + n)
+            return fail(c, LBIB_EINVAL, "checkpoint buffers differ from the context's");
+        o += sizeof(n) + n;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_hi);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_lo);
+    if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint sync");
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (!persistent(c, k)) continue;
+        uint64_t n = 0;
+        std::memcpy(&n, in + off, sizeof(n));
+        off += sizeof(n);
+        e = cudaMemcpy(c->allocs[k].first, in + off, n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint restore");
+        off += n;
+    }
+    invalidate_graphs(c);
+    void *fa = c->allocs[hd.fa_index].first;
+    if (fa != c->fA) std::swap(c->fA, c->fB);
+    for (size_t j = 0; j < c->bodies.size(); ++j) {
+        c->bodies[j].cur = bs[4 * j];
+        c->bodies[j].bcur = bs[4 * j + 1];
+    }
+    c->steps = hd.steps;
+    c->step_host = hd.step_host;
+    c->launches = hd.launches;
+    *c->h_err = 0;
+    c->err = 0;
+    c->msg.clear();
+    return check_device_error(c) == LBIB_OK ? LBIB_OK : c->err;
 }
 
 }  // extern "C"

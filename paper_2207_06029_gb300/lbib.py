@@ -79,7 +79,7 @@ _lib = None
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
-           "lbib_device_bytes", "lbib_mesh_measures_noalloc",
+           "lbib_device_bytes", "lbib_save", "lbib_load", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
            "lbib_batch_destroy", "lbib_batch_last_error",
            "lbib_request_create", "lbib_request_add_body", "lbib_request_destroy", "lbib_serve_create",
@@ -119,6 +119,8 @@ def load():
         L.lbib_set_sweep_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.lbib_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.lbib_load.argtypes = [vp, vp, C.c_size_t]
         L.lbib_mesh_measures_noalloc.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
         L.lbib_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp, C.POINTER(C.c_void_p)]
         L.lbib_batch_step.argtypes = [vp, C.c_int]
@@ -265,6 +267,20 @@ def lbib_autotune(ctx, steps):
 
 def lbib_set_overlap(ctx, enable):
     return _check(ctx, load().lbib_set_overlap(ctx, int(enable)))
+
+
+def lbib_save(ctx):
+    """Checkpoint of the context as bytes."""
+    n = C.c_size_t(0)
+    _check(ctx, load().lbib_save(ctx, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, load().lbib_save(ctx, buf, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def lbib_load(ctx, data):
+    buf = C.create_string_buffer(bytes(data), len(data))
+    return _check(ctx, load().lbib_load(ctx, buf, len(data)))
 
 
 def lbib_set_sweep_config(ctx, row_tiles, block_x=0, block_y=0, far_per_sm=0):

@@ -334,6 +334,53 @@ def test_fp64_totals_conservation_and_forcing(lbib, prec, tol, paper_e):
     assert np.abs(p - (o @ paper_e).sum(axis=0)).max() <= tol * nc * 1e-2
 
 
+def test_checkpoint_resume_continues_the_run(lbib):
+    """Save after 9 steps, run 7 more; a freshly set-up context loaded from
+    the checkpoint runs the same 7 steps to the same state (FP64; only the
+    order of the atomic spreading sums may differ).  A checkpoint of a
+    different set-up is refused; loading clears a sticky error."""
+    case = W.case_capsule_shear(n=28, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
+                                precision=W.PREC_FP64)
+    a = lbib.Context.from_case(case)
+    a.step(9)
+    ck = lbib.lbib_save(a.h)
+    a.step(7)
+    fa, Xa = a.populations(), a.markers(0)[0]
+    b = lbib.Context.from_case(case)
+    lbib.lbib_load(b.h, ck)
+    assert b.counters()[0] == 9
+    b.step(7)
+    assert rel(b.populations(), fa) < 1e-13 and rel(b.markers(0)[0], Xa) < 1e-13
+    other = lbib.Context((28, 28, 30), 0.8, bc=(0, 0, 1), precision=lbib.LBIB_FP64)
+    with pytest.raises(lbib.LbibError) as ei:
+        lbib.lbib_load(other.h, ck)
+    assert ei.value.code == lbib.LBIB_EINVAL
+    other.close()
+    # a sticky error (support reaching a wall) is cleared by loading the
+    # checkpoint of a context set up the same way with the sphere clear of
+    # the walls
+    n = 16
+    ctxs = []
+    for zc in (8.0, 3.2):
+        v, f = W.icosphere(1, 2.0, (8.0, 8.0, zc))
+        ctx = lbib.Context((n, n, n), 0.8, bc=(0, 0, 1), precision=lbib.LBIB_FP64)
+        ctx.add_body(v, f, rigid=True, ref_radius=2.0)
+        ctxs.append(ctx)
+    good = lbib.lbib_save(ctxs[0].h)
+    c = ctxs[1]
+    with pytest.raises(lbib.LbibError) as ei:
+        c.step(1)
+        c.sync()
+    assert ei.value.code == lbib.LBIB_EBODY_WALL
+    lbib.lbib_load(c.h, good)
+    c.step(2)
+    c.sync()
+    assert abs(c.markers(0)[0][:, 2].mean() - 8.0) < 1e-6
+    ctxs[0].close()
+    for ctx in (a, b, c):
+        ctx.close()
+
+
 def test_zero_steps_and_empty_lattice(lbib):
     case = W.case_empty(n=(5, 4, 3), precision=W.PREC_FP64, seed=7)
     ctx = lbib.Context.from_case(case)
