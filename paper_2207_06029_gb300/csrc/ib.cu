@@ -118,6 +118,7 @@ struct MlsSmem {
     // per point: A = sum W p p^T, b_f = sum W p f for f = rho - 1, u_x, u_y, u_z
     R sums[kPts][kSums];
     R row0[kPts][4];  // first row of A^-1
+    int pid[kPts];    // point of each slot (-1 past the end): slots follow the body's cell order
     // per warp: transpose buffer of the 26 products of each node
     R red[kMlsThreads / 32][kSums][33];
 };
@@ -213,9 +214,11 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
 
     // ---------------- phase 0: one lane per point ----------------
     if (warp == w0) {
-        const int p = p0 + lane;
+        const int slot = p0 + lane;
+        const int p = slot < npts ? (B.perm ? B.perm[slot] : slot) : -1;
+        sm.pid[lane] = p;
         sm.vol[lane] = 0.0;
-        if (p < npts) {
+        if (p >= 0) {
             double P[3];
             if (p < B.nv) {
                 P[0] = B.X[3 * p];
@@ -280,9 +283,9 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
 #pragma unroll
     for (int j = 0; j < kPerWarp; ++j) {
         const int lp = warp * kPerWarp + j;
-        const int p = p0 + lp;
+        const int p = sm.pid[lp];
         gu[j][0] = gu[j][1] = gu[j][2] = gu[j][3] = R(0);
-        if (p < npts && lane < 27) {
+        if (p >= 0 && lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
             int cw[3];
             for (int a = 0; a < 3; ++a) {
@@ -309,8 +312,8 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
 #pragma unroll
     for (int j = 0; j < kPerWarp; ++j) {
         const int lp = warp * kPerWarp + j;
-        const int p = p0 + lp;
-        if (p >= npts) break;
+        const int p = sm.pid[lp];
+        if (p < 0) break;
         R W = R(0), dk[3] = {R(0), R(0), R(0)};
         if (lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
@@ -372,8 +375,8 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     __syncthreads();
 
     // ---------------- phase 2: one lane per point ----------------
-    if (warp == w2 && p0 + lane < npts) {
-        const int p = p0 + lane;
+    if (warp == w2 && sm.pid[lane] >= 0) {
+        const int p = sm.pid[lane];
         const R *S = sm.sums[lane];
         double a[10], inv[16];
         for (int q = 0; q < 10; ++q) a[q] = (double)S[q];
@@ -442,8 +445,9 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     // ---------------- phase 3: transfer weights of the markers ----------------
     for (int j = 0; j < kPerWarp; ++j) {
         const int lp = warp * kPerWarp + j;
-        const int p = p0 + lp;
-        if (p >= B.nv || p >= npts) break;
+        const int p = sm.pid[lp];
+        if (p < 0) break;
+        if (p >= B.nv) continue;  // probes keep no transfer weights
         if (lane < 27) {
             const R *r0 = sm.row0[lp];
             const R phi = sm.W[lp][lane] *

@@ -30,6 +30,7 @@ struct DevBody {
     double *U = nullptr, *Ub = nullptr, *Fl = nullptr, *tri_vol = nullptr;
     void *phi = nullptr, *tri_geo = nullptr, *probe = nullptr;  // arithmetic precision R
     void *Xrel[2] = {nullptr, nullptr};                          // R: X - origin, current and next
+    int *perm = nullptr;  // MLS points (markers, probes) in cell order
     int *node = nullptr, *tri = nullptr, *vh_ptr = nullptr, *vh_list = nullptr, *vt_ptr = nullptr,
         *vt_list = nullptr;
     int4 *hinge = nullptr;
@@ -65,6 +66,7 @@ struct Ctx {
     bool split_sweep = true;
     bool own_stream = false;
     std::vector<DevBody> bodies;
+    bool sort_points = true;     // MLS points in cell order (marker binning)
     uint32_t *d_step = nullptr;  // device step counter (tile flags of the IB force)
     uint32_t step_host = 0;      // host mirror of *d_step
     uint32_t *d_sr = nullptr;    // two-word seed counter of the stochastic rounding (bfloat16 storage)
@@ -263,6 +265,7 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.Fl = b.Fl;
     v.phi = b.phi;
     v.node = b.node;
+    v.perm = c->sort_points ? b.perm : nullptr;
     v.tri = b.tri;
     v.tri_geo = b.tri_geo;
     v.tri_vol = b.tri_vol;
@@ -689,6 +692,45 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     b.phi = dev_alloc(c, c->relem * 27 * (size_t)nv);
     b.node = (int *)dev_alloc(c, sizeof(int) * 27 * (size_t)nv);
     b.tri = upload(c, T, &rc);
+    // marker binning: the MLS points (vertices; probes at their triangle's
+    // centroid) ordered by the Morton code of their nearest node
+    // floor(X + 1/2), so that a block's points share support nodes
+    {
+        auto morton = [](int x, int y, int z) {
+            uint64_t code = 0;
+            for (int bit = 0; bit < 10; ++bit)
+                code |= (uint64_t)((x >> bit) & 1) << (3 * bit) | (uint64_t)((y >> bit) & 1) << (3 * bit + 1) |
+                        (uint64_t)((z >> bit) & 1) << (3 * bit + 2);
+            return code;
+        };
+        auto cell = [&](const double *P) {
+            int q[3];
+            for (int a = 0; a < 3; ++a) {
+                long long k = (long long)std::floor(P[a] + 0.5);
+                q[a] = (int)(k < 0 ? 0 : k & 1023);
+            }
+            return morton(q[0], q[1], q[2]);
+        };
+        const int npts = nv + 2 * nt;
+        std::vector<std::pair<uint64_t, int>> keyed(npts);
+        for (int v = 0; v < nv; ++v) keyed[v] = {cell(&verts[3 * v]), v};
+        for (int t = 0; t < nt; ++t) {
+            double cen[3];
+            for (int a = 0; a < 3; ++a)
+                cen[a] = (verts[3 * tris[3 * t] + a] + verts[3 * tris[3 * t + 1] + a] + verts[3 * tris[3 * t + 2] + a]) /
+                         3.0;
+            const uint64_t k = cell(cen);
+            keyed[nv + 2 * t] = {k, nv + 2 * t};
+            keyed[nv + 2 * t + 1] = {k, nv + 2 * t + 1};
+        }
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const std::pair<uint64_t, int> &a, const std::pair<uint64_t, int> &b) {
+                             return a.first < b.first;
+                         });
+        std::vector<int> perm(npts);
+        for (int k = 0; k < npts; ++k) perm[k] = keyed[k].second;
+        b.perm = upload(c, perm, &rc);
+    }
     b.tri_geo = dev_alloc(c, c->relem * 8 * (size_t)nt);
     b.tri_vol = (double *)dev_alloc(c, sizeof(double) * (size_t)nt);
     b.probe = dev_alloc(c, c->relem * 8 * (size_t)nt);

@@ -162,6 +162,7 @@ struct BodyView {
     double *Fl;             // [3nv] Lagrangian IB force
     void *phi;              // [27nv] R: MLS transfer weights of level n
     int *node;              // [27nv] support node indices
+    const int *perm;        // [nv + 2nt] MLS points in cell order (markers, probes), or nullptr
     const int *tri;         // [3nt]
     void *tri_geo;          // [8nt] R: unit normal (3), area, centroid - origin (3), unused
     double *tri_vol;        // [nt] volume terms (x_0 - o) . (e1 x e2)
