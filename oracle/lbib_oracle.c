@@ -21,8 +21,11 @@
  * conservation laws, brute-force streaming, exact discrete steady states
  * (Couette, Poiseuille interior), closed forms (MLS on a node, pressure jump
  * of a linear density, platonic dihedral angles, cube inertia, Stokes
- * rotation of a free sphere in shear) and finite differences of the
- * membrane energies.
+ * rotation of a free sphere in shear), finite differences of the
+ * membrane energies, and, for the IB markers (vertices or, as printed,
+ * triangle centroids), the exact first-step displacement of kinematic
+ * markers in the discrete Couette state and the momentum total of the
+ * spread force.
  */
 #include <math.h>
 #include <stdint.h>
@@ -577,6 +580,7 @@ typedef struct {
     int bend_variant;
     int kinematic; /* membrane: markers advected with the fluid (kinematic IB) */
     int rigid_force; /* rigid: 0 probe stress jump (as printed), 1 momentum exchange */
+    int centroid_markers; /* 1: the IB markers are the triangle centroids (as printed in Sec. 2.3) */
 } orc_body_params;
 
 typedef struct {
@@ -589,6 +593,7 @@ typedef struct {
     double *ks, *l0, *kb, *theta0;
     double V0, A0, mv;
     double *Ub, *U, *Fl;   /* last step: boundary velocity, interpolated velocity, IB force */
+    double *Uc, *Flc;      /* centroid markers [nt*3]: interpolated velocity, IB force */
     /* rigid state */
     double xc[3], q[4], u[3], up[3], w[3], wp[3], m, Vb, Ib[9];
 } orc_body;
@@ -689,6 +694,8 @@ static void body_free(orc_body *b) {
     free(b->Ub);
     free(b->U);
     free(b->Fl);
+    free(b->Uc);
+    free(b->Flc);
 }
 
 void orc_sim_destroy(orc_sim *s) {
@@ -773,6 +780,10 @@ int orc_sim_add_body(orc_sim *s, const double *verts, int nv, const int *tris, i
     b.Ub = (double *)calloc(3 * (size_t)nv, sizeof(double));
     b.U = (double *)calloc(3 * (size_t)nv, sizeof(double));
     b.Fl = (double *)calloc(3 * (size_t)nv, sizeof(double));
+    if (p->centroid_markers) {
+        b.Uc = (double *)calloc(3 * (size_t)nt, sizeof(double));
+        b.Flc = (double *)calloc(3 * (size_t)nt, sizeof(double));
+    }
     if (b.rigid) {
         double V, c[3], I[9];
         orc_mass_properties(verts, nt, tris, &V, c, I);
@@ -870,36 +881,58 @@ static int hydro_force(const orc_sim *s, const double *X, const int *t, double *
  * uses the fluid state of level n; the IB force is added to s->fib. */
 static int body_step(orc_sim *s, orc_body *b) {
     int nv = b->nv, nt = b->nt;
-    double *phi = (double *)malloc(sizeof(double) * 27 * nv);
-    long *node = (long *)malloc(sizeof(long) * 27 * nv);
+    /* the IB markers: the vertices, or (centroid_markers) the triangle
+     * centroids, each carrying its share of the surface */
+    const int cm = b->p.centroid_markers;
+    const int nm = cm ? nt : nv;
+    double *phi = (double *)malloc(sizeof(double) * 27 * nm);
+    long *node = (long *)malloc(sizeof(long) * 27 * nm);
     double *Ftot = (double *)calloc(3 * (size_t)nv, sizeof(double));
     double *Xnew = (double *)malloc(sizeof(double) * 3 * nv);
     double *Av = (double *)calloc((size_t)nv, sizeof(double));
+    double *At = (double *)malloc(sizeof(double) * nt);
     double *Ftri = (double *)malloc(sizeof(double) * 3 * nt);
     double *cen = (double *)malloc(sizeof(double) * 3 * nt);
+    double *Ubc = cm ? (double *)malloc(sizeof(double) * 3 * nt) : NULL;
     int rc = ORC_OK;
 
     /* (1) MLS interpolation of the fluid velocity at each marker, Eq. (uLag). */
-    for (int l = 0; l < nv && !rc; ++l) {
-        double psi[27 * 4];
-        rc = mls_support(s, &b->X[3 * l], psi, &node[27 * l]);
+    for (int l = 0; l < nm && !rc; ++l) {
+        double psi[27 * 4], Xl[3];
+        for (int a = 0; a < 3; ++a)
+            Xl[a] = cm ? (b->X[3 * b->tri[3 * l] + a] + b->X[3 * b->tri[3 * l + 1] + a] +
+                          b->X[3 * b->tri[3 * l + 2] + a]) / 3.0
+                       : b->X[3 * l + a];
+        rc = mls_support(s, Xl, psi, &node[27 * l]);
         if (rc) break;
         double U[3] = {0, 0, 0};
         for (int k = 0; k < 27; ++k) {
             phi[27 * l + k] = psi[4 * k];
             for (int a = 0; a < 3; ++a) U[a] += psi[4 * k] * s->us[3 * node[27 * l + k] + a];
         }
-        for (int a = 0; a < 3; ++a) b->U[3 * l + a] = U[a];
+        for (int a = 0; a < 3; ++a) (cm ? b->Uc : b->U)[3 * l + a] = U[a];
     }
     /* (2) geometry at level n: vertex areas 1/3 sum of incident areas, and
      * the hydrodynamic force of each element (Eqs. hydroForP, hydroForNu). */
     for (int t = 0; t < nt && !rc; ++t) {
         double n[3], A, c[3];
         tri_geom(b->X, &b->tri[3 * t], n, &A, c);
+        At[t] = A;
         for (int q = 0; q < 3; ++q) Av[b->tri[3 * t + q]] += A / 3.0;
         rc = hydro_force(s, b->X, &b->tri[3 * t], &Ftri[3 * t], &cen[3 * t]);
     }
     if (rc) goto done;
+    if (cm) {
+        /* reading (centroid markers): a vertex moves with the mean of its
+         * triangles' centroid velocities, each weighted by the third of the
+         * triangle's area the vertex carries */
+        for (int l = 0; l < 3 * nv; ++l) b->U[l] = 0.0;
+        for (int t = 0; t < nt; ++t)
+            for (int q = 0; q < 3; ++q)
+                for (int a = 0; a < 3; ++a) b->U[3 * b->tri[3 * t + q] + a] += At[t] / 3.0 * b->Uc[3 * t + a];
+        for (int l = 0; l < nv; ++l)
+            for (int a = 0; a < 3; ++a) b->U[3 * l + a] /= Av[l];
+    }
 
     double *Ub = b->Ub;
     if (!b->rigid) {
@@ -959,10 +992,10 @@ static int body_step(orc_sim *s, orc_body *b) {
              * body moving with it, rho_f V du/dt and I_f dw/dt (backward
              * differences, I_f the body's world-frame inertia scaled by
              * rho_f / rho_s) */
-            for (int l = 0; l < nv; ++l) {
+            for (int l = 0; l < nm; ++l) {
                 double r[3], f[3], rxf[3];
-                sub3(&b->X[3 * l], b->xc, r);
-                for (int a = 0; a < 3; ++a) f[a] = -Av[l] * b->Fl[3 * l + a];
+                sub3(cm ? &cen[3 * l] : &b->X[3 * l], b->xc, r);
+                for (int a = 0; a < 3; ++a) f[a] = cm ? -At[l] * b->Flc[3 * l + a] : -Av[l] * b->Fl[3 * l + a];
                 cross3(r, f, rxf);
                 for (int a = 0; a < 3; ++a) {
                     F[a] += f[a];
@@ -1015,6 +1048,13 @@ static int body_step(orc_sim *s, orc_body *b) {
             cross3(wn, r, wxr);
             for (int a = 0; a < 3; ++a) Ub[3 * l + a] = un[a] + wxr[a];
         }
+        if (cm)
+            for (int t = 0; t < nt; ++t) {
+                double r[3], wxr[3];
+                sub3(&cen[3 * t], b->xc, r);
+                cross3(wn, r, wxr);
+                for (int a = 0; a < 3; ++a) Ubc[3 * t + a] = un[a] + wxr[a];
+            }
         /* advance centre and orientation (reading: x_c += u dt; exact
          * rotation by |w| dt about w), then the markers */
         for (int a = 0; a < 3; ++a) {
@@ -1044,15 +1084,28 @@ static int body_step(orc_sim *s, orc_body *b) {
      * with the shape functions of level n.  reading: c_l = A_l, the marker's
      * share of the surface (volume A_l dx over a cell dx^3), which makes the
      * Eulerian total equal sum_l c_l F_l since sum_k phi_k = 1. */
-    for (int l = 0; l < nv; ++l) {
+    for (int l = 0; l < nv; ++l)
+        for (int a = 0; a < 3; ++a) b->Fl[3 * l + a] = Ub[3 * l + a] - b->U[3 * l + a];
+    if (cm && !b->rigid)
+        /* centroid markers of a membrane: the boundary velocity at a
+         * centroid is its interpolated velocity advanced by the mean
+         * Newton acceleration of the triangle's vertices */
+        for (int t = 0; t < nt; ++t)
+            for (int a = 0; a < 3; ++a) {
+                double acc = 0.0;
+                for (int q = 0; q < 3; ++q) acc += b->Fl[3 * b->tri[3 * t + q] + a];
+                Ubc[3 * t + a] = b->Uc[3 * t + a] + acc / 3.0;
+            }
+    for (int l = 0; l < nm; ++l) {
         double Fl[3];
         for (int a = 0; a < 3; ++a) {
-            Fl[a] = Ub[3 * l + a] - b->U[3 * l + a];
-            b->Fl[3 * l + a] = Fl[a];
+            Fl[a] = cm ? Ubc[3 * l + a] - b->Uc[3 * l + a] : b->Fl[3 * l + a];
+            if (cm) b->Flc[3 * l + a] = Fl[a];
         }
+        const double cl = cm ? At[l] : Av[l];
         for (int k = 0; k < 27; ++k) {
             long c = node[27 * l + k];
-            for (int a = 0; a < 3; ++a) s->fib[3 * c + a] += Av[l] * phi[27 * l + k] * Fl[a];
+            for (int a = 0; a < 3; ++a) s->fib[3 * c + a] += cl * phi[27 * l + k] * Fl[a];
         }
     }
     /* (6) shift the marker history: x(t - dt) <- x(t), x(t) <- x(t + dt) */
@@ -1066,8 +1119,10 @@ done:
     free(node);
     free(Ftot);
     free(Av);
+    free(At);
     free(Ftri);
     free(cen);
+    free(Ubc);
     return rc;
 }
 

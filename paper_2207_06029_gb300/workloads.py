@@ -150,12 +150,13 @@ class Body:
     bend_variant: int = 0
     kinematic: int = 0
     rigid_force: int = 0
+    centroid_markers: int = 0
 
     def kwargs(self):
         return dict(rigid=self.rigid, ks0=self.ks0, Eb=self.Eb, kv=self.kv, thickness=self.thickness,
                     density_ratio=self.density_ratio, ref_radius=self.ref_radius, gravity=self.gravity,
                     u0=self.u0, omega0=self.omega0, bend_variant=self.bend_variant, kinematic=self.kinematic,
-                    rigid_force=self.rigid_force)
+                    rigid_force=self.rigid_force, centroid_markers=self.centroid_markers)
 
 
 @dataclasses.dataclass

@@ -188,3 +188,133 @@ def test_momentum_exchange_sphere_spins_at_half_shear_rate():
     assert abs(st["omega"][1] / (gamma / 2) - 1.0) < 0.02
     assert np.abs(st["xc"] - 15.5).max() < 1e-10
     s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# centroid markers (the markers at the triangle centroids, as printed in Sec. 2.3)
+# ---------------------------------------------------------------------------------------
+
+def test_centroid_markers_rigid_galilean_invariance():
+    """Centroid markers: a rigid sphere moving with a uniform periodic flow.
+    MLS reproduces the uniform field at every centroid, the vertices'
+    velocities (area-weighted means of their triangles') equal the flow's,
+    and the body feels no force."""
+    n, U0 = 20, np.array([0.02, -0.01, 0.015])
+    v, f = W.icosphere(2, 3.0, (9.7, 10.2, 9.9))
+    s = oracle.Sim((n, n, n), 0.8)
+    s.set_fields(np.ones(n ** 3), np.tile(U0, (n ** 3, 1)))
+    s.add_body(v, f, rigid=True, density_ratio=1.5, ref_radius=3.0, u0=tuple(U0), centroid_markers=1)
+    assert s.step(20) == 0
+    rho, u = s.fields()
+    assert np.abs(u - U0).max() < 1e-15 and np.abs(rho - 1).max() < 1e-14
+    X, Ub, Fl = s.markers(0)
+    assert np.abs(Fl).max() < 1e-15
+    assert np.abs(X - (v + 20 * U0)).max() < 1e-12
+    s.close()
+
+
+def test_centroid_markers_kinematic_membrane_is_carried_by_a_uniform_flow():
+    n = (20, 18, 22)
+    u0 = np.array([0.01, -0.004, 0.002])
+    v, f = W.icosphere(2, 3.5, (9.3, 8.1, 10.7))
+    s = oracle.Sim(n, 0.8)
+    ncell = n[0] * n[1] * n[2]
+    s.set_fields(np.ones(ncell), np.tile(u0, (ncell, 1)))
+    s.add_body(v, f, rigid=False, ks0=5e-3, Eb=0.01, kv=1.0, ref_radius=3.5, kinematic=1, centroid_markers=1)
+    assert s.step(10) == 0
+    assert np.abs(s.markers(0)[0] - (v + 10 * u0)).max() < 1e-12
+    rho, u = s.fields()
+    assert np.abs(u - u0).max() < 1e-13 and np.abs(rho - 1.0).max() < 1e-13
+    s.close()
+
+
+def vertex_areas(v, f):
+    """A third of the area of each incident triangle (Sec. 2.3)."""
+    A = 0.5 * np.linalg.norm(np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]]), axis=1)
+    Av = np.zeros(len(v))
+    for q in range(3):
+        np.add.at(Av, f[:, q], A / 3.0)
+    return Av
+
+
+@pytest.mark.parametrize("centroid", [0, 1])
+def test_spread_force_total_is_the_membrane_force(centroid):
+    """Momentum given to the fluid: the MLS weights sum to one at every
+    marker, so the spread field totals sum_l c_l F_l.  With vertex markers
+    (c_l = A_v, F_l = a_v the Newton acceleration) and with centroid markers
+    (c_l = A_t, F_l the mean acceleration of the triangle's corners) both
+    totals are sum_v A_v a_v.  A capsule in a sheared fluid with a density
+    gradient (element stresses on every triangle), after one step."""
+    n = 22
+    v, f = W.icosphere(2, 4.0, (10.6, 11.2, 10.3))
+    s = oracle.Sim((n, n, n), 0.8)
+    idx = np.arange(n ** 3)
+    cx, cz = idx % n, idx // (n * n)
+    u = np.zeros((n ** 3, 3))
+    u[:, 0] = 0.005 * (cz - 11.0) / 11.0
+    s.set_fields(1.0 + 0.002 * (cx - 11.0), u)
+    s.add_body(v, f, ks0=0.01, Eb=0.01, kv=1.0, ref_radius=4.0, centroid_markers=centroid)
+    assert s.step(1) == 0
+    Fl = s.markers(0)[2]
+    want = (vertex_areas(v, f)[:, None] * Fl).sum(axis=0)
+    got = s.fib().sum(axis=0)
+    assert np.abs(want).max() > 1e-6
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    s.close()
+
+
+@pytest.mark.parametrize("rigid_force", [0, 1])
+def test_centroid_markers_sphere_spins_at_half_shear_rate(rigid_force):
+    """Stokes' free neutrally buoyant sphere in shear with the IB markers at
+    the centroids: omega = shear_rate/2, both rigid-body force readings."""
+    case = W.case_couette_sphere(steps=200)
+    s = oracle.Sim(case.n, case.tau, bc=case.bc, wall_u=case.wall_u.ravel())
+    s.set_fields(*case.initial_fields())
+    b = case.bodies[0]
+    kw = b.kwargs()
+    kw["centroid_markers"] = 1
+    kw["rigid_force"] = rigid_force
+    s.add_body(b.verts, b.tris, **kw)
+    assert s.step(200) == 0
+    st = s.body(0)
+    gamma = 0.02 / 31.0
+    assert abs(st["omega"][1] / (gamma / 2) - 1.0) < 0.02
+    assert np.abs(st["xc"] - 15.5).max() < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("centroid", [0, 1])
+def test_kinematic_markers_take_the_linear_shear_velocity(centroid):
+    """Couette flow started at f = f^eq(1, u) with u linear in z: the
+    streamed moments of the first step are that linear field exactly (the
+    D3Q19 moments cancel its quadratic terms) and MLS reproduces linear
+    fields, so a kinematic membrane at its rest shape moves, in one step, by
+    u at its vertices (vertex markers) or by the area-weighted mean of u at
+    its triangles' centroids (centroid markers, c_l = A_t, a third to each
+    corner)."""
+    n = (24, 20, 25)
+    U = 1e-3 * (n[2] - 1) / 2.0
+    v, f = W.icosphere(2, 4.0, (11.3, 9.6, 12.2))
+    s = oracle.Sim(n, 0.8, bc=(W.PERIODIC, W.PERIODIC, W.WALL), wall_u=W.shear_walls(U).ravel())
+    s.set_fields(np.ones(n[0] * n[1] * n[2]), W.couette_profile(n, U))
+    s.add_body(v, f, ks0=5e-3, Eb=0.01, kv=1.0, ref_radius=4.0, kinematic=1, centroid_markers=centroid)
+    assert s.step(1) == 0
+
+    def ux(z):
+        return U * (2.0 * z / (n[2] - 1) - 1.0)
+
+    if centroid:
+        A = 0.5 * np.linalg.norm(np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]]), axis=1)
+        cz = v[f].mean(axis=1)[:, 2]
+        num = np.zeros(len(v))
+        for q in range(3):
+            np.add.at(num, f[:, q], A / 3.0 * ux(cz))
+        want_ux = num / vertex_areas(v, f)
+    else:
+        want_ux = ux(v[:, 2])
+    d = s.markers(0)[0] - v
+    assert np.abs(d[:, 0] - want_ux).max() < 1e-15
+    assert np.abs(d[:, 1:]).max() < 1e-15
+    if centroid:
+        assert np.abs(want_ux - ux(v[:, 2])).max() > 1e-6  # the two readings differ
+    s.close()
