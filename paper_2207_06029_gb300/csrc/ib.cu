@@ -182,9 +182,9 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
     return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
 }
 
-// MLS at markers and probes, 32 points per block.  Points 0..nv-1 are the
-// markers; point nv + 2t + side is the probe of triangle t on the outer
-// (side 0) or inner (side 1) face.  With p_k = (1, x_k - X) the fit of a
+// MLS at markers and probes, 32 points per block.  Points 0..nm-1 are the
+// markers (the vertices, or the triangle centroids); point nm + 2t + side is
+// the probe of triangle t on the outer (side 0) or inner (side 1) face.  With p_k = (1, x_k - X) the fit of a
 // field f is a = A^-1 b_f, A = sum_k W_k p_k p_k^T, b_f = sum_k W_k p_k f_k
 // (Eq. l2norm), i.e. f(X) = a_0 and grad f = (a_1, a_2, a_3).
 //  phase 0: one lane per point: position (probes: triangle geometry), the
@@ -201,7 +201,7 @@ template <typename R>
 __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattice &L, const BodyView &B, int *err,
                                          MlsSmem<R> &sm, const int vb, const int nvb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int npts = B.nv + 2 * B.nt;
+    const int nm = B.nm, npts = nm + 2 * B.nt;
     const int p0 = vb * kPts;
     const long long st = L.stride;
     const int nxy = L.nx * L.ny;
@@ -220,14 +220,17 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
         sm.vol[lane] = 0.0;
         if (p >= 0) {
             double P[3];
-            if (p < B.nv) {
+            if (p < nm && B.centroid) {
+                const int *tv = B.tri + 3 * p;
+                for (int a = 0; a < 3; ++a) P[a] = (B.X[3 * tv[0] + a] + B.X[3 * tv[1] + a] + B.X[3 * tv[2] + a]) / 3.0;
+            } else if (p < nm) {
                 P[0] = B.X[3 * p];
                 P[1] = B.X[3 * p + 1];
                 P[2] = B.X[3 * p + 2];
             } else {
                 // probe X_c +- 1.2 n, with X_c = x_0 + (e1 + e2)/3 and the
                 // triangle's edges and normal from origin-relative positions
-                const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
+                const int t = (p - nm) >> 1, side = (p - nm) & 1;
                 const int *tv = B.tri + 3 * t;
                 const R *Xr = (const R *)B.Xrel;
                 R r0[3], e1[3], e2[3];
@@ -303,7 +306,7 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
             gu[j][1] = mom[st + node];
             gu[j][2] = mom[2 * st + node];
             gu[j][3] = mom[3 * st + node];
-            if (p >= B.nv)
+            if (p >= nm)
                 gu[j][0] = mom[node];
             else
                 B.node[27 * p + lane] = node;
@@ -383,11 +386,12 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
         if (!spd_inverse4(a, inv)) atomicCAS(err, 0, -1);
         R Ai[16];
         for (int q = 0; q < 16; ++q) Ai[q] = R(inv[q]);
-        if (p < B.nv) {
+        if (p < nm) {
             for (int q = 0; q < 4; ++q) sm.row0[lane][q] = Ai[q];
+            double *Uo = B.centroid ? B.Uc : B.U;
             for (int jj = 0; jj < 3; ++jj) {
                 const R *bu = S + 14 + 4 * jj;
-                B.U[3 * p + jj] = (double)(Ai[0] * bu[0] + Ai[1] * bu[1] + Ai[2] * bu[2] + Ai[3] * bu[3]);
+                Uo[3 * p + jj] = (double)(Ai[0] * bu[0] + Ai[1] * bu[1] + Ai[2] * bu[2] + Ai[3] * bu[3]);
             }
         } else {
             // fits: c_f[i] = sum_m Ai[i][m] b_f[m]
@@ -399,7 +403,7 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                     cu[jj][i] = Ai[4 * i] * bu[0] + Ai[4 * i + 1] * bu[1] + Ai[4 * i + 2] * bu[2] + Ai[4 * i + 3] * bu[3];
                 }
             }
-            const int t = (p - B.nv) >> 1, side = (p - B.nv) & 1;
+            const int t = (p - nm) >> 1, side = (p - nm) & 1;
             const R rho = R(1) + cr[0];
             const R nu = pick<R>(L.nu_d, L.nu_f);
             R *pr = (R *)B.probe + 8 * t + 4 * side;
@@ -447,7 +451,7 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
         const int lp = warp * kPerWarp + j;
         const int p = sm.pid[lp];
         if (p < 0) break;
-        if (p >= B.nv) continue;  // probes keep no transfer weights
+        if (p >= nm) continue;  // probes keep no transfer weights
         if (lane < 27) {
             const R *r0 = sm.row0[lp];
             const R phi = sm.W[lp][lane] *
@@ -546,13 +550,14 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
     __shared__ BlockBox sbox;
     __shared__ R s_F[8][4];   // per vertex warp: total force (3) and vertex area
     __shared__ R s_Fl[8][3];  // per vertex warp: Lagrangian force
+    __shared__ double s_U[8][3];  // centroid markers: the vertex velocity
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int v0 = vb * (blockDim.x >> 5);  // first vertex of the block
     const int v = v0 + warp;
     // the spreading lanes fetch their node and weight first
     int snode = 0;
     R sphi = R(0);
-    if (v < B.nv && lane < 27) {
+    if (!B.centroid && v < B.nv && lane < 27) {
         snode = B.node[27 * v + lane];
         sphi = ((const R *)B.phi)[27 * v + lane];
     }
@@ -620,6 +625,7 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
     }
     // element terms: volume penalty and hydrodynamic force, 1/3 per vertex
     R Al = R(0);
+    double Uv[3] = {0.0, 0.0, 0.0};
     for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32) {
         const int t = B.vt_list[q] / 3;
         const R *tg = (const R *)B.tri_geo + 8 * t;
@@ -627,6 +633,8 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
         R Fh[3] = {R(0), R(0), R(0)};
         if (!B.kinematic) tri_hydro<R>(B, t, Fh);  // kinematic IB: the fluid's stresses stay in the fluid
         for (int a = 0; a < 3; ++a) F[a] += (cv * tg[a] * tg[3] + Fh[a]) / R(3);
+        if (B.centroid)
+            for (int a = 0; a < 3; ++a) Uv[a] += (double)(tg[3] / R(3)) * B.Uc[3 * t + a];
     }
     for (int a = 0; a < 3; ++a) F[a] = warp_sum(F[a]);
     Al = warp_sum(Al);
@@ -635,6 +643,13 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
         s_F[warp][1] = F[1];
         s_F[warp][2] = F[2];
         s_F[warp][3] = Al;
+    }
+    if (B.centroid) {
+        // the vertex moves with the area-weighted mean of its triangles'
+        // centroid velocities
+        for (int a = 0; a < 3; ++a) Uv[a] = warp_sum(Uv[a]);
+        if (lane == 0)
+            for (int a = 0; a < 3; ++a) s_U[warp][a] = Uv[a] / (double)Al;
     }
     }
     __syncthreads();
@@ -645,7 +660,13 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
     if (warp == (vb & 7) && lane < 24 && v0 + lane / 3 < B.nv) {
         const int j = lane / 3, a = lane % 3, vj = v0 + j;
         const double acc = (double)s_F[j][a] * B.inv_mv;
-        const double U = B.U[3 * vj + a];
+        double U;
+        if (B.centroid) {
+            U = s_U[j][a];
+            B.U[3 * vj + a] = U;
+        } else {
+            U = B.U[3 * vj + a];
+        }
         const double Ub = U + acc;
         const double Fla = Ub - U;
         const double x = B.X[3 * vj + a], xp = B.Xprev[3 * vj + a];
@@ -665,7 +686,8 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
         s_Fl[j][a] = R(Fla);
     }
     __syncthreads();
-    if (v < B.nv) spread_node<R>(L, lane, snode, s_F[warp][3] * sphi, s_Fl[warp], force, stamp, step);
+    if (!B.centroid && v < B.nv)
+        spread_node<R>(L, lane, snode, s_F[warp][3] * sphi, s_Fl[warp], force, stamp, step);
     __syncthreads();
     sbox.flush(B.bbox_next);
 }
@@ -707,6 +729,19 @@ __device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int v
         f[3] = r[1] * Fh[2] - r[2] * Fh[1];
         f[4] = r[2] * Fh[0] - r[0] * Fh[2];
         f[5] = r[0] * Fh[1] - r[1] * Fh[0];
+    } else if (t < B.nt && B.centroid) {
+        // momentum exchange, centroid markers: minus the previous step's IB
+        // force of the triangle's marker times its area, about x_c
+        const R *tg = (const R *)B.tri_geo + 8 * t;
+        const R c = -tg[3];
+        const R Fv[3] = {c * R(B.Flc[3 * t]), c * R(B.Flc[3 * t + 1]), c * R(B.Flc[3 * t + 2])};
+        const R r[3] = {tg[4] - xc[0], tg[5] - xc[1], tg[6] - xc[2]};
+        f[0] = Fv[0];
+        f[1] = Fv[1];
+        f[2] = Fv[2];
+        f[3] = r[1] * Fv[2] - r[2] * Fv[1];
+        f[4] = r[2] * Fv[0] - r[0] * Fv[2];
+        f[5] = r[0] * Fv[1] - r[1] * Fv[0];
     } else if (t < B.nt) {
         // momentum exchange: minus the IB force of the previous step, each
         // corner carrying a third of the triangle's area (sum_l A_l F_l)
@@ -905,16 +940,30 @@ __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyV
     __shared__ BlockBox sbox;
     __shared__ R s_Al[8];
     __shared__ R s_Fl[8][3];
+    __shared__ double s_U[8][3];  // centroid markers: the vertex velocity
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int v0 = vb * (blockDim.x >> 5);
     const int v = v0 + warp;
     sbox.init();
     if (v < B.nv) {
         R Al = R(0);
-        for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32)
-            Al += ((const R *)B.tri_geo)[8 * (B.vt_list[q] / 3) + 3] / R(3);
+        double Uv[3] = {0.0, 0.0, 0.0};
+        for (int q = B.vt_ptr[v] + lane; q < B.vt_ptr[v + 1]; q += 32) {
+            const int t = B.vt_list[q] / 3;
+            const R At3 = ((const R *)B.tri_geo)[8 * t + 3] / R(3);
+            Al += At3;
+            if (B.centroid)
+                for (int a = 0; a < 3; ++a) Uv[a] += (double)At3 * B.Uc[3 * t + a];
+        }
         Al = warp_sum(Al);
         if (lane == 0) s_Al[warp] = Al;
+        if (B.centroid) {
+            // the vertex velocity: area-weighted mean of its triangles'
+            // centroid velocities
+            for (int a = 0; a < 3; ++a) Uv[a] = warp_sum(Uv[a]);
+            if (lane == 0)
+                for (int a = 0; a < 3; ++a) s_U[warp][a] = Uv[a] / (double)Al;
+        }
     }
     __syncthreads();
     // FP64 for the block's 8 markers at once: lane 3 j + a of one warp
@@ -926,7 +975,14 @@ __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyV
         const double *xc = S + RigidState::XC, *Rn = S + RigidState::ROT;
         const double r1 = B.X[3 * vj + a1] - xo[a1], r2 = B.X[3 * vj + a2] - xo[a2];
         const double ub = un[a] + (wn[a1] * r2 - wn[a2] * r1);  // (w x r)_a
-        const double Fla = ub - B.U[3 * vj + a];
+        double U;
+        if (B.centroid) {
+            U = s_U[j][a];
+            B.U[3 * vj + a] = U;
+        } else {
+            U = B.U[3 * vj + a];
+        }
+        const double Fla = ub - U;
         B.Ub[3 * vj + a] = ub;
         B.Fl[3 * vj + a] = Fla;
         const double *xb = B.Xbody + 3 * vj;
@@ -937,7 +993,7 @@ __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyV
         s_Fl[j][a] = R(Fla);
     }
     __syncthreads();
-    if (v < B.nv) spread_warp<R>(L, B, v, lane, s_Al[warp], s_Fl[warp], force, stamp, step);
+    if (!B.centroid && v < B.nv) spread_warp<R>(L, B, v, lane, s_Al[warp], s_Fl[warp], force, stamp, step);
     __syncthreads();
     sbox.flush(B.bbox_next);
 }
@@ -946,6 +1002,54 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
                                                        uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
     rigid_markers_body<R>(L, B, force, stamp, dstep, blockIdx.x);
+}
+
+// IB force of centroid markers, one warp per triangle: the boundary
+// velocity at the centroid (rigid: u + w x (X_c - x_c) of level n;
+// membrane: the interpolated velocity advanced by the mean Newton
+// acceleration of the triangle's vertices, which the structure kernel left
+// as their Lagrangian force), F_l = U_b - U spread with c_l = A_t.
+template <typename R>
+__global__ void __launch_bounds__(256) k_centroid_spread(Lattice L, BodyView B, R *__restrict__ force,
+                                                         uint32_t *__restrict__ stamp,
+                                                         const uint32_t *__restrict__ dstep) {
+    const uint32_t step = *dstep;
+    __shared__ R s_A[8];
+    __shared__ R s_Fl[8][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int vb = blockIdx.x;
+    const int t0 = vb * 8, t = t0 + warp;
+    int snode = 0;
+    R sphi = R(0);
+    if (t < B.nt && lane < 27) {
+        snode = B.node[27 * t + lane];
+        sphi = ((const R *)B.phi)[27 * t + lane];
+    }
+    if (t < B.nt && lane == 0) s_A[warp] = ((const R *)B.tri_geo)[8 * t + 3];
+    // FP64 for the block's 8 markers at once: lane 3 j + a of one warp
+    // handles component a of marker j
+    if (warp == (vb & 7) && lane < 24 && t0 + lane / 3 < B.nt) {
+        const int j = lane / 3, a = lane % 3, tj = t0 + j;
+        const int *tv = B.tri + 3 * tj;
+        const double uc = B.Uc[3 * tj + a];
+        double ub;
+        if (B.rigid) {
+            const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+            const double *S = B.rstate;
+            const double *un = S + RigidState::U, *wn = S + RigidState::W, *xo = S + RigidState::XC_OLD;
+            const double r1 = (B.X[3 * tv[0] + a1] + B.X[3 * tv[1] + a1] + B.X[3 * tv[2] + a1]) / 3.0 - xo[a1];
+            const double r2 = (B.X[3 * tv[0] + a2] + B.X[3 * tv[1] + a2] + B.X[3 * tv[2] + a2]) / 3.0 - xo[a2];
+            ub = un[a] + (wn[a1] * r2 - wn[a2] * r1);
+        } else {
+            const double acc = B.Fl[3 * tv[0] + a] + B.Fl[3 * tv[1] + a] + B.Fl[3 * tv[2] + a];
+            ub = uc + acc / 3.0;
+        }
+        const double Fla = ub - uc;
+        B.Flc[3 * tj + a] = Fla;
+        s_Fl[j][a] = R(Fla);
+    }
+    __syncthreads();
+    if (t < B.nt) spread_node<R>(L, lane, snode, s_A[warp] * sphi, s_Fl[warp], force, stamp, step);
 }
 
 // ---- batch kernels: the bodies of all lattices of a batch per launch ----
@@ -1024,7 +1128,7 @@ cudaError_t launch_batch_ib(int prec, const BatchTables &T, const BatchGrid &G, 
 }
 
 // ---- launchers ----
-int mls_blocks(const BodyView &B) { return (B.nv + 2 * B.nt + kPts - 1) / kPts; }
+int mls_blocks(const BodyView &B) { return (B.nm + 2 * B.nt + kPts - 1) / kPts; }
 
 template <typename S, typename R>
 static cudaError_t ib_front_t(const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm, int *err,
@@ -1063,6 +1167,16 @@ cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const B
     }
 }
 
+static cudaError_t launch_centroid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
+                                   const uint32_t *step, cudaStream_t s) {
+    const unsigned g = (unsigned)((B.nt + 7) / 8);  // 8 warps (triangles) per block
+    if (prec == 0)
+        k_centroid_spread<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
+    else
+        k_centroid_spread<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
                             const uint32_t *step, cudaStream_t s) {
     const unsigned g = (unsigned)((B.nv + 7) / 8);  // 8 warps (vertices) per block
@@ -1070,7 +1184,9 @@ cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void 
         k_membrane<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
     else
         k_membrane<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !B.centroid) return e;
+    return launch_centroid(prec, L, B, force, stamp, step, s);
 }
 
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
@@ -1087,7 +1203,9 @@ cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *fo
         k_rigid_markers<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
     else
         k_rigid_markers<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !B.centroid) return e;
+    return launch_centroid(prec, L, B, force, stamp, step, s);
 }
 
 }  // namespace lbib

@@ -28,6 +28,7 @@ struct DevBody {
     double *X[3] = {nullptr, nullptr, nullptr};  // rotating buffers: prev, cur, next
     int cur = 1;
     double *U = nullptr, *Ub = nullptr, *Fl = nullptr, *tri_vol = nullptr;
+    double *Uc = nullptr, *Flc = nullptr;  // centroid markers
     void *phi = nullptr, *tri_geo = nullptr, *probe = nullptr;  // arithmetic precision R
     void *Xrel[2] = {nullptr, nullptr};                          // R: X - origin, current and next
     int *perm = nullptr;  // MLS points (markers, probes) in cell order
@@ -263,6 +264,10 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.U = b.U;
     v.Ub = b.Ub;
     v.Fl = b.Fl;
+    v.centroid = b.p.centroid_markers;
+    v.nm = b.p.centroid_markers ? b.nt : b.nv;
+    v.Uc = b.Uc;
+    v.Flc = b.Flc;
     v.phi = b.phi;
     v.node = b.node;
     v.perm = c->sort_points ? b.perm : nullptr;
@@ -689,10 +694,16 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     b.U = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
     b.Ub = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
     b.Fl = upload(c, std::vector<double>(3 * (size_t)nv, 0.0), &rc);
-    b.phi = dev_alloc(c, c->relem * 27 * (size_t)nv);
-    b.node = (int *)dev_alloc(c, sizeof(int) * 27 * (size_t)nv);
+    const bool cm = bp->centroid_markers != 0;
+    const int nm = cm ? nt : nv;  // IB markers: vertices or triangle centroids
+    if (cm) {
+        b.Uc = upload(c, std::vector<double>(3 * (size_t)nt, 0.0), &rc);
+        b.Flc = upload(c, std::vector<double>(3 * (size_t)nt, 0.0), &rc);
+    }
+    b.phi = dev_alloc(c, c->relem * 27 * (size_t)nm);
+    b.node = (int *)dev_alloc(c, sizeof(int) * 27 * (size_t)nm);
     b.tri = upload(c, T, &rc);
-    // marker binning: the MLS points (vertices; probes at their triangle's
+    // marker binning: the MLS points (markers; probes at their triangle's
     // centroid) ordered by the Morton code of their nearest node
     // floor(X + 1/2), so that a block's points share support nodes
     {
@@ -711,18 +722,20 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
             }
             return morton(q[0], q[1], q[2]);
         };
-        const int npts = nv + 2 * nt;
+        const int npts = nm + 2 * nt;
         std::vector<std::pair<uint64_t, int>> keyed(npts);
-        for (int v = 0; v < nv; ++v) keyed[v] = {cell(&verts[3 * v]), v};
         for (int t = 0; t < nt; ++t) {
             double cen[3];
             for (int a = 0; a < 3; ++a)
                 cen[a] = (verts[3 * tris[3 * t] + a] + verts[3 * tris[3 * t + 1] + a] + verts[3 * tris[3 * t + 2] + a]) /
                          3.0;
             const uint64_t k = cell(cen);
-            keyed[nv + 2 * t] = {k, nv + 2 * t};
-            keyed[nv + 2 * t + 1] = {k, nv + 2 * t + 1};
+            if (cm) keyed[t] = {k, t};
+            keyed[nm + 2 * t] = {k, nm + 2 * t};
+            keyed[nm + 2 * t + 1] = {k, nm + 2 * t + 1};
         }
+        if (!cm)
+            for (int v = 0; v < nv; ++v) keyed[v] = {cell(&verts[3 * v]), v};
         std::stable_sort(keyed.begin(), keyed.end(),
                          [](const std::pair<uint64_t, int> &a, const std::pair<uint64_t, int> &b) {
                              return a.first < b.first;
@@ -807,6 +820,7 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         BodyView tmp{};
         tmp.nv = nv;
         tmp.nt = nt;
+        tmp.nm = nm;
         // partial sums: one per MLS block (membrane volume) or six per
         // force block (rigid force and moment)
         b.nvol_part = std::max(mls_blocks(tmp), 6 * ((nt + 255) / 256));
@@ -885,10 +899,10 @@ int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external, int 
         cudaError_t e;
         if (b.rigid) {
             e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->d_step, hi);
-            c->launches += 2;
+            c->launches += 2 + v.centroid;
         } else {
             e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->d_step, hi);
-            c->launches += 1;
+            c->launches += 1 + v.centroid;
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
     }
@@ -1665,6 +1679,11 @@ int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out) {
             delete b;
             return bfail(nullptr, LBIB_EINVAL, "the contexts of a batch share one precision");
         }
+        for (const DevBody &db : c->bodies)
+            if (db.p.centroid_markers) {
+                delete b;
+                return bfail(nullptr, LBIB_EINVAL, "bodies with centroid markers are stepped by lbib_step only");
+            }
         b->prec = c->prec;
         b->ctx.push_back(c);
     }

@@ -160,9 +160,14 @@ struct BodyView {
     double *U;              // [3nv] interpolated fluid velocity
     double *Ub;             // [3nv] boundary velocity imposed by the IB force
     double *Fl;             // [3nv] Lagrangian IB force
-    void *phi;              // [27nv] R: MLS transfer weights of level n
-    int *node;              // [27nv] support node indices
-    const int *perm;        // [nv + 2nt] MLS points in cell order (markers, probes), or nullptr
+    // IB markers: the nv vertices, or (centroid) the nt triangle centroids
+    int centroid;
+    int nm;                 // number of markers: nv or nt
+    double *Uc;             // centroid markers [3nt]: interpolated fluid velocity
+    double *Flc;            // centroid markers [3nt]: Lagrangian IB force
+    void *phi;              // [27nm] R: MLS transfer weights of level n
+    int *node;              // [27nm] support node indices
+    const int *perm;        // [nm + 2nt] MLS points in cell order (markers, probes), or nullptr
     const int *tri;         // [3nt]
     void *tri_geo;          // [8nt] R: unit normal (3), area, centroid - origin (3), unused
     double *tri_vol;        // [nt] volume terms (x_0 - o) . (e1 x e2)

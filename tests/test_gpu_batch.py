@@ -192,3 +192,15 @@ def test_batch_rejects_mixed_precisions(lbib):
     assert ei.value.code == lbib.LBIB_EINVAL
     a.close()
     b.close()
+
+
+def test_batch_refuses_centroid_marker_bodies(lbib):
+    case = mixed_cases(W.PREC_FP32)[0]
+    case.bodies[0].centroid_markers = 1
+    ctxs = [lbib.Context.from_case(case), lbib.Context.from_case(mixed_cases(W.PREC_FP32)[1])]
+    with pytest.raises(lbib.LbibError) as ei:
+        lbib.Batch(ctxs)
+    assert ei.value.code == lbib.LBIB_EINVAL
+    ctxs[0].step(2)  # still steps alone
+    for ctx in ctxs:
+        ctx.close()

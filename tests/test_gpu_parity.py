@@ -170,6 +170,44 @@ def test_fp64_momentum_exchange_rigid_bodies(lbib):
         check_fp64(g, o)
 
 
+def centroid_cases():
+    """Centroid IB markers on every body kind: a perturbed capsule in shear
+    (dynamic and kinematic), a heavy sphere settling in a walled box (both
+    rigid-body force readings) and the free sphere in Couette flow."""
+    out = []
+    for kinematic in (0, 1):
+        case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01,
+                                    kv=1.0, precision=W.PREC_FP64)
+        case.bodies[0].verts = W.perturb(case.bodies[0].verts, 0.02, seed=11)
+        case.bodies[0].kinematic = kinematic
+        out.append(case)
+    v, f = W.icosphere(3, 3.5, (10.0, 11.0, 17.0))
+    for rigid_force in (0, 1):
+        out.append(W.Case("settle_c", (20, 22, 30), 0.7, (W.WALL, W.WALL, W.WALL), np.zeros((6, 3)),
+                          precision=W.PREC_FP64,
+                          bodies=[W.Body(v, f, rigid=True, density_ratio=1.5, ref_radius=3.5,
+                                         gravity=(0.0, 0.0, -2e-5), rigid_force=rigid_force)]))
+    out.append(W.case_couette_sphere())
+    for case in out:
+        case.bodies[0].centroid_markers = 1
+    return out
+
+
+@pytest.mark.parametrize("k", range(5))
+def test_fp64_centroid_markers(lbib, k):
+    case = centroid_cases()[k]
+    g = run_gpu(lbib, case, 30)
+    o = run_oracle(case, 30)
+    check_fp64(g, o)
+    if case.bodies[0].rigid:
+        # omega of the settling sphere is round-off of cancelling moments:
+        # held on the scale u / R of the body's motion
+        bg, bo = g["bodies"][0], o["bodies"][0]
+        scale = max(np.abs(bo["u"]).max(), np.abs(bo["omega"]).max() * case.bodies[0].ref_radius)
+        assert np.abs(bg["u"] - bo["u"]).max() <= 1e-12 * scale
+        assert np.abs(bg["omega"] - bo["omega"]).max() * case.bodies[0].ref_radius <= 1e-12 * scale
+
+
 def test_fp64_two_bodies_and_gravity_periodic(lbib):
     """Two bodies in one periodic lattice: a settling rigid sphere and a
     capsule (shared force field, several spreads per step)."""
@@ -204,6 +242,16 @@ def test_fp32_capsule_96_full_size(lbib, Ca, Eb):
     leaves the stability region of the explicit marker update (the oracle
     diverges as well)."""
     case = W.case_capsule_shear(Ca=Ca, Eb=Eb, kv=1.0)
+    g = run_gpu(lbib, case, 60)
+    o = run_oracle(case, 60)
+    check_fp32(g, o)
+
+
+def test_fp32_capsule_96_centroid_markers(lbib):
+    """The 96^3 capsule (Ca 0.05) with its IB markers at the 5120 triangle
+    centroids, FP32, 60 steps."""
+    case = W.case_capsule_shear(Ca=0.05, Eb=0.01, kv=1.0)
+    case.bodies[0].centroid_markers = 1
     g = run_gpu(lbib, case, 60)
     o = run_oracle(case, 60)
     check_fp32(g, o)
