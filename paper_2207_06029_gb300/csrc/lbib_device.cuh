@@ -15,6 +15,15 @@ constexpr int kPeriodic = 0;
 constexpr int kWall = 1;
 constexpr int kTile = 8;  // edge of the cubic tiles that carry an IB-force flag
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may be scheduled once every block of
+// its predecessor in the stream has called chain_release() (or ended); it
+// calls chain_wait() before its first global-memory access, which returns
+// when the predecessor has completed and its writes are visible.  Without
+// that launch attribute chain_wait() returns at once.
+__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // D3Q19 velocities, columns of the matrix of Eq. (e_i), Sec. 2.1.
 __host__ __device__ constexpr int ex(int i) {
     return (i == 1 || i == 7 || i == 8 || i == 9 || i == 10) ? 1

@@ -8,6 +8,26 @@
 
 namespace lbib {
 
+// Launches a kernel of the step chain with programmatic stream
+// serialization: its blocks may be scheduled while the previous kernel in
+// the stream ends, and wait in chain_wait() for that kernel's results
+// (this hides the launch gap between the short kernels of the IB stage).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // sweep.cu
 // part: 0 the whole lattice, 1 the nodes outside box, 2 the nodes inside box
 // stamp == nullptr: no IB force is read; step points to the device step counter
