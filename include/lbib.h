@@ -70,7 +70,10 @@ typedef struct {
     int precision;           /* lbib_prec */
     void *stream;            /* cudaStream_t to run on, or NULL for a library-owned stream */
     /* optional device allocator (e.g. a PyTorch caching allocator); both NULL
-     * means cudaMalloc / cudaFree */
+     * means cudaMalloc / cudaFree.  Blocks must be 256-byte aligned, as
+     * cudaMalloc's are (the kernels use 16-byte vector accesses); a
+     * misaligned block is handed back to free and counts as a failed
+     * allocation (LBIB_ENOMEM) */
     void *(*alloc)(size_t bytes, void *user);
     void (*free)(void *ptr, void *user);
     void *alloc_user;
@@ -272,6 +275,14 @@ int lbib_batch_counters(void *batch, long long *steps, long long *launches);
  * advance by about 14 * (7 + 2 * steps) steps.  choice (optional, 3 ints):
  * threads (0: one launch per lattice), order, cells per thread. */
 int lbib_batch_autotune(void *batch, int steps, int *choice);
+
+/* Sets what lbib_batch_autotune chooses: threads a block of the batched
+ * sweep (a multiple of 32 up to 512; 0: one one-lattice sweep launch per
+ * lattice on side streams), order (0 lattices as given, 1 largest first)
+ * and cells a sweep thread (1 to 16).  Waits for the batch's queued work
+ * and rebuilds its tables.  LBIB_EINVAL for values out of range (the batch
+ * is unchanged then).  Results are the same in every configuration. */
+int lbib_batch_set_config(void *batch, int threads, int order, int cells_per_thread);
 
 /* Releases the batch (not its contexts). */
 void lbib_batch_destroy(void *batch);

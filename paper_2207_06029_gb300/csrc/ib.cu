@@ -37,6 +37,33 @@ __device__ __forceinline__ T warp_sum(T v) {
 // rho - 1 and u* = (sum f e + g_ext/2)/rho.  Grid-stride over the box
 // recorded on the device by the previous step's update.
 // ---------------------------------------------------------------------------
+// Support-region moments, node-interleaved: mom[4 node + q] holds rho - 1
+// and the predictor velocity u*_x, u*_y, u*_z of node `node`, so that the
+// MLS gather of one support node is a single 16-byte (FP32) or two
+// 16-byte (FP64) loads.
+__device__ __forceinline__ void mom_store(float *m, int node, float a, float b, float c, float d) {
+    reinterpret_cast<float4 *>(m)[node] = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void mom_store(double *m, int node, double a, double b, double c, double d) {
+    reinterpret_cast<double2 *>(m)[2 * node] = make_double2(a, b);
+    reinterpret_cast<double2 *>(m)[2 * node + 1] = make_double2(c, d);
+}
+__device__ __forceinline__ void mom_load(const float *m, int node, float *v) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(m) + node);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void mom_load(const double *m, int node, double *v) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(m) + 2 * node);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(m) + 2 * node + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
 template <typename S, typename R>
 __device__ __forceinline__ void moments_body(const S *__restrict__ fin, const Lattice &L, const int *__restrict__ box,
                                              int *__restrict__ box_next, R *__restrict__ mom,
@@ -88,10 +115,9 @@ __device__ __forceinline__ void moments_body(const S *__restrict__ fin, const La
         }
         const int node = c[0] + L.nx * c[1] + nxy * c[2];
         const R rho = R(1) + drho;
-        mom[node] = drho;
-        mom[st + node] = (jx + R(0.5) * pick<R>(L.gext_d[0], L.gext_f[0])) / rho;
-        mom[2 * st + node] = (jy + R(0.5) * pick<R>(L.gext_d[1], L.gext_f[1])) / rho;
-        mom[3 * st + node] = (jz + R(0.5) * pick<R>(L.gext_d[2], L.gext_f[2])) / rho;
+        mom_store(mom, node, drho, (jx + R(0.5) * pick<R>(L.gext_d[0], L.gext_f[0])) / rho,
+                  (jy + R(0.5) * pick<R>(L.gext_d[1], L.gext_f[1])) / rho,
+                  (jz + R(0.5) * pick<R>(L.gext_d[2], L.gext_f[2])) / rho);
     }
 }
 
@@ -204,7 +230,6 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nm = B.nm, npts = nm + 2 * B.nt;
     const int p0 = vb * kPts;
-    const long long st = L.stride;
     const int nxy = L.nx * L.ny;
     const int n[3] = {L.nx, L.ny, L.nz};
 
@@ -304,13 +329,11 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                 cw[a] = cc;
             }
             const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
-            gu[j][1] = mom[st + node];
-            gu[j][2] = mom[2 * st + node];
-            gu[j][3] = mom[3 * st + node];
-            if (p >= nm)
-                gu[j][0] = mom[node];
-            else
+            mom_load(mom, node, gu[j]);
+            if (p < nm) {
+                gu[j][0] = R(0);  // markers use the velocity fit only
                 B.node[27 * p + lane] = node;
+            }
         }
     }
 #pragma unroll

@@ -112,6 +112,10 @@ void *dev_alloc(Ctx *c, size_t bytes) {
     void *ptr = nullptr;
     if (c->p.alloc) {
         ptr = c->p.alloc(bytes, c->p.alloc_user);
+        if (ptr && (reinterpret_cast<uintptr_t>(ptr) & 255)) {
+            if (c->p.free) c->p.free(ptr, c->p.alloc_user);
+            ptr = nullptr;
+        }
     } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
         cudaGetLastError();
         ptr = nullptr;
@@ -1846,6 +1850,19 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
         choice[2] = best_c;
     }
     return rc ? rc : rc2;
+}
+
+int lbib_batch_set_config(void *h, int threads, int order, int cells_per_thread) {
+    Batch *b = as_batch(h);
+    if (!b) return LBIB_EINVAL;
+    if (threads < 0 || threads > 512 || threads % 32 || order < 0 || order > 1 || cells_per_thread < 1 ||
+        cells_per_thread > 16)
+        return bfail(b, LBIB_EINVAL, "bad batch configuration");
+    b->sweep_split = threads == 0;
+    b->sweep_threads = threads ? threads : 256;
+    b->order = order;
+    b->sweep_cpt = cells_per_thread;
+    return batch_build(b);
 }
 
 void lbib_batch_destroy(void *h) {

@@ -184,6 +184,31 @@ def test_context_stepped_outside_the_batch_is_refused(lbib):
         ctx.close()
 
 
+@pytest.mark.parametrize("config", [(0, 1, 4), (128, 1, 1), (512, 0, 16), (64, 0, 3)])
+def test_batch_configurations_compute_the_same_steps(lbib, config):
+    """lbib_batch_set_config: per-lattice sweeps or the batched sweep in
+    other shapes, FP64, against the contexts stepped alone."""
+    cases = mixed_cases(W.PREC_FP64)
+    alone = run_alone(lbib, cases, 8)
+    ctxs = [lbib.Context.from_case(c) for c in cases]
+    batch = lbib.Batch(ctxs)
+    batch.set_config(*config)
+    batch.step(8)
+    batch.sync()
+    for ctx, case, a in zip(ctxs, cases, alone):
+        s = state(ctx, case)
+        assert rel(s["f"], a["f"]) < 1e-13
+        for x, y in zip(s["X"], a["X"]):
+            assert rel(x, y) < 1e-13
+    for bad in [(100, 0, 4), (1024, 0, 4), (256, 2, 4), (256, 0, 0), (256, 0, 17)]:
+        with pytest.raises(lbib.LbibError) as ei:
+            batch.set_config(*bad)
+        assert ei.value.code == lbib.LBIB_EINVAL
+    batch.close()
+    for ctx in ctxs:
+        ctx.close()
+
+
 def test_batch_rejects_mixed_precisions(lbib):
     a = lbib.Context((8, 8, 8), 0.8, precision=lbib.LBIB_FP32)
     b = lbib.Context((8, 8, 8), 0.8, precision=lbib.LBIB_FP64)
