@@ -162,6 +162,23 @@ int lbib_get_populations(void *ctx, double *f, int on_device);
  * [3*nv] host doubles; any may be NULL.  Synchronises. */
 int lbib_get_markers(void *ctx, int body, double *X, double *V, double *F);
 
+/* The same three arrays, copied asynchronously: the copies are queued on the
+ * context's stream after the steps already queued, and the call returns at
+ * once.  The host arrays must stay valid until the stream reaches the
+ * copies, and are read only after a synchronisation (lbib_sync, or an event
+ * recorded on the context's stream after this call); page-locked host
+ * memory makes the copies overlap later steps.  Device errors of the steps
+ * surface at the next synchronising call.  LBIB_EINVAL for a bad body. */
+int lbib_get_markers_async(void *ctx, int body, double *X, double *V, double *F);
+
+/* Advances the context by nsteps steps and queues, after each step k, the
+ * asynchronous copy of body `body`'s markers into X + 3 nv k, V + 3 nv k and
+ * F + 3 nv k (host arrays of nsteps * 3 * nv doubles; any may be NULL): a
+ * trajectory recorded without a host round trip per step.  The same rules
+ * as lbib_get_markers_async apply to the host arrays.  Errors as
+ * lbib_step. */
+int lbib_step_markers(void *ctx, int nsteps, int body, double *X, double *V, double *F);
+
 /* Body summary after the last step.  Synchronises. */
 int lbib_get_body(void *ctx, int body, lbib_body_state *out);
 

@@ -1143,20 +1143,41 @@ int lbib_get_populations(void *h, double *f, int on_device) {
     return rc;
 }
 
-int lbib_get_markers(void *h, int body, double *X, double *V, double *F) {
+int lbib_get_markers_async(void *h, int body, double *X, double *V, double *F) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;
     if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
-    int rc = sync_ctx(c);
-    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    if (c->err && c->err != LBIB_EBODY_WALL) return c->err;
     DevBody &b = c->bodies[body];
     const size_t bytes = 3 * (size_t)b.nv * sizeof(double);
     cudaError_t e = cudaSuccess;
-    if (X) e = cudaMemcpy(X, b.X[b.cur], bytes, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && V) e = cudaMemcpy(V, b.Ub, bytes, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && F) e = cudaMemcpy(F, b.Fl, bytes, cudaMemcpyDeviceToHost);
+    if (X) e = cudaMemcpyAsync(X, b.X[b.cur], bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && V) e = cudaMemcpyAsync(V, b.Ub, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, b.Fl, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "markers copy");
-    return rc;
+    return LBIB_OK;
+}
+
+int lbib_step_markers(void *h, int nsteps, int body, double *X, double *V, double *F) {
+    Ctx *c = as_ctx(h);
+    if (!c || nsteps < 0) return LBIB_EINVAL;
+    if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
+    const size_t n3 = 3 * (size_t)c->bodies[body].nv;
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = lbib_step(h, 1);
+        if (!rc)
+            rc = lbib_get_markers_async(h, body, X ? X + n3 * k : nullptr, V ? V + n3 * k : nullptr,
+                                        F ? F + n3 * k : nullptr);
+        if (rc) return rc;
+    }
+    return LBIB_OK;
+}
+
+int lbib_get_markers(void *h, int body, double *X, double *V, double *F) {
+    // the copies and the device error word in one round trip
+    int rc = lbib_get_markers_async(h, body, X, V, F);
+    if (rc) return rc;
+    return sync_ctx(as_ctx(h));
 }
 
 int lbib_get_body(void *h, int body, lbib_body_state *out) {

@@ -78,7 +78,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
-           "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_body", "lbib_counters",
+           "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_markers_async", "lbib_step_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
            "lbib_device_bytes", "lbib_save", "lbib_load", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
@@ -111,6 +111,8 @@ def load():
         L.lbib_get_populations.argtypes = [vp, vp, C.c_int]
         L.lbib_get_totals.argtypes = [vp, dp]
         L.lbib_get_markers.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.lbib_get_markers_async.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.lbib_step_markers.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
         L.lbib_get_body.argtypes = [vp, C.c_int, C.POINTER(lbib_body_state)]
         L.lbib_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.lbib_profile.argtypes = [vp, C.c_int]
@@ -234,6 +236,19 @@ def lbib_get_populations(ctx, f):
 
 def lbib_get_markers(ctx, body, X=None, V=None, F=None):
     return _check(ctx, load().lbib_get_markers(ctx, int(body), _ptr(X)[0], _ptr(V)[0], _ptr(F)[0]))
+
+
+def lbib_get_markers_async(ctx, body, X=None, V=None, F=None):
+    """Queues the copies (host arrays or page-locked CPU tensors; read them
+    after a synchronisation)."""
+    return _check(ctx, load().lbib_get_markers_async(ctx, int(body), _ptr(X)[0], _ptr(V)[0], _ptr(F)[0]))
+
+
+def lbib_step_markers(ctx, nsteps, body, X=None, V=None, F=None):
+    """nsteps steps, the markers of each queued for copying into X[k], V[k],
+    F[k] (arrays of shape (nsteps, nv, 3); read them after a
+    synchronisation)."""
+    return _check(ctx, load().lbib_step_markers(ctx, int(nsteps), int(body), _ptr(X)[0], _ptr(V)[0], _ptr(F)[0]))
 
 
 def lbib_get_body(ctx, body):

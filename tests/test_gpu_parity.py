@@ -429,6 +429,58 @@ def test_checkpoint_resume_continues_the_run(lbib):
         ctx.close()
 
 
+def test_async_marker_copies_are_ordered_on_the_stream(lbib):
+    """lbib_get_markers_async queued after step 3 returns the markers of
+    step 3 although two more steps are queued before the synchronisation
+    (page-locked and pageable host arrays): the values a synchronous read
+    gave at step 3."""
+    case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
+                                precision=W.PREC_FP64)
+    nv = case.bodies[0].verts.shape[0]
+    ctx = lbib.Context.from_case(case)
+    ctx.step(3)
+    X3, V3, F3 = ctx.markers(0)
+    pinned = [torch.empty((nv, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    lbib.lbib_get_markers_async(ctx.h, 0, *pinned)
+    pageable = [np.full((nv, 3), np.nan) for _ in range(3)]
+    lbib.lbib_get_markers_async(ctx.h, 0, *pageable)
+    ctx.step(2)
+    lbib.lbib_sync(ctx.h)
+    for got in (pinned, pageable):
+        for a, b in zip(got, (X3, V3, F3)):
+            assert np.array_equal(np.asarray(a), b)
+    assert not np.array_equal(ctx.markers(0)[0], X3)  # the context went on to step 5
+    with pytest.raises(lbib.LbibError) as ei:
+        lbib.lbib_get_markers_async(ctx.h, 1, *pageable)
+    assert ei.value.code == lbib.LBIB_EINVAL
+    ctx.close()
+
+
+def test_recorded_trajectory_matches_step_by_step_reads(lbib):
+    """lbib_step_markers: five steps with every step's markers queued into a
+    host ring, against a context read synchronously after each step (the
+    two differ only in the order of the atomic spreading sums)."""
+    case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
+                                precision=W.PREC_FP64)
+    nv = case.bodies[0].verts.shape[0]
+    ref = lbib.Context.from_case(case)
+    want = []
+    for k in range(5):
+        ref.step(1)
+        want.append(ref.markers(0))
+    ref.close()
+    ctx = lbib.Context.from_case(case)
+    X = torch.empty((5, nv, 3), dtype=torch.float64, pin_memory=True)
+    F = np.full((5, nv, 3), np.nan)
+    lbib.lbib_step_markers(ctx.h, 5, 0, X, None, F)
+    lbib.lbib_sync(ctx.h)
+    for k in range(5):
+        assert rel(X[k].numpy(), want[k][0]) < 1e-13
+        assert np.abs(F[k] - want[k][2]).max() < 1e-10 * max(np.abs(want[k][2]).max(), 1e-3)
+    assert ctx.counters()[0] == 5
+    ctx.close()
+
+
 def test_zero_steps_and_empty_lattice(lbib):
     case = W.case_empty(n=(5, 4, 3), precision=W.PREC_FP64, seed=7)
     ctx = lbib.Context.from_case(case)
