@@ -101,7 +101,7 @@ typedef struct {
                               * triangles' area; 1: the IB markers are the triangle centroids (as
                               * printed in Sec. 2.3), each carrying its triangle's area, the vertices
                               * moving with the area-weighted mean of their triangles' centroid
-                              * velocities.  A batch (lbib_batch_create) refuses such bodies */
+                              * velocities */
 } lbib_body_params;
 
 typedef struct {
@@ -267,9 +267,8 @@ int lbib_device_bytes(void *ctx, size_t *bytes);
 /* Creates a batch of n contexts (same precision; each context in at most
  * one live batch).  stream: cudaStream_t of the batch, or NULL for a
  * library-owned one.  Waits for the contexts' queued work.  out receives
- * the batch.  LBIB_EINVAL for mixed precisions, repeated or NULL contexts,
- * or bodies with centroid markers; the message is
- * lbib_batch_last_error(NULL). */
+ * the batch.  LBIB_EINVAL for mixed precisions, repeated or NULL contexts;
+ * the message is lbib_batch_last_error(NULL). */
 int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out);
 
 /* Advances every context of the batch by nsteps (asynchronously on the
@@ -359,9 +358,7 @@ void lbib_request_destroy(void *req);
 /* Starts a server on the current device with its own stream and worker
  * thread. */
 int lbib_serve_create(const lbib_serve_params *sp, void **server);
-/* Queues a request (the server takes ownership); id receives its ticket.
- * A batched server fails a request with centroid-marker bodies at once
- * (state LBIB_REQ_FAILED, error LBIB_EINVAL): batches refuse them. */
+/* Queues a request (the server takes ownership); id receives its ticket. */
 int lbib_serve_submit(void *server, void *req, long long *id);
 /* Waits until the request is done or failed (timeout_s < 0: no limit);
  * state receives LBIB_REQ_*.  Returns LBIB_ETIMEOUT if still running, the

@@ -1035,14 +1035,13 @@ __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R 
 // acceleration of the triangle's vertices, which the structure kernel left
 // as their Lagrangian force), F_l = U_b - U spread with c_l = A_t.
 template <typename R>
-__global__ void __launch_bounds__(256) k_centroid_spread(Lattice L, BodyView B, R *__restrict__ force,
-                                                         uint32_t *__restrict__ stamp,
-                                                         const uint32_t *__restrict__ dstep) {
+__device__ __forceinline__ void centroid_body(const Lattice &L, const BodyView &B, R *__restrict__ force,
+                                              uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep,
+                                              const int vb) {
     const uint32_t step = *dstep;
     __shared__ R s_A[8];
     __shared__ R s_Fl[8][3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int vb = blockIdx.x;
     const int t0 = vb * 8, t = t0 + warp;
     int snode = 0;
     R sphi = R(0);
@@ -1075,6 +1074,13 @@ __global__ void __launch_bounds__(256) k_centroid_spread(Lattice L, BodyView B, 
     }
     __syncthreads();
     if (t < B.nt) spread_node<R>(L, lane, snode, s_A[warp] * sphi, s_Fl[warp], force, stamp, step);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_centroid_spread(Lattice L, BodyView B, R *__restrict__ force,
+                                                         uint32_t *__restrict__ stamp,
+                                                         const uint32_t *__restrict__ dstep) {
+    centroid_body<R>(L, B, force, stamp, dstep, blockIdx.x);
 }
 
 // ---- batch kernels: the bodies of all lattices of a batch per launch ----
@@ -1133,6 +1139,17 @@ __global__ void __launch_bounds__(256) kb_rigid_markers(BatchTables T, int phase
     rigid_markers_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.rm_pre + m));
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) kb_centroid_spread(BatchTables T, int phase) {
+    __shared__ Lattice L;
+    __shared__ BodyRef br;
+    const int m = __ldg(T.cen_blk + blockIdx.x);
+    stage_shared(br, T.body + phase * T.nb + __ldg(T.cen_id + m));
+    stage_shared(L, T.lat + br.lat);
+    const LatRef &F = T.ref[phase * T.nl + br.lat];
+    centroid_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.cen_pre + m));
+}
+
 template <typename S, typename R>
 static cudaError_t batch_ib_t(const BatchTables &T, const BatchGrid &G, int phase, cudaStream_t s) {
     if (G.mom > 0) kb_moments<S, R><<<G.mom, 256, 0, s>>>(T, phase);
@@ -1140,6 +1157,7 @@ static cudaError_t batch_ib_t(const BatchTables &T, const BatchGrid &G, int phas
     if (G.memb > 0) kb_membrane<R><<<G.memb, 256, 0, s>>>(T, phase);
     if (G.rf > 0) kb_rigid_forces<R><<<G.rf, 256, 0, s>>>(T, phase);
     if (G.rm > 0) kb_rigid_markers<R><<<G.rm, 256, 0, s>>>(T, phase);
+    if (G.cen > 0) kb_centroid_spread<R><<<G.cen, 256, 0, s>>>(T, phase);  // after the structure kernels
     return cudaGetLastError();
 }
 

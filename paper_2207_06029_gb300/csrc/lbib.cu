@@ -1478,7 +1478,8 @@ int batch_build(Batch *b) {
             r.parity = (int)((c->steps + k) & 1);
         }
     }
-    std::vector<int> mom_pre(1, 0), mls_pre(1, 0), memb_id, memb_pre(1, 0), rigid_id, rf_pre(1, 0), rm_pre(1, 0);
+    std::vector<int> mom_pre(1, 0), mls_pre(1, 0), memb_id, memb_pre(1, 0), rigid_id, rf_pre(1, 0), rm_pre(1, 0),
+        cen_id, cen_pre(1, 0);
     for (int q = 0; q < nb; ++q) {
         Ctx *c = b->ctx[bodies[q].first];
         DevBody &d = c->bodies[bodies[q].second];
@@ -1504,6 +1505,10 @@ int batch_build(Batch *b) {
             memb_id.push_back(q);
             memb_pre.push_back(memb_pre.back() + (d.nv + 7) / 8);
         }
+        if (d.p.centroid_markers) {
+            cen_id.push_back(q);
+            cen_pre.push_back(cen_pre.back() + (d.nt + 7) / 8);
+        }
     }
     // sweep slots: lattices in launch order (0: as given, 1: largest first)
     std::vector<int> order(nl);
@@ -1524,7 +1529,7 @@ int batch_build(Batch *b) {
     };
     const std::vector<int> sweep_blk = blocks_of(sweep_pre), mom_blk = blocks_of(mom_pre),
                            mls_blk = blocks_of(mls_pre), memb_blk = blocks_of(memb_pre), rf_blk = blocks_of(rf_pre),
-                           rm_blk = blocks_of(rm_pre);
+                           rm_blk = blocks_of(rm_pre), cen_blk = blocks_of(cen_pre);
     // one device block for all tables
     size_t off = 0;
     auto place = [&](size_t bytes) {
@@ -1540,7 +1545,9 @@ int batch_build(Batch *b) {
                  o_rf = place(sizeof(int) * rf_pre.size()), o_rm = place(sizeof(int) * rm_pre.size()),
                  o_bs = place(sizeof(int) * sweep_blk.size()), o_bmo = place(sizeof(int) * mom_blk.size()),
                  o_bml = place(sizeof(int) * mls_blk.size()), o_bme = place(sizeof(int) * memb_blk.size()),
-                 o_brf = place(sizeof(int) * rf_blk.size()), o_brm = place(sizeof(int) * rm_blk.size());
+                 o_brf = place(sizeof(int) * rf_blk.size()), o_brm = place(sizeof(int) * rm_blk.size()),
+                 o_cid = place(sizeof(int) * cen_id.size()), o_cpre = place(sizeof(int) * cen_pre.size()),
+                 o_bce = place(sizeof(int) * cen_blk.size());
     cudaError_t e = cudaMalloc(&b->dmem, off);
     if (e != cudaSuccess) {
         b->dmem = nullptr;
@@ -1568,6 +1575,9 @@ int batch_build(Batch *b) {
     put(o_bme, memb_blk.data(), sizeof(int) * memb_blk.size());
     put(o_brf, rf_blk.data(), sizeof(int) * rf_blk.size());
     put(o_brm, rm_blk.data(), sizeof(int) * rm_blk.size());
+    put(o_cid, cen_id.data(), sizeof(int) * cen_id.size());
+    put(o_cpre, cen_pre.data(), sizeof(int) * cen_pre.size());
+    put(o_bce, cen_blk.data(), sizeof(int) * cen_blk.size());
     e = cudaMemcpy(b->dmem, host.data(), off, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bcuda(b, e, "batch tables upload");
     unsigned char *d = static_cast<unsigned char *>(b->dmem);
@@ -1576,6 +1586,7 @@ int batch_build(Batch *b) {
     T.nb = nb;
     T.nmemb = (int)memb_id.size();
     T.nrigid = (int)rigid_id.size();
+    T.ncen = (int)cen_id.size();
     T.lat = reinterpret_cast<const Lattice *>(d + o_lat);
     T.ref = reinterpret_cast<const LatRef *>(d + o_ref);
     T.body = reinterpret_cast<const BodyRef *>(d + o_body);
@@ -1594,9 +1605,13 @@ int batch_build(Batch *b) {
     T.memb_blk = reinterpret_cast<const int *>(d + o_bme);
     T.rf_blk = reinterpret_cast<const int *>(d + o_brf);
     T.rm_blk = reinterpret_cast<const int *>(d + o_brm);
+    T.cen_id = reinterpret_cast<const int *>(d + o_cid);
+    T.cen_pre = reinterpret_cast<const int *>(d + o_cpre);
+    T.cen_blk = reinterpret_cast<const int *>(d + o_bce);
     T.sweep_threads = b->sweep_threads;
     T.sweep_cpt = b->sweep_cpt;
-    b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back()};
+    b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back(),
+                     cen_pre.back()};
     b->lat_h = lat;
     b->ref_h = ref;
     b->order_h = order;
@@ -1631,7 +1646,7 @@ int batch_enqueue(Batch *b, int phase, bool store, cudaStream_t st) {
 
 int batch_launches_per_step(const Batch *b) {
     int n = 0;
-    for (int v : {b->G.mom, b->G.mls, b->G.memb, b->G.rf, b->G.rm}) n += v > 0;
+    for (int v : {b->G.mom, b->G.mls, b->G.memb, b->G.rf, b->G.rm, b->G.cen}) n += v > 0;
     return n + (b->sweep_split ? (int)b->lat_h.size() : (b->G.sweep > 0));
 }
 
@@ -1704,11 +1719,6 @@ int lbib_batch_create(void *const *ctxs, int n, void *stream, void **out) {
             delete b;
             return bfail(nullptr, LBIB_EINVAL, "the contexts of a batch share one precision");
         }
-        for (const DevBody &db : c->bodies)
-            if (db.p.centroid_markers) {
-                delete b;
-                return bfail(nullptr, LBIB_EINVAL, "bodies with centroid markers are stepped by lbib_step only");
-            }
         b->prec = c->prec;
         b->ctx.push_back(c);
     }

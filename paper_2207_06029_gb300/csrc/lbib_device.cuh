@@ -229,7 +229,7 @@ struct BodyRef {
 // over its items by prefix sums of per-item block counts; *_blk maps each
 // block to its item directly (one cached load instead of a search).
 struct BatchTables {
-    int nl, nb, nmemb, nrigid;
+    int nl, nb, nmemb, nrigid, ncen;
     const Lattice *lat;    // [nl]
     const LatRef *ref;     // [6 nl]: phase-major
     const BodyRef *body;   // [6 nb]: phase-major
@@ -242,7 +242,9 @@ struct BatchTables {
     const int *rigid_id;   // [nrigid] rigid bodies
     const int *rf_pre;     // [nrigid + 1] triangle blocks of the force reduction
     const int *rm_pre;     // [nrigid + 1] blocks of 8 marker warps
-    const int *sweep_blk, *mom_blk, *mls_blk, *memb_blk, *rf_blk, *rm_blk;  // item of each block
+    const int *cen_id;     // [ncen] bodies with centroid markers
+    const int *cen_pre;    // [ncen + 1] blocks of 8 triangle warps
+    const int *sweep_blk, *mom_blk, *mls_blk, *memb_blk, *rf_blk, *rm_blk, *cen_blk;  // item of each block
     int sweep_threads;     // threads per sweep block
     int sweep_cpt;         // cells per sweep thread (blocks per lattice = cells / (threads * cpt))
 };

@@ -62,7 +62,7 @@ cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *fo
 
 // batches (sweep.cu and ib.cu); grid sizes are the totals of the prefix tables
 struct BatchGrid {
-    int sweep, mom, mls, memb, rf, rm;
+    int sweep, mom, mls, memb, rf, rm, cen;
 };
 cudaError_t launch_batch_ib(int prec, const BatchTables &T, const BatchGrid &G, int phase, cudaStream_t s);
 cudaError_t launch_batch_sweep(int prec, const BatchTables &T, const BatchGrid &G, int phase, int store_fields,

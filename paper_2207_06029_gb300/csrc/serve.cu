@@ -348,16 +348,6 @@ int lbib_serve_submit(void *h, void *req, long long *id) {
     r->t_submit = Clock::now();
     r->state = LBIB_REQ_QUEUED;
     s->all[r->id] = r;
-    bool batchable = true;
-    for (const ReqBody &b : r->bodies) batchable = batchable && !b.bp.centroid_markers;
-    if (s->sp.mode == LBIB_SERVE_BATCHED && !batchable) {
-        // a batch refuses centroid-marker bodies: fail this run alone, now
-        r->t_admit = r->t_submit;
-        finish(s, r, LBIB_EINVAL, "bodies with centroid markers are served in plain mode only");
-        s->cv_done.notify_all();
-        if (id) *id = r->id;
-        return LBIB_OK;
-    }
     s->queue.push_back(r);
     if (id) *id = r->id;
     s->cv_work.notify_one();

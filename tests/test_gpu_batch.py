@@ -219,13 +219,25 @@ def test_batch_rejects_mixed_precisions(lbib):
     b.close()
 
 
-def test_batch_refuses_centroid_marker_bodies(lbib):
-    case = mixed_cases(W.PREC_FP32)[0]
-    case.bodies[0].centroid_markers = 1
-    ctxs = [lbib.Context.from_case(case), lbib.Context.from_case(mixed_cases(W.PREC_FP32)[1])]
-    with pytest.raises(lbib.LbibError) as ei:
-        lbib.Batch(ctxs)
-    assert ei.value.code == lbib.LBIB_EINVAL
-    ctxs[0].step(2)  # still steps alone
+def test_batch_with_centroid_marker_bodies_equals_contexts_alone(lbib):
+    """Bodies with centroid IB markers (a capsule in shear, a settling sphere
+    with the momentum-exchange force) batched with a vertex-marker body:
+    the centroid spreading kernel of the batch computes what each context
+    computes alone (FP64, 1e-13)."""
+    cases = mixed_cases(W.PREC_FP64)[:3]
+    cases[0].bodies[0].centroid_markers = 1
+    cases[1].bodies[0].centroid_markers = 1
+    cases[1].bodies[0].rigid_force = 1
+    alone = run_alone(lbib, cases, 13)
+    ctxs = [lbib.Context.from_case(c) for c in cases]
+    batch = lbib.Batch(ctxs)
+    batch.step(13)
+    batch.sync()
+    for ctx, case, a in zip(ctxs, cases, alone):
+        st = state(ctx, case)
+        assert rel(st["f"], a["f"]) < 1e-13
+        for x, y in zip(st["X"], a["X"]):
+            assert rel(x, y) < 1e-13
+    batch.close()
     for ctx in ctxs:
         ctx.close()

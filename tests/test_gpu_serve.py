@@ -146,27 +146,23 @@ def test_taking_and_destroying_results_while_the_server_runs(lbib):
     assert stats["runs_done"] == len(ids) and stats["runs_failed"] == 0
 
 
-def test_centroid_marker_runs_fail_alone_in_batched_mode_and_run_in_plain_mode(lbib):
-    """A batch refuses centroid-marker bodies: a batched server fails such a
-    request at submission without touching the others; a plain server runs
-    it and returns what the context computes alone."""
+def test_centroid_marker_runs_are_served_batched_and_plain(lbib):
+    """A run whose capsule has centroid IB markers, served beside other runs
+    in batched mode and alone in plain mode, returns what it computes
+    alone."""
     reqs = requests(W.PREC_FP64)[:2]
     odd = W.case_capsule_shear(n=26, tau=0.7, shear_rate=1e-3, radius=4.5, level=3, Ca=0.1, Eb=0.005, kv=1.0,
                                precision=W.PREC_FP64)
     odd.bodies[0].centroid_markers = 1
-    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=16, max_active=8)
-    ids = [lbib.lbib_serve_submit(server, lbib.request_from_case(c, s)) for c, s in reqs]
-    bad = lbib.lbib_serve_submit(server, lbib.request_from_case(odd, 20))
-    rc, state = lbib.lbib_serve_wait(server, bad, WAIT_S)
-    assert rc == lbib.LBIB_EINVAL and state == lbib.LBIB_REQ_FAILED
-    for rid, (case, _) in zip(ids, reqs):
-        take(lbib, server, rid, case)
-    stats = lbib.lbib_serve_stats(server)
-    lbib.lbib_serve_destroy(server)
-    assert stats["runs_done"] == 2 and stats["runs_failed"] == 1
-    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=7, max_active=8, mode=lbib.LBIB_SERVE_PLAIN)
-    rid = lbib.lbib_serve_submit(server, lbib.request_from_case(odd, 20))
-    (f, X, nsteps), _ = take(lbib, server, rid, odd)
-    lbib.lbib_serve_destroy(server)
     f0, X0 = alone(lbib, odd, 20)
-    assert nsteps == 20 and rel(f, f0) < 1e-13 and rel(X[0], X0[0]) < 1e-13
+    for mode in (lbib.LBIB_SERVE_BATCHED, lbib.LBIB_SERVE_PLAIN):
+        server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=7, max_active=8, mode=mode)
+        ids = [lbib.lbib_serve_submit(server, lbib.request_from_case(c, s)) for c, s in reqs]
+        rid = lbib.lbib_serve_submit(server, lbib.request_from_case(odd, 20))
+        (f, X, nsteps), _ = take(lbib, server, rid, odd)
+        for i, (case, _) in zip(ids, reqs):
+            take(lbib, server, i, case)
+        stats = lbib.lbib_serve_stats(server)
+        lbib.lbib_serve_destroy(server)
+        assert stats["runs_done"] == 3 and stats["runs_failed"] == 0
+        assert nsteps == 20 and rel(f, f0) < 1e-13 and rel(X[0], X0[0]) < 1e-13
