@@ -310,6 +310,50 @@ def device_fields(torch, case):
     return (torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u.reshape(-1))).cuda())
 
 
+def large_sweep_leg(args):
+    """The same whole-lattice sweep measured the same way (overlap off, L2
+    written and read clean before each step, CUDA events on the stream) on
+    the 160x160x480 settling lattice, where the launch ramp is a small part
+    of the kernel: the sweep's roofline on a lattice large enough to stream."""
+    import torch
+
+    from paper_2207_06029_gb300 import lbib
+    stream = torch.cuda.current_stream()
+    case = workload_case("settling")
+    alloc_fn, free_fn, live = torch_allocator(torch)
+    params = lbib.make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
+                              stream=stream.cuda_stream)
+    params.alloc, params.free = alloc_fn, free_fn
+    h = lbib.lbib_create(params)
+    rho, u = device_fields(torch, case)
+    lbib.lbib_set_fields(h, rho, u)
+    b = case.bodies[0]
+    lbib.lbib_add_body(h, b.verts, b.tris, lbib.make_body_params(**b.kwargs()))
+    lbib.lbib_step(h, 3)
+    lbib.lbib_set_output(h, -1)
+    lbib.lbib_set_overlap(h, 0)
+    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    acc = torch.empty((), dtype=torch.float32, device="cuda")
+    lbib.lbib_profile(h, 1)
+    lbib.lbib_get_profile(h)
+    n = 10
+    for _ in range(n):
+        flush_w.zero_()
+        torch.sum(flush_r, dim=0, out=acc)
+        lbib.lbib_step(h, 1)
+    _, _, sweep_ms, _, nprof = lbib.lbib_get_profile(h)
+    lbib.lbib_profile(h, 0)
+    lbib.lbib_destroy(h)
+    live.clear()
+    us = 1e3 * sweep_ms / max(nprof, 1)
+    peak, kind = hbm_peak()
+    achieved = 152.0 * case.ncell / (us * 1e-6) / 1e9
+    return {"workload": "settling sphere 160x160x480 (12.3 M cells), fp32", "kernel": "k_sweep<float,float>",
+            "sweep_us": us, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": kind, "launches_timed": nprof}
+
+
 def batch_leg(args):
     """64 capsule-in-shear cases of uneven cubic lattices (48^3..112^3)
     advanced together by the batch launches, six steps per graph launch."""
@@ -546,6 +590,8 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    if rank == 0 and world == 1 and args.workload != "settling":
+        line["roofline_large_lattice"] = large_sweep_leg(args)
     if args.batch and rank == 0 and world == 1:
         line["batch"] = batch_leg(args)
     if args.serve and rank == 0 and world == 1:
