@@ -67,7 +67,6 @@ struct Ctx {
     bool split_sweep = true;
     bool own_stream = false;
     std::vector<DevBody> bodies;
-    bool sort_points = true;     // MLS points in cell order (marker binning)
     uint32_t *d_step = nullptr;  // device step counter (tile flags of the IB force)
     uint32_t step_host = 0;      // host mirror of *d_step
     uint32_t *d_sr = nullptr;    // two-word seed counter of the stochastic rounding (bfloat16 storage)
@@ -274,7 +273,7 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.Flc = b.Flc;
     v.phi = b.phi;
     v.node = b.node;
-    v.perm = c->sort_points ? b.perm : nullptr;
+    v.perm = b.perm;
     v.tri = b.tri;
     v.tri_geo = b.tri_geo;
     v.tri_vol = b.tri_vol;
