@@ -70,10 +70,13 @@ def sweep_source_hash():
     return hashlib.sha256((sweep + dev).encode()).hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current sweep source; else None."""
-    path = os.path.join(ROOT, "profiles", "sweep_fp32_capsule96.md")
+SWEEP_PROFILES = {"capsule96": "sweep_fp32_capsule96.md", "settling": "sweep_fp32_settling.md"}
+
+
+def ncu_traffic(workload="capsule96"):
+    """DRAM bytes per sweep launch of the workload from its committed ncu
+    summary, if that was taken on the current sweep source; else None."""
+    path = os.path.join(ROOT, "profiles", SWEEP_PROFILES[workload])
     try:
         txt = open(path).read()
     except OSError:
@@ -351,7 +354,7 @@ def large_sweep_leg(args):
     achieved = 152.0 * case.ncell / (us * 1e-6) / 1e9
     return {"workload": "settling sphere 160x160x480 (12.3 M cells), fp32", "kernel": "k_sweep<float,float>",
             "sweep_us": us, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": kind, "launches_timed": nprof}
+            "traffic": ncu_traffic("settling"), "peak_source": kind, "launches_timed": nprof}
 
 
 def batch_leg(args):
@@ -567,7 +570,7 @@ def main():
                                  "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
                    "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
                      "kernel": ("k_sweep_tile<float,float> (shared-memory row tiles, 128-bit loads/stores)"
                                 if r["tuned"][3] else "k_sweep<float,float>"),
                      "peak_source": peak_kind, "sweep_us": r["iso_sweep_us"],
