@@ -38,6 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 WORKLOADS = {
     "capsule96": "capsule_shear_96^3_Ca0.05_fp32",
     "settling": "settling_sphere_160x160x480_fp32",
+    "couette_fp64": "couette_rigid_sphere_32^3_fp64",
+    "capsule96_fp64": "capsule_shear_96^3_Ca0.05_fp64",
 }
 
 
@@ -45,8 +47,11 @@ def workload_case(name="capsule96"):
     from paper_2207_06029_gb300 import workloads as W
     if name == "settling":
         return W.case_settling(precision=W.PREC_FP32)
+    if name == "couette_fp64":
+        return W.case_couette_sphere(precision=W.PREC_FP64)
+    prec = W.PREC_FP64 if name == "capsule96_fp64" else W.PREC_FP32
     return W.case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=0.05, Eb=0.01, kv=1.0,
-                                precision=W.PREC_FP32)
+                                precision=prec)
 
 
 def hbm_peak():
@@ -70,12 +75,30 @@ def sweep_source_hash():
     return hashlib.sha256((sweep + dev).encode()).hexdigest()[:16]
 
 
-SWEEP_PROFILES = {"capsule96": "sweep_fp32_capsule96.md", "settling": "sweep_fp32_settling.md"}
+SWEEP_PROFILES = {"capsule96": "sweep_fp32_capsule96.md", "settling": "sweep_fp32_settling.md",
+                  "couette_fp64": "sweep_fp64_capsule96.md", "capsule96_fp64": "sweep_fp64_capsule96.md"}
+
+
+def profile_figure(workload, key):
+    """A figure (`key: value`) of the workload's committed ncu summary, if
+    that was taken on the current sweep source; else None."""
+    path = os.path.join(ROOT, "profiles", SWEEP_PROFILES[workload])
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(key + r":\s*([0-9.eE+]+)", txt)
+    s = re.search(r"sweep_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != sweep_source_hash():
+        return None
+    return float(m.group(1))
 
 
 def ncu_traffic(workload="capsule96"):
     """DRAM bytes per sweep launch of the workload from its committed ncu
     summary, if that was taken on the current sweep source; else None."""
+    if workload.endswith("fp64"):
+        return None  # the FP64 summary records the arithmetic of the sweep, not a launch of this lattice
     path = os.path.join(ROOT, "profiles", SWEEP_PROFILES[workload])
     try:
         txt = open(path).read()
@@ -556,30 +579,33 @@ def main():
     ms = ms_all[0]
     value = job_mlups(r["ncell"], args.steps, world, ms)
     peak, peak_kind = hbm_peak()
-    bytes_per_launch = 152.0 * r["ncell"]  # 19 reads + 19 writes of 4 bytes per cell
+    fp64 = args.workload.endswith("fp64")
+    bytes_per_cell = 304.0 if fp64 else 152.0  # 19 reads + 19 writes of 8 or 4 bytes per cell
+    bytes_per_launch = bytes_per_cell * r["ncell"]
     achieved = bytes_per_launch / (r["iso_sweep_us"] * 1e-6) / 1e9
     concurrent_s = r["sweep_ms"] * 1e-3 / max(r["nprof"], 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "fp32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
                    "fields_output": "off in the timed loop (e2e reads them)",
                    "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
                                  "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
-                   "populations": "fp32 deviations f_i - w_i; markers and MLS solve fp64"},
+                   "populations": ("fp64 deviations f_i - w_i, fp64 arithmetic" if fp64 else
+                                   "fp32 deviations f_i - w_i; markers and MLS solve fp64")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
-                     "kernel": ("k_sweep_tile<float,float> (shared-memory row tiles, 128-bit loads/stores)"
-                                if r["tuned"][3] else "k_sweep<float,float>"),
+                     "kernel": ("k_sweep_tile<{0},{0}> (shared-memory row tiles, 128-bit loads/stores)"
+                                if r["tuned"][3] else "k_sweep<{0},{0}>").format("double" if fp64 else "float"),
                      "peak_source": peak_kind, "sweep_us": r["iso_sweep_us"],
                      "sweep_in_step_us": 1e6 * concurrent_s,
                      "sweep_in_step_frac": bytes_per_launch / concurrent_s / 1e9 / peak,
                      "mls_us_per_step": 1e3 * r["mls_ms"] / max(r["nprof"], 1),
                      "structure_us_per_step": 1e3 * r["struct_ms"] / max(r["nprof"], 1),
                      "step_us_per_step": 1e3 * r["step_ms"] / max(r["nprof"], 1),
-                     "note": "achieved = 152 B/cell x cells / the mean CUDA-event duration of the whole-lattice "
+                     "note": f"achieved = {bytes_per_cell:.0f} B/cell x cells / the mean CUDA-event duration of the whole-lattice "
                              "k_sweep launch (one per step, overlap off, L2 flushed before each step); "
                              "sweep_in_step_* and the stage times come from a profiled loop of the tuned step, "
                              "where the sweep runs as two launches, the far field concurrently with the IB "
@@ -593,7 +619,31 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
-    if rank == 0 and world == 1 and args.workload != "settling":
+    if fp64:
+        # the FP64 sweep issues its arithmetic on GB300's narrow FP64 pipe:
+        # its roofline is the measured FP64 FMA rate, the FP64 operations per
+        # cell counted by ncu (committed summary) times the cells per launch
+        flop_cell = profile_figure(args.workload, "fp64_flop_per_cell")
+        inst_cell = profile_figure(args.workload, "fp64_inst_per_cell")
+        from paper_2207_06029_gb300 import lbib
+        fma64 = lbib.lbib_measure_fma(True)
+        # the pipe issues one FP64 instruction per slot: 2 flops as an FMA,
+        # 1 as an add or a multiply; the peak for the sweep's mix
+        peak = fma64 / 1e12 * (flop_cell / inst_cell / 2.0 if flop_cell and inst_cell else 1.0)
+        hbm = line["roofline"]
+        line["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                            "peak_source": "measured FP64 FMA rate (lbib_measure_fma) x the sweep's flop per "
+                                           "FP64 instruction / 2 (ncu instruction counts, committed summary)",
+                            "fma_tflops": fma64 / 1e12,
+                            "flop_per_cell": flop_cell, "kernel": hbm["kernel"], "sweep_us": r["iso_sweep_us"],
+                            "achieved": (flop_cell * r["ncell"] / (r["iso_sweep_us"] * 1e-6) / 1e12
+                                         if flop_cell else None),
+                            "traffic": None, "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
+        for k in ("sweep_in_step_us", "mls_us_per_step", "structure_us_per_step", "step_us_per_step"):
+            line["roofline"][k] = hbm[k]
+        line["roofline"]["frac"] = (line["roofline"]["achieved"] / line["roofline"]["peak"]
+                                    if flop_cell else None)
+    if rank == 0 and world == 1 and args.workload == "capsule96":
         line["roofline_large_lattice"] = large_sweep_leg(args)
     if args.batch and rank == 0 and world == 1:
         line["batch"] = batch_leg(args)

@@ -405,6 +405,15 @@ void lbib_serve_destroy(void *server);
  * no cudaMalloc, cudaFree or allocating library routine. */
 int lbib_mesh_measures_noalloc(const double *X, int nv, const int *tris, int nt, double *out, void *stream);
 
+/* Fused multiply-add throughput of the current device in flops/s (two per
+ * FMA), FP64 (fp64 = 1) or FP32 (0), measured by a short kernel of
+ * independent FMA chains (a few blocks per SM, about 10 ms): the arithmetic
+ * peak for the roofline of FP64 kernels, which GB300 issues at a small
+ * fraction of its FP32 rate.  Allocates and frees a few bytes; synchronises
+ * its own stream.  LBIB_EINVAL for a NULL output, LBIB_ECUDA on a CUDA
+ * error.  Not part of the method (a measurement aid). */
+int lbib_measure_fma(int fp64, double *flops_per_s);
+
 /* Releases all device and host memory of the context (NULL is a no-op). */
 void lbib_destroy(void *ctx);
 

@@ -86,7 +86,7 @@ EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_b
            "lbib_batch_destroy", "lbib_batch_last_error",
            "lbib_request_create", "lbib_request_add_body", "lbib_request_destroy", "lbib_serve_create",
            "lbib_serve_submit", "lbib_serve_wait", "lbib_serve_take", "lbib_serve_stats", "lbib_serve_destroy",
-           "lbib_destroy",
+           "lbib_measure_fma", "lbib_destroy",
            "lbib_last_error"]
 
 
@@ -112,6 +112,7 @@ def load():
         L.lbib_get_totals.argtypes = [vp, dp]
         L.lbib_get_markers.argtypes = [vp, C.c_int, vp, vp, vp]
         L.lbib_get_markers_async.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.lbib_measure_fma.argtypes = [C.c_int, dp]
         L.lbib_step_markers.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
         L.lbib_get_body.argtypes = [vp, C.c_int, C.POINTER(lbib_body_state)]
         L.lbib_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
@@ -249,6 +250,14 @@ def lbib_step_markers(ctx, nsteps, body, X=None, V=None, F=None):
     F[k] (arrays of shape (nsteps, nv, 3); read them after a
     synchronisation)."""
     return _check(ctx, load().lbib_step_markers(ctx, int(nsteps), int(body), _ptr(X)[0], _ptr(V)[0], _ptr(F)[0]))
+
+
+def lbib_measure_fma(fp64=True):
+    """FMA throughput of the current device in flops/s (a measurement aid)."""
+    out = C.c_double()
+    rc = load().lbib_measure_fma(int(bool(fp64)), C.byref(out))
+    _check(None, rc)
+    return out.value
 
 
 def lbib_get_body(ctx, body):
