@@ -63,3 +63,19 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
     p = lbib.make_params((8, 8, 8), 0.8, precision=7)
     with pytest.raises(lbib.LbibError):
         lbib.lbib_create(p)
+
+
+def test_measure_fma_rejects_a_null_output_without_touching_the_gpu(libpath):
+    from paper_2207_06029_gb300 import lbib
+    import ctypes as C
+    assert lbib.load().lbib_measure_fma(1, C.cast(None, C.POINTER(C.c_double))) == lbib.LBIB_EINVAL
+
+
+@pytest.mark.gpu
+def test_measured_fma_rates_are_positive_and_fp64_is_the_slower(libpath):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_06029_gb300 import lbib
+    f64, f32 = lbib.lbib_measure_fma(True), lbib.lbib_measure_fma(False)
+    assert 0.0 < f64 < f32
