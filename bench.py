@@ -40,16 +40,28 @@ WORKLOADS = {
     "settling": "settling_sphere_160x160x480_fp32",
     "couette_fp64": "couette_rigid_sphere_32^3_fp64",
     "capsule96_fp64": "capsule_shear_96^3_Ca0.05_fp64",
+    "capsule96_fp16": "capsule_shear_96^3_Ca0.05_fp16dev",
+    "capsule96_bf16": "capsule_shear_96^3_Ca0.05_bf16dev",
+    "settling_fp16": "settling_sphere_160x160x480_fp16dev",
+    "settling_bf16": "settling_sphere_160x160x480_bf16dev",
 }
+# storage of the populations per workload suffix: (precision, bytes per value, C++ type)
+STORAGE = {"fp64": ("PREC_FP64", 8, "double"), "fp32": ("PREC_FP32", 4, "float"),
+           "fp16": ("PREC_FP16_DEV", 2, "__half"), "bf16": ("PREC_BF16_DEV", 2, "__nv_bfloat16")}
+
+
+def storage(name):
+    suffix = name.rsplit("_", 1)[-1]
+    return STORAGE[suffix] if suffix in STORAGE else STORAGE["fp32"]
 
 
 def workload_case(name="capsule96"):
     from paper_2207_06029_gb300 import workloads as W
-    if name == "settling":
-        return W.case_settling(precision=W.PREC_FP32)
+    prec = getattr(W, storage(name)[0])
+    if name.startswith("settling"):
+        return W.case_settling(precision=prec)
     if name == "couette_fp64":
         return W.case_couette_sphere(precision=W.PREC_FP64)
-    prec = W.PREC_FP64 if name == "capsule96_fp64" else W.PREC_FP32
     return W.case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=0.05, Eb=0.01, kv=1.0,
                                 precision=prec)
 
@@ -97,8 +109,8 @@ def profile_figure(workload, key):
 def ncu_traffic(workload="capsule96"):
     """DRAM bytes per sweep launch of the workload from its committed ncu
     summary, if that was taken on the current sweep source; else None."""
-    if workload.endswith("fp64"):
-        return None  # the FP64 summary records the arithmetic of the sweep, not a launch of this lattice
+    if workload not in ("capsule96", "settling"):
+        return None  # summaries of DRAM traffic exist for the FP32 lattices
     path = os.path.join(ROOT, "profiles", SWEEP_PROFILES[workload])
     try:
         txt = open(path).read()
@@ -580,25 +592,26 @@ def main():
     value = job_mlups(r["ncell"], args.steps, world, ms)
     peak, peak_kind = hbm_peak()
     fp64 = args.workload.endswith("fp64")
-    bytes_per_cell = 304.0 if fp64 else 152.0  # 19 reads + 19 writes of 8 or 4 bytes per cell
+    _, elem, ctype = storage(args.workload)
+    bytes_per_cell = 38.0 * elem  # 19 reads + 19 writes of one stored value per cell
     bytes_per_launch = bytes_per_cell * r["ncell"]
     achieved = bytes_per_launch / (r["iso_sweep_us"] * 1e-6) / 1e9
     concurrent_s = r["sweep_ms"] * 1e-3 / max(r["nprof"], 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if fp64 else "fp32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {8: "f64", 4: "fp32", 2: "fp32 (fp16/bf16 storage)"}[elem], "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
                    "fields_output": "off in the timed loop (e2e reads them)",
                    "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
                                  "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
                    "populations": ("fp64 deviations f_i - w_i, fp64 arithmetic" if fp64 else
-                                   "fp32 deviations f_i - w_i; markers and MLS solve fp64")},
+                                   f"{ctype} deviations f_i - w_i, fp32 arithmetic; markers and MLS solve fp64")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
-                     "kernel": ("k_sweep_tile<{0},{0}> (shared-memory row tiles, 128-bit loads/stores)"
-                                if r["tuned"][3] else "k_sweep<{0},{0}>").format("double" if fp64 else "float"),
+                     "kernel": ("k_sweep_tile<{0},{1}> (shared-memory row tiles, 128-bit loads/stores)"
+                                if r["tuned"][3] else "k_sweep<{0},{1}>").format(ctype, "double" if fp64 else "float"),
                      "peak_source": peak_kind, "sweep_us": r["iso_sweep_us"],
                      "sweep_in_step_us": 1e6 * concurrent_s,
                      "sweep_in_step_frac": bytes_per_launch / concurrent_s / 1e9 / peak,

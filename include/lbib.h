@@ -198,9 +198,9 @@ int lbib_profile(void *ctx, int enable);
 int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
 
 /* Times the step in several launch configurations and keeps the fastest:
- * the sweep kernel and its block shape (the 4-wide FP32 kernel with 128-bit
- * loads and stores where nx is a multiple of 4, or the one-node kernel in
- * several shapes), then (single-body contexts) the overlap of the far-field
+ * the sweep kernel and its block shape (the row-tile kernel with 128-bit
+ * loads and stores where rows are whole 16-byte vectors, or the one-node
+ * kernel in several shapes), then (single-body contexts) the overlap of the far-field
  * sweep with the IB stage.  Each trial runs
  * 1 + 2 * `steps` real time steps, so the simulation advances by about
  * 16 * `steps` steps.  choice (optional, 5 ints) receives block x, block y (0, 0: whole
@@ -210,7 +210,8 @@ int lbib_autotune(void *ctx, int steps, int *choice);
 
 /* Sets the sweep launch configuration (what lbib_autotune chooses):
  * row_tiles = 1 selects the row-tile kernel (x-rows staged in shared memory
- * with 128-bit loads and stores; FP32/FP64 with nx a multiple of 4, else
+ * with 128-bit loads and stores; any precision with rows of whole 16-byte
+ * vectors: nx a multiple of 4 in FP32/FP64, of 8 in FP16/BF16, else
  * ignored), 0 the one-node kernel with blocks of block_x * block_y threads
  * (0, 0: whole x-rows); far_per_sm > 0 runs the far-field sweep (overlap
  * on) with that many resident blocks per SM striding over the lattice, so

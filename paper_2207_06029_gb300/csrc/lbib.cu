@@ -1291,9 +1291,8 @@ int lbib_autotune(void *h, int steps, int *choice) {
     // x-rows of the one-node kernel, then fixed 2D shapes
     const int shapes[][3] = {{0, 0, 0}, {0, 0, 1}, {32, 8, 0}, {64, 4, 0}, {128, 2, 0}, {256, 1, 0}, {32, 4, 0},
                              {64, 2, 0}};
-    const int esz = c->prec == LBIB_FP64 ? 8 : 4;
-    const bool vec_ok = (c->prec == LBIB_FP32 || c->prec == LBIB_FP64) && (c->L.nx & 3) == 0 &&
-                        (c->L.nx * esz) % 16 == 0 &&
+    const int esz = c->prec == LBIB_FP64 ? 8 : c->prec == LBIB_FP32 ? 4 : 2;
+    const bool vec_ok = (c->L.nx & 3) == 0 && (c->L.nx * esz) % 16 == 0 &&
                         19LL * std::max(1, std::min(256 / c->L.nx, c->L.ny)) * c->L.nx * esz <= 160 * 1024 &&
                         c->L.nx <= 512;
     const bool saved_split = c->split_sweep;

@@ -103,10 +103,11 @@ struct Pop<__nv_bfloat16, float> {
     // stochastic rounding: adding 16 uniform random bits below the bfloat16
     // mantissa and truncating rounds the magnitude up with probability equal
     // to the discarded fraction, so the stored value is unbiased
-    __device__ static void st_sr(__nv_bfloat16 *p, float v, uint32_t r) {
+    __device__ static __nv_bfloat16 to_sr(float v, uint32_t r) {
         const uint32_t b = (__float_as_uint(v * kHalfScale) + (r >> 16)) & 0xFFFF0000u;
-        *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
+        return __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
+    __device__ static void st_sr(__nv_bfloat16 *p, float v, uint32_t r) { *p = to_sr(v, r); }
 };
 
 // Random bits for stochastic rounding from a counter: lowbias32 (the

@@ -271,11 +271,13 @@ __device__ __forceinline__ void clamp_box(const Lattice &L, const int *box, int 
     const int n[3] = {L.nx, L.ny, L.nz};
     for (int a = 0; a < 3; ++a) {
         long long l = box[a], h = box[3 + a];
-        if (a == 0 && (L.nx & 3) == 0 && h >= l) {
-            // whole groups of 4 along x, so that the 4-wide sweep never
-            // splits a group between the far-field and the box sweeps
-            l &= ~3LL;  // down to a multiple of 4 (two's complement: also below 0)
-            h |= 3LL;   // up to the last node of its group
+        if (a == 0 && h >= l && (L.nx & 3) == 0) {
+            // whole groups of 8 (or 4) nodes along x, so that the 16-byte
+            // vectors of the row-tile sweep (4 FP32 or 8 FP16/BF16 values)
+            // never straddle the far-field and box sweeps
+            const long long g = (L.nx & 7) == 0 ? 7LL : 3LL;
+            l &= ~g;  // down to a multiple of the group (two's complement: also below 0)
+            h |= g;   // up to the last node of its group
         }
         if (L.bc[a] == kWall) {
             l = l < 0 ? 0 : l;
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
     S *sm = reinterpret_cast<S *>(tile_raw);  // [Q][rows][nx]
     constexpr int V = 16 / sizeof(S);         // nodes per 16-byte vector
     const uint32_t step = stamp ? *dstep : 0u;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) sr[parity ^ 1] = sr[parity] + 1u;
+    const uint32_t seed = sr[parity];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) sr[parity ^ 1] = seed + 1u;
     const int nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny;
     const int z = blockIdx.y, y0 = blockIdx.x * rows;
     const int nrows = min(rows, ny - y0);
@@ -424,8 +427,27 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
     }
     __syncthreads();  // every staged value has been read
     if (mine) {
+        // the rounding of the one-node sweep: bfloat16 rounds stochastically
+        // with the cell's random stream, the values taken in the same order
+        constexpr bool kSR = std::is_same<S, __nv_bfloat16>::value;
+        const long long idx = x + (long long)y * nx + (long long)z * nxy;
+        uint32_t rs = kSR ? (lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u) : 0u;
+        auto put = [&](int i) {
+            S v;
+            if constexpr (kSR) {
+                rs = xorshift32(rs);
+                v = Pop<S, R>::to_sr(g[i], rs);
+            } else {
+                v = Pop<S, R>::to(g[i]);
+            }
+            sm[(i * rows + r) * nx + x] = v;
+        };
+        put(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) sm[(i * rows + r) * nx + x] = Pop<S, R>::to(g[i]);
+        for (int k = 0; k < 9; ++k) {
+            put(pair_rep(k));
+            put(opp(pair_rep(k)));
+        }
     }
     __syncthreads();
     if (grp < G && !(box && in_box(L, lo, ext, sq * V, y0 + sr_, z))) {  // not the box sweep's nodes
@@ -552,7 +574,6 @@ static int tile_rows(const Lattice &L) {
     if (!L.sweep_vec || (L.nx & 3) != 0 || (L.nx * (int)sizeof(S)) % 16 != 0 ||
         (L.stride * (long long)sizeof(S)) % 16 != 0)
         return 0;
-    if (!(std::is_same<S, float>::value || std::is_same<S, double>::value)) return 0;
     int rows = 256 / L.nx;
     if (rows < 1) rows = 1;
     if (rows > L.ny) rows = L.ny;
