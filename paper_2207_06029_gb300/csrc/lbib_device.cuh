@@ -77,6 +77,12 @@ struct Pop<double, double> {
     __device__ static void st(double *p, double v) { __stcs(p, v); }
     __device__ static double from(double v) { return v; }
     __device__ static double to(double v) { return v; }
+    // raw: the stored value itself (the deviation times 2^kScaleLog2)
+    static constexpr int kScaleLog2 = 0;
+    __device__ static double ld_raw(const double *p) { return __ldg(p); }
+    __device__ static void st_raw(double *p, double v) { __stcs(p, v); }
+    __device__ static double from_raw(double v) { return v; }
+    __device__ static double to_raw(double v) { return v; }
 };
 template <>
 struct Pop<float, float> {
@@ -84,6 +90,11 @@ struct Pop<float, float> {
     __device__ static void st(float *p, float v) { __stcs(p, v); }
     __device__ static float from(float v) { return v; }
     __device__ static float to(float v) { return v; }
+    static constexpr int kScaleLog2 = 0;
+    __device__ static float ld_raw(const float *p) { return __ldg(p); }
+    __device__ static void st_raw(float *p, float v) { __stcs(p, v); }
+    __device__ static float from_raw(float v) { return v; }
+    __device__ static float to_raw(float v) { return v; }
 };
 template <>
 struct Pop<__half, float> {
@@ -91,6 +102,11 @@ struct Pop<__half, float> {
     __device__ static void st(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
     __device__ static float from(__half v) { return __half2float(v) * (1.0f / kHalfScale); }
     __device__ static __half to(float v) { return __float2half_rn(v * kHalfScale); }
+    static constexpr int kScaleLog2 = 8;  // kHalfScale = 2^8
+    __device__ static float ld_raw(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static void st_raw(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static float from_raw(__half v) { return __half2float(v); }
+    __device__ static __half to_raw(float v) { return __float2half_rn(v); }
 };
 template <>
 struct Pop<__nv_bfloat16, float> {
@@ -103,10 +119,17 @@ struct Pop<__nv_bfloat16, float> {
     // stochastic rounding: adding 16 uniform random bits below the bfloat16
     // mantissa and truncating rounds the magnitude up with probability equal
     // to the discarded fraction, so the stored value is unbiased
-    __device__ static __nv_bfloat16 to_sr(float v, uint32_t r) {
-        const uint32_t b = (__float_as_uint(v * kHalfScale) + (r >> 16)) & 0xFFFF0000u;
+    static constexpr int kScaleLog2 = 8;  // kHalfScale = 2^8
+    __device__ static float ld_raw(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void st_raw(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static float from_raw(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 to_raw(float v) { return __float2bfloat16_rn(v); }
+    __device__ static __nv_bfloat16 to_sr_raw(float v, uint32_t r) {
+        const uint32_t b = (__float_as_uint(v) + (r >> 16)) & 0xFFFF0000u;
         return __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
+    __device__ static void st_sr_raw(__nv_bfloat16 *p, float v, uint32_t r) { *p = to_sr_raw(v, r); }
+    __device__ static __nv_bfloat16 to_sr(float v, uint32_t r) { return to_sr_raw(v * kHalfScale, r); }
     __device__ static void st_sr(__nv_bfloat16 *p, float v, uint32_t r) { *p = to_sr(v, r); }
 };
 

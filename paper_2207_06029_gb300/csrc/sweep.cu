@@ -88,11 +88,16 @@ __device__ __forceinline__ void wall_corner(R (&g)[Q], unsigned unknown, const R
 // Walls, moments, body force and BGK/Guo collision of node (x, y, z) whose
 // streamed populations are g (Eqs. evoleq, eqfunc, forcing; Zou-He walls);
 // on return g holds the post-collision populations and rho, u the moments
-// of the collision (stored as the macroscopic fields).
-template <typename R>
+// of the collision (stored as the macroscopic fields).  g is in stored
+// units, the deviations times 2^kLog2S (16-bit storage scales them by 2^8):
+// scaling by a power of two commutes with every rounding, so the update runs
+// on the scaled values (the four moments and the equilibrium weights carry
+// the factor) and gives exactly the scaled result.
+template <typename R, int kLog2S = 0>
 __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                              uint32_t step, const Lattice &L, int x, int y, int z, long long idx,
                                              R &rho_o, R &ux_o, R &uy_o, R &uz_o) {
+    constexpr R kS = R(1 << kLog2S), kInvS = R(1) / R(1 << kLog2S);  // exact powers of two
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const long long st = L.stride;
     // walls (faces -x,+x,-y,+y,-z,+z; the index-0 face has inward normal +)
@@ -117,6 +122,9 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
                                     : (s > 0 ? dirmask(2, 1) : dirmask(2, -1)));
     }
     if (nf) {
+        if (kLog2S)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] *= kInvS;
         const int wc = wall_code(code[0], code[1], code[2]);
         R uw[3];
         for (int b = 0; b < 3; ++b) uw[b] = pick<R>(L.uw_d[wc][b], L.uw_f[wc][b]);
@@ -130,6 +138,9 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
         } else {
             wall_corner(g, unknown, uw);
         }
+        if (kLog2S)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] *= kS;
     }
 
     // moments of the streamed populations, over the pairs (i, opp(i))
@@ -142,6 +153,12 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
         if (ex(i)) jx += R(ex(i)) * dif;
         if (ey(i)) jy += R(ey(i)) * dif;
         if (ez(i)) jz += R(ez(i)) * dif;
+    }
+    if (kLog2S) {
+        dr *= kInvS;
+        jx *= kInvS;
+        jy *= kInvS;
+        jz *= kInvS;
     }
     const R rho = R(1) + dr;
 
@@ -174,14 +191,42 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
     // which is g - omega (g - (f^eq - w)) + F_i of Eqs. (evoleq, eqfunc,
     // forcing) regrouped so that each pair (i, opp(i)) shares E and O.
     const R inv = R(1) / rho;
+    const R omega = pick<R>(L.omega_d, L.omega_f);
+    const R om1 = R(1) - omega, ca = R(3) * omega * rho, cb = R(4.5) * omega * rho;
+    if (F0 == R(0) && F1 == R(0) && F2 == R(0)) {
+        // no body force on this node (the common case): the same update with
+        // the Guo terms, which vanish exactly, left out
+        const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+        const R uu = ux * ux + uy * uy + uz * uz;
+        const R A0 = omega * (dr - R(1.5) * rho * uu);
+        g[0] = om1 * g[0] + (wq<R>(0) * kS) * A0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = pair_rep(k), o = opp(i);
+            R eu = R(0);
+            if (ex(i)) eu += R(ex(i)) * ux;
+            if (ey(i)) eu += R(ey(i)) * uy;
+            if (ez(i)) eu += R(ez(i)) * uz;
+            const R w = wq<R>(i) * kS;
+            const R E = eu * (cb * eu), Od = ca * eu;
+            const R base = w * (A0 + E), odd = w * Od;
+            const R gi = om1 * g[i] + (base + odd), go = om1 * g[o] + (base - odd);
+            g[i] = gi;
+            g[o] = go;
+        }
+        rho_o = rho;
+        ux_o = ux;
+        uy_o = uy;
+        uz_o = uz;
+        return;
+    }
     const R ux = (jx + R(0.5) * F0) * inv, uy = (jy + R(0.5) * F1) * inv, uz = (jz + R(0.5) * F2) * inv;
-    const R omega = pick<R>(L.omega_d, L.omega_f), cF = pick<R>(L.cF_d, L.cF_f);
+    const R cF = pick<R>(L.cF_d, L.cF_f);
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * F0 + uy * F1 + uz * F2;
-    const R om1 = R(1) - omega, ca = R(3) * omega * rho, cb = R(4.5) * omega * rho;
     const R c3 = R(3) * cF, c9 = R(9) * cF;
     const R A0 = omega * (dr - R(1.5) * rho * uu) - c3 * uF;
-    const R g0 = om1 * g[0] + wq<R>(0) * A0;
+    const R g0 = om1 * g[0] + (wq<R>(0) * kS) * A0;
     g[0] = g0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -190,7 +235,7 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
         if (ex(i)) { eu += R(ex(i)) * ux; eF += R(ex(i)) * F0; }
         if (ey(i)) { eu += R(ey(i)) * uy; eF += R(ey(i)) * F1; }
         if (ez(i)) { eu += R(ez(i)) * uz; eF += R(ez(i)) * F2; }
-        const R w = wq<R>(i);
+        const R w = wq<R>(i) * kS;
         const R E = eu * (cb * eu + c9 * eF), Od = ca * eu + c3 * eF;
         const R base = w * (A0 + E), odd = w * Od;
         const R gi = om1 * g[i] + (base + odd), go = om1 * g[o] + (base - odd);
@@ -232,11 +277,11 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
         const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
         const int sy = ey(i) > 0 ? oy_m : ey(i) < 0 ? oy_p : oy_0;
         const int sz = ez(i) > 0 ? oz_m : ez(i) < 0 ? oz_p : oz_0;
-        g[i] = Pop<S, R>::ld(fin + (long long)i * st + (sx + sy + sz));
+        g[i] = Pop<S, R>::ld_raw(fin + (long long)i * st + (sx + sy + sz));
     }
 
     R rho, ux, uy, uz;
-    collide_node<R>(g, force, stamp, step, L, x, y, z, idx, rho, ux, uy, uz);
+    collide_node<R, Pop<S, R>::kScaleLog2>(g, force, stamp, step, L, x, y, z, idx, rho, ux, uy, uz);
     // bfloat16 storage rounds stochastically (8-bit mantissa: nearest
     // rounding of a smooth flow repeats the same error at every node of a
     // plane and step, a bias); the other formats round to nearest
@@ -245,9 +290,9 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
     auto put = [&](S *p, R v) {
         if constexpr (kSR) {
             rs = xorshift32(rs);
-            Pop<S, R>::st_sr(p, v, rs);
+            Pop<S, R>::st_sr_raw(p, v, rs);
         } else {
-            Pop<S, R>::st(p, v);
+            Pop<S, R>::st_raw(p, v);
         }
     };
     put(fout + idx, g[0]);
@@ -413,11 +458,11 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
-            g[i] = Pop<S, R>::from(sm[(i * rows + r) * nx + sx]);
+            g[i] = Pop<S, R>::from_raw(sm[(i * rows + r) * nx + sx]);
         }
         const long long idx = x + (long long)y * nx + (long long)z * nxy;
         R rho, ux, uy, uz;
-        collide_node<R>(g, force, stamp, step, L, x, y, z, idx, rho, ux, uy, uz);
+        collide_node<R, Pop<S, R>::kScaleLog2>(g, force, stamp, step, L, x, y, z, idx, rho, ux, uy, uz);
         if (fields) {
             fields[idx] = rho;
             fields[st + idx] = ux;
@@ -436,9 +481,9 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
             S v;
             if constexpr (kSR) {
                 rs = xorshift32(rs);
-                v = Pop<S, R>::to_sr(g[i], rs);
+                v = Pop<S, R>::to_sr_raw(g[i], rs);
             } else {
-                v = Pop<S, R>::to(g[i]);
+                v = Pop<S, R>::to_raw(g[i]);
             }
             sm[(i * rows + r) * nx + x] = v;
         };
