@@ -124,10 +124,13 @@ struct Pop<__nv_bfloat16, float> {
     __device__ static void st_raw(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static float from_raw(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __nv_bfloat16 to_raw(float v) { return __float2bfloat16_rn(v); }
-    __device__ static __nv_bfloat16 to_sr_raw(float v, uint32_t r) {
-        const uint32_t b = (__float_as_uint(v) + (r >> 16)) & 0xFFFF0000u;
+    // r16: 16 random bits added below the kept mantissa before truncation
+    __device__ static __nv_bfloat16 to_sr_bits(float v, uint32_t r16) {
+        const uint32_t b = (__float_as_uint(v) + r16) & 0xFFFF0000u;
         return __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
+    __device__ static void st_sr_bits(__nv_bfloat16 *p, float v, uint32_t r16) { *p = to_sr_bits(v, r16); }
+    __device__ static __nv_bfloat16 to_sr_raw(float v, uint32_t r) { return to_sr_bits(v, r >> 16); }
     __device__ static void st_sr_raw(__nv_bfloat16 *p, float v, uint32_t r) { *p = to_sr_raw(v, r); }
     __device__ static __nv_bfloat16 to_sr(float v, uint32_t r) { return to_sr_raw(v * kHalfScale, r); }
     __device__ static void st_sr(__nv_bfloat16 *p, float v, uint32_t r) { *p = to_sr(v, r); }

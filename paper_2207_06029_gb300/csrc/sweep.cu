@@ -285,22 +285,28 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
     // bfloat16 storage rounds stochastically (8-bit mantissa: nearest
     // rounding of a smooth flow repeats the same error at every node of a
     // plane and step, a bias); the other formats round to nearest
+    // (one 32-bit draw rounds g0 and then each pair (i, opp(i)): its high
+    // 16 bits for i, its low 16 bits for the opposite direction)
     constexpr bool kSR = std::is_same<S, __nv_bfloat16>::value;
-    uint32_t rs = kSR ? (lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u) : 0u;
-    auto put = [&](S *p, R v) {
-        if constexpr (kSR) {
-            rs = xorshift32(rs);
-            Pop<S, R>::st_sr_raw(p, v, rs);
-        } else {
-            Pop<S, R>::st_raw(p, v);
-        }
-    };
-    put(fout + idx, g[0]);
+    if constexpr (kSR) {
+        uint32_t rs = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u;
+        rs = xorshift32(rs);
+        Pop<S, R>::st_sr_bits(fout + idx, g[0], rs >> 16);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int i = pair_rep(k), o = opp(i);
-        put(fout + (long long)i * st + idx, g[i]);
-        put(fout + (long long)o * st + idx, g[o]);
+        for (int k = 0; k < 9; ++k) {
+            const int i = pair_rep(k), o = opp(i);
+            rs = xorshift32(rs);
+            Pop<S, R>::st_sr_bits(fout + (long long)i * st + idx, g[i], rs >> 16);
+            Pop<S, R>::st_sr_bits(fout + (long long)o * st + idx, g[o], rs & 0xFFFFu);
+        }
+    } else {
+        Pop<S, R>::st_raw(fout + idx, g[0]);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = pair_rep(k), o = opp(i);
+            Pop<S, R>::st_raw(fout + (long long)i * st + idx, g[i]);
+            Pop<S, R>::st_raw(fout + (long long)o * st + idx, g[o]);
+        }
     }
     if (fields) {
         fields[idx] = rho;
@@ -476,22 +482,21 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
         // with the cell's random stream, the values taken in the same order
         constexpr bool kSR = std::is_same<S, __nv_bfloat16>::value;
         const long long idx = x + (long long)y * nx + (long long)z * nxy;
-        uint32_t rs = kSR ? (lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u) : 0u;
-        auto put = [&](int i) {
-            S v;
-            if constexpr (kSR) {
-                rs = xorshift32(rs);
-                v = Pop<S, R>::to_sr_raw(g[i], rs);
-            } else {
-                v = Pop<S, R>::to_raw(g[i]);
-            }
-            sm[(i * rows + r) * nx + x] = v;
-        };
-        put(0);
+        S *row = sm + r * nx + x;  // value of direction i at row[i * rows * nx]
+        if constexpr (kSR) {
+            uint32_t rs = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u;
+            rs = xorshift32(rs);
+            row[0] = Pop<S, R>::to_sr_bits(g[0], rs >> 16);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            put(pair_rep(k));
-            put(opp(pair_rep(k)));
+            for (int k = 0; k < 9; ++k) {
+                const int i = pair_rep(k), o = opp(i);
+                rs = xorshift32(rs);
+                row[i * rows * nx] = Pop<S, R>::to_sr_bits(g[i], rs >> 16);
+                row[o * rows * nx] = Pop<S, R>::to_sr_bits(g[o], rs & 0xFFFFu);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) row[i * rows * nx] = Pop<S, R>::to_raw(g[i]);
         }
     }
     __syncthreads();
