@@ -401,6 +401,7 @@ int lbib_create(const lbib_params *p, void **out) {
     L.ntz = (n[2] + kTile - 1) / kTile;
     L.ncell = (int)ncell;
     L.stride = (ncell + 63) / 64 * 64;
+    L.off32 = (long long)Q * L.stride <= 0xFFFFFFFFLL;
     L.sweep_vec = 0;  // the one-node sweep; the autotuner may pick the row-tile kernel
     for (int a = 0; a < 3; ++a) {
         L.bc[a] = p->bc[a];
@@ -1608,6 +1609,8 @@ int batch_build(Batch *b) {
     T.cen_blk = reinterpret_cast<const int *>(d + o_bce);
     T.sweep_threads = b->sweep_threads;
     T.sweep_cpt = b->sweep_cpt;
+    T.sweep_off32 = 1;
+    for (const Lattice &Li : lat) T.sweep_off32 &= Li.off32;
     b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back(),
                      cen_pre.back()};
     b->lat_h = lat;

@@ -162,6 +162,7 @@ struct Lattice {
     int ntx, nty, ntz;      // tiles per axis
     int ncell;              // nx*ny*nz
     long long stride;       // elements between population planes (ncell padded)
+    int off32;              // 1: all 19 planes lie within 2^32 elements of the first
     int bc[3];
     double tau;
     double gext[3];
@@ -274,6 +275,7 @@ struct BatchTables {
     const int *sweep_blk, *mom_blk, *mls_blk, *memb_blk, *rf_blk, *rm_blk, *cen_blk;  // item of each block
     int sweep_threads;     // threads per sweep block
     int sweep_cpt;         // cells per sweep thread (blocks per lattice = cells / (threads * cpt))
+    int sweep_off32;       // 1: every lattice of the batch has off32 set
 };
 
 // Copies a table entry into shared memory with the whole block (the batch

@@ -248,8 +248,20 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
     uz_o = uz;
 }
 
+// Element o of population plane i.  With 32-bit plane offsets (every
+// element of the 19 planes within 2^32 of the base, L.off32) the address is
+// one 32-bit multiply-add and one widening multiply-add; else the offset is
+// formed in 64 bits.
+template <bool kOff32, typename T>
+__device__ __forceinline__ T *plane_ptr(T *base, const Lattice &L, int i, int o) {
+    if constexpr (kOff32)
+        return base + ((unsigned)i * (unsigned)L.stride + (unsigned)o);
+    else
+        return base + ((long long)i * L.stride + o);
+}
+
 // Stream, walls and collision of node (x, y, z).
-template <typename S, typename R>
+template <typename S, typename R, bool kOff32>
 __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restrict__ fout, R *__restrict__ force,
                                            const uint32_t *__restrict__ stamp, uint32_t step, const Lattice &L,
                                            R *__restrict__ fields, int x, int y, int z, uint32_t seed) {
@@ -277,7 +289,7 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
         const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : x;
         const int sy = ey(i) > 0 ? oy_m : ey(i) < 0 ? oy_p : oy_0;
         const int sz = ez(i) > 0 ? oz_m : ez(i) < 0 ? oz_p : oz_0;
-        g[i] = Pop<S, R>::ld_raw(fin + (long long)i * st + (sx + sy + sz));
+        g[i] = Pop<S, R>::ld_raw(plane_ptr<kOff32>(fin, L, i, sx + sy + sz));
     }
 
     R rho, ux, uy, uz;
@@ -291,21 +303,21 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
     if constexpr (kSR) {
         uint32_t rs = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u;
         rs = xorshift32(rs);
-        Pop<S, R>::st_sr_bits(fout + idx, g[0], rs >> 16);
+        Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, 0, idx), g[0], rs >> 16);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int i = pair_rep(k), o = opp(i);
             rs = xorshift32(rs);
-            Pop<S, R>::st_sr_bits(fout + (long long)i * st + idx, g[i], rs >> 16);
-            Pop<S, R>::st_sr_bits(fout + (long long)o * st + idx, g[o], rs & 0xFFFFu);
+            Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, i, idx), g[i], rs >> 16);
+            Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, o, idx), g[o], rs & 0xFFFFu);
         }
     } else {
-        Pop<S, R>::st_raw(fout + idx, g[0]);
+        Pop<S, R>::st_raw(plane_ptr<kOff32>(fout, L, 0, idx), g[0]);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int i = pair_rep(k), o = opp(i);
-            Pop<S, R>::st_raw(fout + (long long)i * st + idx, g[i]);
-            Pop<S, R>::st_raw(fout + (long long)o * st + idx, g[o]);
+            Pop<S, R>::st_raw(plane_ptr<kOff32>(fout, L, i, idx), g[i]);
+            Pop<S, R>::st_raw(plane_ptr<kOff32>(fout, L, o, idx), g[o]);
         }
     }
     if (fields) {
@@ -355,7 +367,7 @@ __device__ __forceinline__ bool in_box(const Lattice &L, const int *lo, const in
 // Whole lattice (box == nullptr), or every node outside the box.
 // sr: the two-word rounding-seed counter of the lattice; a step reads word
 // `parity` and advances the other one (parity alternates with the steps).
-template <typename S, typename R>
+template <typename S, typename R, bool kOff32>
 __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__restrict__ fout,
                                                R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                                const uint32_t *__restrict__ dstep, Lattice L,
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
         clamp_box(L, box, lo, ext);
         if (in_box(L, lo, ext, x, y, z)) return;
     }
-    sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
+    sweep_cell<S, R, kOff32>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
 }
 
 // The far field (nodes outside the body box) with a bounded number of
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(256) k_sweep(const S *__restrict__ fin, S *__r
 // the lattice, so that SM resources stay free for the IB kernels running
 // beside it (the block scheduler cannot take resources back from blocks
 // already resident).
-template <typename S, typename R>
+template <typename S, typename R, bool kOff32>
 __global__ void __launch_bounds__(256) k_sweep_far(const S *__restrict__ fin, S *__restrict__ fout,
                                                    R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                                    const uint32_t *__restrict__ dstep, Lattice L,
@@ -398,7 +410,7 @@ __global__ void __launch_bounds__(256) k_sweep_far(const S *__restrict__ fin, S 
         const int tx = t % gx, ty = (t / gx) % gy, z = t / (gx * gy);
         const int x = tx * blockDim.x + threadIdx.x, y = ty * blockDim.y + threadIdx.y;
         if (x >= L.nx || y >= L.ny || in_box(L, lo, ext, x, y, z)) continue;
-        sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
+        sweep_cell<S, R, kOff32>(fin, fout, force, stamp, step, L, fields, x, y, z, seed);
     }
 }
 
@@ -509,7 +521,7 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
 }
 
 // The nodes inside the box (grid-stride; periodic coordinates wrap).
-template <typename S, typename R>
+template <typename S, typename R, bool kOff32>
 __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S *__restrict__ fout,
                                                    R *__restrict__ force, const uint32_t *__restrict__ stamp,
                                                    const uint32_t *__restrict__ dstep, Lattice L,
@@ -525,7 +537,7 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
         int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
         for (int a = 0; a < 3; ++a)
             if (L.bc[a] == kPeriodic) c[a] = ((c[a] % n[a]) + n[a]) % n[a];
-        sweep_cell<S, R>(fin, fout, force, stamp, step, L, fields, c[0], c[1], c[2], seed);
+        sweep_cell<S, R, kOff32>(fin, fout, force, stamp, step, L, fields, c[0], c[1], c[2], seed);
     }
 }
 
@@ -533,7 +545,7 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
 // blocks of a lattice stride over its cells (x fastest), a few cells per
 // thread so that the per-block set-up (the lattice entry staged in shared
 // memory) is amortised.
-template <typename S, typename R>
+template <typename S, typename R, bool kOff32>
 __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int store_fields) {
     __shared__ Lattice L;
     const int slot = __ldg(T.sweep_blk + blockIdx.x);
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int st
     R *fields = store_fields ? (R *)F.fields : nullptr;
     for (int c = (blockIdx.x - b0) * blockDim.x + threadIdx.x; c < L.ncell; c += nb * blockDim.x) {
         const int x = c % L.nx, yz = c / L.nx, y = yz % L.ny, z = yz / L.ny;
-        sweep_cell<S, R>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L, fields, x, y, z, seed);
+        sweep_cell<S, R, kOff32>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L, fields, x, y, z, seed);
     }
 }
 
@@ -647,12 +659,12 @@ static void sweep_shape(const Lattice &L, dim3 &grid, dim3 &block) {
 }
 
 // part: 0 whole lattice, 1 outside the box, 2 inside the box
-template <typename S, typename R>
+template <typename S, typename R, bool kOff32>
 static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint32_t *stamp, const uint32_t *step,
                            const Lattice &L, void *fields, int part, const int *box, uint32_t *sr, int parity,
                            int nsm, cudaStream_t s) {
     if (part == 2) {
-        k_sweep_box<S, R><<<4 * nsm, 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
+        k_sweep_box<S, R, kOff32><<<4 * nsm, 256, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L,
                                                   (R *)fields, box, sr, parity);
     } else if (const int rows = tile_rows<S>(L)) {
         const dim3 grid((L.ny + rows - 1) / rows, L.nz);
@@ -663,34 +675,48 @@ static cudaError_t sweep_t(const void *fin, void *fout, void *force, const uint3
     } else if (part == 1 && L.far_per_sm > 0) {
         dim3 grid, block;
         sweep_shape(L, grid, block);
-        k_sweep_far<S, R><<<L.far_per_sm * nsm, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step,
+        k_sweep_far<S, R, kOff32><<<L.far_per_sm * nsm, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step,
                                                                L, (R *)fields, box, sr, parity, (int)grid.x,
                                                                (int)grid.y);
     } else {
         dim3 grid, block;
         sweep_shape(L, grid, block);
-        k_sweep<S, R><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L, (R *)fields,
+        k_sweep<S, R, kOff32><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, (R *)force, stamp, step, L, (R *)fields,
                                              part == 1 ? box : nullptr, sr, parity);
     }
     return cudaGetLastError();
+}
+
+template <typename S, typename R>
+static cudaError_t sweep_any(const void *fin, void *fout, void *force, const uint32_t *stamp, const uint32_t *step,
+                             const Lattice &L, void *fields, int part, const int *box, uint32_t *sr, int parity,
+                             int nsm, cudaStream_t s) {
+    if (L.off32)
+        return sweep_t<S, R, true>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+    return sweep_t<S, R, false>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
 }
 
 cudaError_t launch_sweep(int prec, const void *fin, void *fout, void *force, const uint32_t *stamp,
                          const uint32_t *step, const Lattice &L, void *fields, int part, const int *box,
                          uint32_t *sr, int parity, int nsm, cudaStream_t s) {
     switch (prec) {
-        case 0: return sweep_t<double, double>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
-        case 1: return sweep_t<float, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
-        case 2: return sweep_t<__half, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+        case 0: return sweep_any<double, double>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+        case 1: return sweep_any<float, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
+        case 2: return sweep_any<__half, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm, s);
         default:
-            return sweep_t<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity, nsm,
-                                                 s);
+            return sweep_any<__nv_bfloat16, float>(fin, fout, force, stamp, step, L, fields, part, box, sr, parity,
+                                                   nsm, s);
     }
 }
 
 template <typename S, typename R>
 static cudaError_t batch_sweep_t(const BatchTables &T, const BatchGrid &G, int phase, int store, cudaStream_t s) {
-    if (G.sweep > 0) kb_sweep<S, R><<<G.sweep, T.sweep_threads, 0, s>>>(T, phase, store);
+    if (G.sweep > 0) {
+        if (T.sweep_off32)
+            kb_sweep<S, R, true><<<G.sweep, T.sweep_threads, 0, s>>>(T, phase, store);
+        else
+            kb_sweep<S, R, false><<<G.sweep, T.sweep_threads, 0, s>>>(T, phase, store);
+    }
     return cudaGetLastError();
 }
 

@@ -515,3 +515,47 @@ def test_invalid_bodies_rejected(lbib):
     with pytest.raises(lbib.LbibError):
         ctx.add_body(v, f, density_ratio=0.0)
     ctx.close()
+
+
+@pytest.mark.parametrize("nz", [592, 600])
+def test_plane_offsets_at_the_32_bit_limit(lbib, nz):
+    """The sweep forms population addresses with 32-bit plane offsets while
+    all 19 planes lie within 2^32 elements of the first, and in 64 bits
+    above that.  616 x 616 x 592 (224.6 M nodes) is just below the limit,
+    616 x 616 x 600 (227.7 M nodes) just above it.  A periodic FP32 lattice
+    filled with copies of a random 8^3 state evolves exactly as the 8^3
+    lattice does (every copy sees the same neighbours and the arithmetic per
+    node is the same), so after three steps the fields of every node equal
+    those of the small lattice bit for bit: an offset that wraps or a plane
+    addressed from the wrong base would differ at the size of the flow."""
+    small = W.case_empty(n=(8, 8, 8), tau=0.8, precision=W.PREC_FP32, seed=11, amplitude=2e-2)
+    ctx = lbib.Context.from_case(small)
+    ctx.step(3)
+    rho_s, u_s = ctx.fields()
+    ctx.close()
+    n = (616, 616, nz)
+    assert (19 * ((n[0] * n[1] * n[2] + 63) // 64 * 64) > 2 ** 32) == (nz == 600)
+    reps = (nz // 8, n[1] // 8, n[0] // 8)
+    rho0, u0 = small.initial_fields()
+    dev = torch.device("cuda")
+    rho = torch.from_numpy(rho0.reshape(8, 8, 8)).to(dev).repeat(*reps).contiguous()
+    u = torch.from_numpy(u0.reshape(8, 8, 8, 3)).to(dev).repeat(*reps, 1).contiguous()
+    h = lbib.lbib_create(lbib.make_params(n, 0.8, bc=(W.PERIODIC,) * 3, precision=lbib.LBIB_FP32))
+    try:
+        torch.cuda.synchronize()
+        lbib.lbib_set_fields(h, rho, u)
+        del rho, u
+        lbib.lbib_step(h, 3)
+        rho_b = torch.empty(n[0] * n[1] * n[2], dtype=torch.float64, device=dev)
+        u_b = torch.empty(3 * n[0] * n[1] * n[2], dtype=torch.float64, device=dev)
+        lbib.lbib_get_fields(h, rho_b, u_b)
+        torch.cuda.synchronize()
+    finally:
+        lbib.lbib_destroy(h)
+    want_rho = torch.from_numpy(rho_s.reshape(8, 8, 8)).to(dev).repeat(*reps).reshape(-1)
+    assert torch.equal(rho_b, want_rho)
+    del rho_b, want_rho
+    want_u = torch.from_numpy(u_s.reshape(8, 8, 8, 3)).to(dev).repeat(*reps, 1).reshape(-1)
+    assert torch.equal(u_b, want_u)
+    del u_b, want_u
+    torch.cuda.empty_cache()
