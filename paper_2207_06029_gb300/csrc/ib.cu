@@ -91,7 +91,7 @@ __device__ __forceinline__ void moments_body(const S *__restrict__ fin, const La
         int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
         int cm[3], cp[3];
         for (int a = 0; a < 3; ++a) {
-            if (L.bc[a] == kPeriodic) c[a] = ((c[a] % n[a]) + n[a]) % n[a];
+            if (L.bc[a] == kPeriodic) c[a] = wrap_periodic(c[a], n[a]);
             int vm = c[a] - 1, vp = c[a] + 1;
             if (vm < 0) vm = L.bc[a] == kPeriodic ? n[a] - 1 : 0;
             if (vp >= n[a]) vp = L.bc[a] == kPeriodic ? 0 : n[a] - 1;

@@ -183,6 +183,14 @@ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
+// Image of coordinate c in [0, n) on a periodic axis (no division when c
+// is already inside).
+__device__ __forceinline__ int wrap_periodic(int c, int n) {
+    if ((unsigned)c < (unsigned)n) return c;
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
 // Wall velocity table index of a node: per axis 0 (interior), 1 (index-0
 // face), 2 (last face); entry = mean velocity of the faces present.
 __host__ __device__ constexpr int wall_code(int cx, int cy, int cz) { return cx + 3 * cy + 9 * cz; }

@@ -356,11 +356,13 @@ __device__ __forceinline__ void clamp_box(const Lattice &L, const int *box, int 
 
 __device__ __forceinline__ bool in_box(const Lattice &L, const int *lo, const int *ext, int x, int y, int z) {
     const int c[3] = {x, y, z}, n[3] = {L.nx, L.ny, L.nz};
-    for (int a = 0; a < 3; ++a) {
-        int d = c[a] - lo[a];
-        if (L.bc[a] == kPeriodic) d = ((d % n[a]) + n[a]) % n[a];
-        if (d < 0 || d >= ext[a]) return false;
-    }
+    // walled axes first (no wrap; most far-field nodes fail one of them)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (L.bc[a] != kPeriodic && (unsigned)(c[a] - lo[a]) >= (unsigned)ext[a]) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (L.bc[a] == kPeriodic && (unsigned)wrap_periodic(c[a] - lo[a], n[a]) >= (unsigned)ext[a]) return false;
     return true;
 }
 
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(256) k_sweep_box(const S *__restrict__ fin, S 
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         int c[3] = {lo[0] + k % ext[0], lo[1] + (k / ext[0]) % ext[1], lo[2] + k / (ext[0] * ext[1])};
         for (int a = 0; a < 3; ++a)
-            if (L.bc[a] == kPeriodic) c[a] = ((c[a] % n[a]) + n[a]) % n[a];
+            if (L.bc[a] == kPeriodic) c[a] = wrap_periodic(c[a], n[a]);
         sweep_cell<S, R, kOff32>(fin, fout, force, stamp, step, L, fields, c[0], c[1], c[2], seed);
     }
 }
