@@ -444,7 +444,7 @@ def batch_leg(args):
     return out
 
 
-def serve_leg(args, mode, precision, max_active=64, batch_cells=0, small=False):
+def serve_leg(args, mode, precision, max_active=64, batch_cells=0, small=False, batch_order=0):
     """A seeded Poisson stream (4 requests/s) of capsule-in-shear and
     settling-sphere runs through the serving engine; latency from submission
     to completion."""
@@ -456,7 +456,7 @@ def serve_leg(args, mode, precision, max_active=64, batch_cells=0, small=False):
     else:
         stream = W.serve_stream(count=args.serve_requests, precision=precision)
     server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=max_active, mode=mode,
-                                    batch_cells=batch_cells)
+                                    batch_cells=batch_cells, batch_order=batch_order)
     reqs = [(t, lbib.request_from_case(case, steps), case, steps) for t, case, steps in stream]
     t0 = time.perf_counter()
     ids = []
@@ -667,13 +667,17 @@ def main():
             "stream": f"{args.serve_requests} requests, Poisson 4/s, half capsule-in-shear half settling sphere, "
                       "cubic N~U{32..160} (capsules N>=48), steps~U{1000..6000}, budget 150 GB",
             "batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32),
-            "batched_fp32_srpt_8M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, batch_cells=8 << 20),
+            "batched_fp32_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, batch_cells=1 << 20,
+                                                batch_order=lbib.LBIB_SERVE_OLDEST),
+            "batched_fp32_srpt_2M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, batch_cells=2 << 20),
             "plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32),
-            "batched_fp16_dev_srpt_8M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV,
-                                                  batch_cells=8 << 20),
+            "batched_fp16_dev_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV,
+                                                    batch_cells=1 << 20, batch_order=lbib.LBIB_SERVE_OLDEST),
             "small_stream": "64 requests, Poisson 40/s, same mix, cubic N~U{32..64} (capsules 48..64), "
                             "steps~U{500..2000}",
             "small_batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, small=True),
+            "small_batched_fp32_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, small=True,
+                                                      batch_cells=1 << 20, batch_order=lbib.LBIB_SERVE_OLDEST),
             "small_plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32, small=True),
         }
     if not args.no_cpu_baseline:

@@ -313,13 +313,15 @@ const char *lbib_batch_last_error(const void *batch);
  * queued requests in arrival order while the estimated device memory of the
  * admitted ones fits hbm_budget, and advances all admitted runs together as
  * one batch (lbib_batch_*), chunk_steps steps at a time or fewer: a chunk
- * ends when the run with the fewest remaining steps finishes.  Finished runs
+ * ends when the run with the fewest remaining steps finishes.  A chunk that
+ * advances a single run steps it with lbib_step.  Finished runs
  * leave the batch, arrivals join it, and the batch is rebuilt (continuous
  * batching).  LBIB_SERVE_PLAIN instead runs one request at a time with
  * lbib_step, in arrival order.  A finished run's context stays resident (and
  * counts against the budget) until the caller takes it. */
 enum { LBIB_REQ_QUEUED = 0, LBIB_REQ_RUNNING = 1, LBIB_REQ_DONE = 2, LBIB_REQ_FAILED = 3 };
 enum { LBIB_SERVE_BATCHED = 0, LBIB_SERVE_PLAIN = 1 };
+enum { LBIB_SERVE_SHORTEST = 0, LBIB_SERVE_OLDEST = 1 };
 
 typedef struct {
     size_t hbm_budget;  /* bytes of device memory the admitted runs may hold */
@@ -327,8 +329,11 @@ typedef struct {
     int max_active;     /* most runs in the batch at once (>= 1) */
     int mode;           /* LBIB_SERVE_BATCHED or LBIB_SERVE_PLAIN */
     long long batch_cells; /* batched mode: 0 advances every admitted run in each chunk; > 0 advances
-                            * the runs with the least remaining work (cells x steps) up to this many
-                            * lattice cells (at least one run), the others waiting resident */
+                            * up to this many lattice cells of runs (at least one run), chosen in
+                            * batch_order, the others waiting resident */
+    int batch_order;       /* with batch_cells > 0: LBIB_SERVE_SHORTEST the runs with the least
+                            * remaining work (cells x steps) first, LBIB_SERVE_OLDEST the earliest
+                            * submitted first.  LBIB_EINVAL for other values. */
 } lbib_serve_params;
 
 typedef struct {

@@ -7,8 +7,9 @@
 // of steps at a time.  A chunk ends when the run with the fewest remaining
 // steps finishes; finished runs leave the batch (their contexts stay
 // resident until the caller takes them), new arrivals join, and the batch is
-// rebuilt: continuous batching.  The plain mode runs one request at a time
-// with lbib_step, in arrival order, for comparison.
+// rebuilt: continuous batching.  A chunk with a single run advances it with
+// lbib_step.  The plain mode runs one request at a time with lbib_step, in
+// arrival order, for comparison.
 //
 // Built on the public C ABI only.
 #include <cuda_runtime.h>
@@ -204,14 +205,17 @@ void worker_loop(Server *s) {
         }
         if (act.empty()) continue;
         if (s->sp.mode == LBIB_SERVE_BATCHED && s->sp.batch_cells > 0 && act.size() > 1) {
-            // shortest remaining work first: the runs with the least
-            // remaining cell updates, up to batch_cells lattice cells (at
-            // least one run); the others stay resident and wait
-            std::stable_sort(act.begin(), act.end(), [](const Request *a, const Request *b) {
-                const double wa = (double)a->remaining * a->p.nx * a->p.ny * a->p.nz;
-                const double wb = (double)b->remaining * b->p.nx * b->p.ny * b->p.nz;
-                return wa < wb;
-            });
+            // up to batch_cells lattice cells of runs (at least one run),
+            // the runs with the least remaining cell updates first or the
+            // earliest submitted first; the others stay resident and wait
+            if (s->sp.batch_order == LBIB_SERVE_OLDEST)
+                std::stable_sort(act.begin(), act.end(), [](const Request *a, const Request *b) { return a->id < b->id; });
+            else
+                std::stable_sort(act.begin(), act.end(), [](const Request *a, const Request *b) {
+                    const double wa = (double)a->remaining * a->p.nx * a->p.ny * a->p.nz;
+                    const double wb = (double)b->remaining * b->p.nx * b->p.ny * b->p.nz;
+                    return wa < wb;
+                });
             long long cells = 0;
             size_t k = 0;
             for (; k < act.size(); ++k) {
@@ -226,10 +230,14 @@ void worker_loop(Server *s) {
         const auto t_a = Clock::now();
         int brc = LBIB_OK;
         bool advanced = false;  // the chunk's steps were enqueued for every run
-        if (s->sp.mode == LBIB_SERVE_PLAIN) {
+        if (s->sp.mode == LBIB_SERVE_PLAIN || act.size() == 1) {
+            // one run: its own step (the IB stage beside the far-field
+            // sweep, the context's sweep shape), as in plain mode; a batch
+            // that holds the context is rebuilt before it is used again
             brc = lbib_step(act[0]->ctx, (int)chunk);
             advanced = brc == LBIB_OK;
             if (!brc) brc = lbib_sync(act[0]->ctx);
+            stale = true;
         } else {
             if (stale || act != members) {
                 if (batch) lbib_batch_destroy(batch);
@@ -323,7 +331,8 @@ void lbib_request_destroy(void *req) {
 
 int lbib_serve_create(const lbib_serve_params *sp, void **out) {
     if (!sp || !out || sp->hbm_budget == 0 || sp->max_active < 1 ||
-        (sp->mode != LBIB_SERVE_BATCHED && sp->mode != LBIB_SERVE_PLAIN))
+        (sp->mode != LBIB_SERVE_BATCHED && sp->mode != LBIB_SERVE_PLAIN) ||
+        (sp->batch_order != LBIB_SERVE_SHORTEST && sp->batch_order != LBIB_SERVE_OLDEST))
         return LBIB_EINVAL;
     Server *s = new Server();
     s->sp = *sp;

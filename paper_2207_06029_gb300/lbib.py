@@ -49,11 +49,12 @@ class lbib_body_state(C.Structure):
 
 LBIB_REQ_QUEUED, LBIB_REQ_RUNNING, LBIB_REQ_DONE, LBIB_REQ_FAILED = 0, 1, 2, 3
 LBIB_SERVE_BATCHED, LBIB_SERVE_PLAIN = 0, 1
+LBIB_SERVE_SHORTEST, LBIB_SERVE_OLDEST = 0, 1
 
 
 class lbib_serve_params(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("chunk_steps", C.c_int), ("max_active", C.c_int), ("mode", C.c_int),
-                ("batch_cells", C.c_longlong)]
+                ("batch_cells", C.c_longlong), ("batch_order", C.c_int)]
 
 
 class lbib_serve_times(C.Structure):
@@ -589,8 +590,10 @@ def lbib_request_destroy(req):
     load().lbib_request_destroy(req)
 
 
-def lbib_serve_create(hbm_budget, chunk_steps=500, max_active=64, mode=LBIB_SERVE_BATCHED, batch_cells=0):
-    sp = lbib_serve_params(int(hbm_budget), int(chunk_steps), int(max_active), int(mode), int(batch_cells))
+def lbib_serve_create(hbm_budget, chunk_steps=500, max_active=64, mode=LBIB_SERVE_BATCHED, batch_cells=0,
+                      batch_order=0):
+    sp = lbib_serve_params(int(hbm_budget), int(chunk_steps), int(max_active), int(mode), int(batch_cells),
+                           int(batch_order))
     h = C.c_void_p()
     _scheck(load().lbib_serve_create(C.byref(sp), C.byref(h)), "server")
     return h

@@ -66,13 +66,14 @@ def take(L, server, rid, case):
     return out, times
 
 
-@pytest.mark.parametrize("batch_cells", [0, 40000])
-def test_each_result_is_the_same_alone_and_in_the_mix(lbib, batch_cells):
-    """batch_cells = 0: every admitted run in every chunk; 40000: the runs
-    with the least remaining work, about one lattice per chunk, the others
-    waiting resident."""
+@pytest.mark.parametrize("batch_cells,order", [(0, 0), (40000, 0), (40000, 1)])
+def test_each_result_is_the_same_alone_and_in_the_mix(lbib, batch_cells, order):
+    """batch_cells = 0: every admitted run in every chunk; 40000: about one
+    lattice per chunk, the runs with the least remaining work (order 0) or
+    the earliest submitted (order 1), the others waiting resident."""
     reqs = requests(W.PREC_FP64)
-    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=16, max_active=8, batch_cells=batch_cells)
+    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=16, max_active=8, batch_cells=batch_cells,
+                                    batch_order=order)
     ids = []
     for k, (case, steps) in enumerate(reqs):
         ids.append(lbib.lbib_serve_submit(server, lbib.request_from_case(case, steps)))
@@ -166,3 +167,21 @@ def test_centroid_marker_runs_are_served_batched_and_plain(lbib):
         lbib.lbib_serve_destroy(server)
         assert stats["runs_done"] == 3 and stats["runs_failed"] == 0
         assert nsteps == 20 and rel(f, f0) < 1e-13 and rel(X[0], X0[0]) < 1e-13
+
+
+def test_oldest_first_order_finishes_runs_in_submission_order(lbib):
+    """With batch_cells below two lattices and the earliest submitted run
+    first, the runs advance one at a time in submission order (the resident
+    ones wait), so they finish in that order whatever their lengths; an
+    unknown order is refused."""
+    reqs = requests(W.PREC_FP32)
+    server = lbib.lbib_serve_create(hbm_budget=8 << 30, chunk_steps=8, max_active=8, batch_cells=1,
+                                    batch_order=lbib.LBIB_SERVE_OLDEST)
+    ids = [lbib.lbib_serve_submit(server, lbib.request_from_case(c, s)) for c, s in reqs]
+    results = [take(lbib, server, rid, case) for rid, (case, _) in zip(ids, reqs)]
+    lbib.lbib_serve_destroy(server)
+    done = [t["done_s"] for _, t in results]
+    assert done == sorted(done)
+    with pytest.raises(lbib.LbibError) as ei:
+        lbib.lbib_serve_create(hbm_budget=8 << 30, batch_order=2)
+    assert ei.value.code == lbib.LBIB_EINVAL
