@@ -523,6 +523,17 @@ def cpu_baseline(seconds=12.0, min_steps=2, workload="capsule96"):
             "sample": f"{steps} steps of the {WORKLOADS[workload]} case (FP64 oracle, OpenMP over z-planes)"}
 
 
+def cpu_baseline_one_core(seconds=6.0, workload="capsule96"):
+    """The same sample on one host core: a fresh process (the oracle's
+    OpenMP team is sized when its library loads) with OMP_NUM_THREADS=1."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(seconds),
+                        "--workload", workload], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else f"exit {r.returncode}"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,7 +552,12 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--overlap", default="auto", choices=["auto", "on", "off"],
                     help="far-field sweep concurrent with the IB stage (auto: as tuned)")
+    ap.add_argument("--cpu-sample", type=float, default=0.0,
+                    help="only time the oracle for this many seconds on the host and print its figure")
     args = ap.parse_args()
+    if args.cpu_sample > 0:
+        print(json.dumps(cpu_baseline(args.cpu_sample, workload=args.workload)))
+        return
     if args.warmup < 3:
         args.warmup = 3
 
@@ -682,6 +698,7 @@ def main():
         }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, workload=args.workload)
+        line["cpu_baseline"]["one_core"] = cpu_baseline_one_core(workload=args.workload)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
