@@ -643,8 +643,9 @@ def main():
                 "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"]),
                 "steps": r["e2e_steps"], "setup_ms": 1e3 * r["e2e_setup_s"],
                 "note": "context creation from host fields, mesh upload and graph capture included; the markers "
-                        "of every step copied to pinned host buffers behind the step and read on the host one "
-                        "step later; the fields read at the end"},
+                        "of every step staged on the device behind the step, copied to pinned host buffers after "
+                        "each chunk of ten steps and checked on the host while the next chunk runs; the fields "
+                        "read at the end"},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }

@@ -171,12 +171,16 @@ int lbib_get_markers(void *ctx, int body, double *X, double *V, double *F);
  * surface at the next synchronising call.  LBIB_EINVAL for a bad body. */
 int lbib_get_markers_async(void *ctx, int body, double *X, double *V, double *F);
 
-/* Advances the context by nsteps steps and queues, after each step k, the
- * asynchronous copy of body `body`'s markers into X + 3 nv k, V + 3 nv k and
- * F + 3 nv k (host arrays of nsteps * 3 * nv doubles; any may be NULL): a
- * trajectory recorded without a host round trip per step.  The same rules
- * as lbib_get_markers_async apply to the host arrays.  Errors as
- * lbib_step. */
+/* Advances the context by nsteps steps and records body `body`'s markers
+ * after each step k into X + 3 nv k, V + 3 nv k and F + 3 nv k (host arrays
+ * of nsteps * 3 * nv doubles; any may be NULL): a trajectory recorded
+ * without a host round trip per step.  Each step's markers are staged on the
+ * device by one small kernel queued behind the step (in a context-owned
+ * buffer of 3 * nsteps * 3 nv doubles, kept for later calls and grown when
+ * needed); the device-to-host copies, one per requested array, are queued
+ * after the last step.  The same rules as lbib_get_markers_async apply to
+ * the host arrays.  Errors as lbib_step; LBIB_ENOMEM if the staging buffer
+ * cannot be allocated. */
 int lbib_step_markers(void *ctx, int nsteps, int body, double *X, double *V, double *F);
 
 /* Body summary after the last step.  Synchronises. */

@@ -85,6 +85,8 @@ struct Ctx {
     std::string msg;
     size_t bytes = 0;
     std::vector<std::pair<void *, size_t>> allocs;
+    double *mstage = nullptr;  // lbib_step_markers: device staging of the recorded markers
+    size_t mstage_bytes = 0;
     std::vector<void *> transient;  // allocations a checkpoint leaves out (scratch, support moments)
     bool profile = false;
     std::vector<cudaEvent_t> events;  // per step: begin, after MLS, after structure, after sweep
@@ -124,6 +126,20 @@ void *dev_alloc(Ctx *c, size_t bytes) {
         c->bytes += bytes;
     }
     return ptr;
+}
+
+// Frees one block of dev_alloc (the caller has synchronised its uses).
+void dev_free_one(Ctx *c, void *ptr) {
+    for (size_t k = 0; k < c->allocs.size(); ++k)
+        if (c->allocs[k].first == ptr) {
+            if (c->p.free)
+                c->p.free(ptr, c->p.alloc_user);
+            else
+                cudaFree(ptr);
+            c->bytes -= c->allocs[k].second;
+            c->allocs.erase(c->allocs.begin() + k);
+            return;
+        }
 }
 
 void dev_free_all(Ctx *c) {
@@ -1158,18 +1174,59 @@ int lbib_get_markers_async(void *h, int body, double *X, double *V, double *F) {
     return LBIB_OK;
 }
 
+// Step k's markers into slot k of the staging planes (X, U_b, F_l).
+__global__ void k_stage_markers(const double *__restrict__ X, const double *__restrict__ Ub,
+                                const double *__restrict__ Fl, double *__restrict__ dst, long long n3,
+                                long long plane, int slot) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        if (X) dst[slot * n3 + i] = X[i];
+        if (Ub) dst[plane + slot * n3 + i] = Ub[i];
+        if (Fl) dst[2 * plane + slot * n3 + i] = Fl[i];
+    }
+}
+
 int lbib_step_markers(void *h, int nsteps, int body, double *X, double *V, double *F) {
     Ctx *c = as_ctx(h);
     if (!c || nsteps < 0) return LBIB_EINVAL;
     if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
+    if (nsteps == 0) return LBIB_OK;
+    if (c->err && c->err != LBIB_EBODY_WALL) return c->err;
     const size_t n3 = 3 * (size_t)c->bodies[body].nv;
+    const size_t plane = n3 * (size_t)nsteps, need = 3 * plane * sizeof(double);
+    if (need > c->mstage_bytes) {
+        // a larger staging buffer; the old one may still feed queued copies
+        if (c->mstage) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "marker staging");
+            dev_free_one(c, c->mstage);
+            c->mstage = nullptr;
+            c->mstage_bytes = 0;
+        }
+        c->mstage = static_cast<double *>(dev_alloc(c, need));
+        if (!c->mstage) return fail(c, LBIB_ENOMEM, "marker staging buffer of %zu bytes", need);
+        c->mstage_bytes = need;
+    }
+    // each step's markers go to the staging planes on the device (one small
+    // kernel behind the step); the host copies follow the last step, one
+    // per requested array
+    const int blocks = (int)std::min<size_t>((n3 + 255) / 256, 1024);
     for (int k = 0; k < nsteps; ++k) {
         int rc = lbib_step(h, 1);
-        if (!rc)
-            rc = lbib_get_markers_async(h, body, X ? X + n3 * k : nullptr, V ? V + n3 * k : nullptr,
-                                        F ? F + n3 * k : nullptr);
         if (rc) return rc;
+        DevBody &b = c->bodies[body];
+        k_stage_markers<<<blocks, 256, 0, c->stream>>>(X ? b.X[b.cur] : nullptr, V ? b.Ub : nullptr,
+                                                       F ? b.Fl : nullptr, c->mstage, (long long)n3,
+                                                       (long long)plane, k);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "marker staging");
+        c->launches++;
     }
+    const size_t bytes = plane * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (X) e = cudaMemcpyAsync(X, c->mstage, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && V) e = cudaMemcpyAsync(V, c->mstage + plane, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, c->mstage + 2 * plane, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "markers copy");
     return LBIB_OK;
 }
 

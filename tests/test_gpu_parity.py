@@ -457,27 +457,39 @@ def test_async_marker_copies_are_ordered_on_the_stream(lbib):
 
 
 def test_recorded_trajectory_matches_step_by_step_reads(lbib):
-    """lbib_step_markers: five steps with every step's markers queued into a
-    host ring, against a context read synchronously after each step (the
-    two differ only in the order of the atomic spreading sums)."""
+    """lbib_step_markers: calls of 5, 9 (the device staging buffer grows), 2
+    and 0 steps with every step's markers recorded into host rings (pinned
+    and pageable; V omitted in one call), against a context read
+    synchronously after each step (the two differ only in the order of the
+    atomic spreading sums)."""
     case = W.case_capsule_shear(n=24, tau=0.8, shear_rate=2e-3, radius=5.0, level=3, Ca=0.05, Eb=0.01, kv=1.0,
                                 precision=W.PREC_FP64)
     nv = case.bodies[0].verts.shape[0]
+    calls = [5, 9, 2, 0]
     ref = lbib.Context.from_case(case)
     want = []
-    for k in range(5):
+    for k in range(sum(calls)):
         ref.step(1)
         want.append(ref.markers(0))
     ref.close()
     ctx = lbib.Context.from_case(case)
-    X = torch.empty((5, nv, 3), dtype=torch.float64, pin_memory=True)
-    F = np.full((5, nv, 3), np.nan)
-    lbib.lbib_step_markers(ctx.h, 5, 0, X, None, F)
-    lbib.lbib_sync(ctx.h)
-    for k in range(5):
-        assert rel(X[k].numpy(), want[k][0]) < 1e-13
-        assert np.abs(F[k] - want[k][2]).max() < 1e-10 * max(np.abs(want[k][2]).max(), 1e-3)
-    assert ctx.counters()[0] == 5
+    done = 0
+    for j, n in enumerate(calls):
+        X = torch.empty((max(n, 1), nv, 3), dtype=torch.float64, pin_memory=True)
+        V = np.full((max(n, 1), nv, 3), np.nan)
+        F = np.full((max(n, 1), nv, 3), np.nan)
+        lbib.lbib_step_markers(ctx.h, n, 0, X, V if j != 0 else None, F)
+        lbib.lbib_sync(ctx.h)
+        for k in range(n):
+            Xw, Vw, Fw = want[done + k]
+            assert rel(X[k].numpy(), Xw) < 1e-13
+            if j != 0:
+                assert np.abs(V[k] - Vw).max() < 1e-10 * max(np.abs(Vw).max(), 1e-3)
+            assert np.abs(F[k] - Fw).max() < 1e-10 * max(np.abs(Fw).max(), 1e-3)
+        if j == 0:
+            assert np.isnan(V).all()
+        done += n
+    assert ctx.counters()[0] == sum(calls)
     ctx.close()
 
 
