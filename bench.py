@@ -286,8 +286,8 @@ def run_gpu(args, rank, world):
     chunk = 10
     nvb = b.verts.shape[0]
     Xb = [torch.empty((chunk, nvb, 3), dtype=torch.float64, pin_memory=True) for _ in range(2)]
-    Vb = [torch.empty_like(Xb[0]) for _ in range(2)]
-    Fb = [torch.empty_like(Xb[0]) for _ in range(2)]
+    Vb = [torch.empty((chunk, nvb, 3), dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    Fb = [torch.empty((chunk, nvb, 3), dtype=torch.float64, pin_memory=True) for _ in range(2)]
     ready = [torch.cuda.Event() for _ in range(2)]
     Xh = Xb[0][0]
     rho_h = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
