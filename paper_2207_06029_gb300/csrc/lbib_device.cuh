@@ -137,8 +137,8 @@ struct Pop<__nv_bfloat16, float> {
 };
 
 // Random bits for stochastic rounding from a counter: lowbias32 (the
-// integer hash of C. Wellons' "Prospecting for Hash Functions", 2018) seeds
-// a xorshift32 stream (G. Marsaglia, "Xorshift RNGs", 2003) per cell.
+// integer hash of C. Wellons' "Prospecting for Hash Functions", 2018) of the
+// cell index and the step's seed starts a Weyl sequence per cell (sr_draw).
 __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352du;
@@ -147,12 +147,10 @@ __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
-__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
-    x ^= x << 13;
-    x ^= x >> 17;
-    x ^= x << 5;
-    return x;
-}
+// Draw k of a cell: base + k * 0x9E3779B9 (the golden-ratio increment is
+// odd, so each 16-bit half of the draws steps through its range without
+// repeats); the hashed base makes each draw uniform across cells and steps.
+__device__ __forceinline__ uint32_t sr_draw(uint32_t base, int k) { return base + (uint32_t)k * 0x9E3779B9u; }
 
 // ---- views passed by value to kernels ----
 // Scalar parameters exist in both precisions so that the FP32 kernels never

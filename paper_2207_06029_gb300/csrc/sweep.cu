@@ -301,13 +301,12 @@ __device__ __forceinline__ void sweep_cell(const S *__restrict__ fin, S *__restr
     // 16 bits for i, its low 16 bits for the opposite direction)
     constexpr bool kSR = std::is_same<S, __nv_bfloat16>::value;
     if constexpr (kSR) {
-        uint32_t rs = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u;
-        rs = xorshift32(rs);
-        Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, 0, idx), g[0], rs >> 16);
+        const uint32_t base = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed));
+        Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, 0, idx), g[0], sr_draw(base, 0) >> 16);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int i = pair_rep(k), o = opp(i);
-            rs = xorshift32(rs);
+            const uint32_t rs = sr_draw(base, k + 1);
             Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, i, idx), g[i], rs >> 16);
             Pop<S, R>::st_sr_bits(plane_ptr<kOff32>(fout, L, o, idx), g[o], rs & 0xFFFFu);
         }
@@ -498,13 +497,12 @@ __global__ void __launch_bounds__(512) k_sweep_tile(const S *__restrict__ fin, S
         const long long idx = x + (long long)y * nx + (long long)z * nxy;
         S *row = sm + r * nx + x;  // value of direction i at row[i * rows * nx]
         if constexpr (kSR) {
-            uint32_t rs = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed)) | 1u;
-            rs = xorshift32(rs);
-            row[0] = Pop<S, R>::to_sr_bits(g[0], rs >> 16);
+            const uint32_t base = lowbias32((uint32_t)idx * 0x9E3779B9u ^ lowbias32(seed));
+            row[0] = Pop<S, R>::to_sr_bits(g[0], sr_draw(base, 0) >> 16);
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
                 const int i = pair_rep(k), o = opp(i);
-                rs = xorshift32(rs);
+                const uint32_t rs = sr_draw(base, k + 1);
                 row[i * rows * nx] = Pop<S, R>::to_sr_bits(g[i], rs >> 16);
                 row[o * rows * nx] = Pop<S, R>::to_sr_bits(g[o], rs & 0xFFFFu);
             }
