@@ -79,3 +79,35 @@ def test_measured_fma_rates_are_positive_and_fp64_is_the_slower(libpath):
     from paper_2207_06029_gb300 import lbib
     f64, f32 = lbib.lbib_measure_fma(True), lbib.lbib_measure_fma(False)
     assert 0.0 < f64 < f32
+
+
+STRUCTS = ["lbib_params", "lbib_body_params", "lbib_body_state", "lbib_serve_params", "lbib_serve_times",
+           "lbib_serve_summary"]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the header's field names,
+    offsets and size, as gcc lays out include/lbib.h (a field added to the
+    header but not to the binding would shift every later field)."""
+    import ctypes
+    from paper_2207_06029_gb300 import lbib as L
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbib.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(L, name)._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    want = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        want[(s, f)] = int(v)
+    for name in STRUCTS:
+        cls = getattr(L, name)
+        assert ctypes.sizeof(cls) == want[(name, "size")], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == want[(name, field)], (name, field)
