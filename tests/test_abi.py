@@ -65,6 +65,17 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
         lbib.lbib_create(p)
 
 
+def test_serve_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
+    """Server parameters are checked before the worker, stream or device are
+    touched: no budget, no active slot, an unknown mode or batch order."""
+    from paper_2207_06029_gb300 import lbib
+    for kw in [dict(hbm_budget=0), dict(hbm_budget=1 << 30, max_active=0), dict(hbm_budget=1 << 30, mode=2),
+               dict(hbm_budget=1 << 30, batch_order=2), dict(hbm_budget=1 << 30, batch_order=-1)]:
+        with pytest.raises(lbib.LbibError) as ei:
+            lbib.lbib_serve_create(**kw)
+        assert ei.value.code == lbib.LBIB_EINVAL, kw
+
+
 def test_measure_fma_rejects_a_null_output_without_touching_the_gpu(libpath):
     from paper_2207_06029_gb300 import lbib
     import ctypes as C
