@@ -46,7 +46,7 @@ enum {
     LBIB_EINVAL = -1,      /* invalid argument or parameter */
     LBIB_ENOMEM = -2,      /* device or host allocation failed */
     LBIB_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
-    LBIB_EDIVERGED = -4,   /* reserved: non-finite state detected */
+    LBIB_EDIVERGED = -4,   /* the run diverged (see lbib_set_watchdog) */
     LBIB_EBODY_WALL = -5,  /* an MLS support (marker or probe) reached a wall node */
     LBIB_ETIMEOUT = -6,    /* reserved: a bounded device wait expired */
     LBIB_ETOOBIG = -7      /* a size exceeds a fixed maximum (lbib_mesh_measures_noalloc) */
@@ -144,6 +144,32 @@ int lbib_step(void *ctx, int nsteps);
 
 /* Waits for the context stream and reports device-side errors. */
 int lbib_sync(void *ctx);
+
+/* Divergence detection (no counterpart in the paper; an explicit scheme
+ * run outside its stability range produces NaN or runaway values, which
+ * must fail the run instead of finishing it silently).  The run fails with
+ * the sticky LBIB_EDIVERGED when:
+ *  - every step, on the device: a marker (or probe) coordinate is non-finite
+ *    or beyond 1e9, or a membrane vertex moves a lattice unit or more in one
+ *    step (lattice velocities stay far below the speed of sound 0.577);
+ *  - every `every` steps (a multiple of the context's step count; default
+ *    1000, 0 turns it off), after that step, a watchdog kernel reads the
+ *    whole lattice: some node's density is non-finite or not positive, or
+ *    its speed |u| reaches the lattice speed of sound 1/sqrt(3), or the
+ *    total mass, reduced in FP64 in a fixed order, differs from that of the
+ *    first check after lbib_create / lbib_set_fields / lbib_set_populations
+ *    by more than mass_tol relative (default 0.1).
+ * The error surfaces at the next synchronising call, like LBIB_EBODY_WALL;
+ * the state stays readable (lbib_get_*).  In a batch the watchdog of each
+ * context runs after the lbib_batch_step call during which its cadence
+ * fell.  Each check reads the populations once (76 B per node in FP32).
+ * LBIB_EINVAL for every < 0 or mass_tol <= 0. */
+int lbib_set_watchdog(void *ctx, int every, double mass_tol);
+
+/* Runs the watchdog check on the current state now (queued after the steps
+ * already queued), synchronises and returns the context's error:
+ * LBIB_EDIVERGED if this or an earlier check failed, LBIB_OK otherwise. */
+int lbib_check(void *ctx);
 
 /* Density and velocity u = (sum f e + f_lb/2)/rho of the last collision
  * (Sec. 2.1): rho[ncell], u[3*ncell]; either may be NULL.  Synchronises. */
@@ -321,7 +347,9 @@ const char *lbib_batch_last_error(const void *batch);
  * advances a single run steps it with lbib_step.  Finished runs
  * leave the batch, arrivals join it, and the batch is rebuilt (continuous
  * batching).  LBIB_SERVE_PLAIN instead runs one request at a time with
- * lbib_step, in arrival order.  A finished run's context stays resident (and
+ * lbib_step, in arrival order.  A run that diverges (lbib_set_watchdog, at
+ * its context's default cadence, and lbib_check when its steps are done)
+ * fails with LBIB_EDIVERGED and leaves the batch; the other runs go on.  A finished run's context stays resident (and
  * counts against the budget) until the caller takes it. */
 enum { LBIB_REQ_QUEUED = 0, LBIB_REQ_RUNNING = 1, LBIB_REQ_DONE = 2, LBIB_REQ_FAILED = 3 };
 enum { LBIB_SERVE_BATCHED = 0, LBIB_SERVE_PLAIN = 1 };
@@ -399,16 +427,23 @@ void lbib_serve_destroy(void *server);
  * X[3*nv] (vertex x, y, z) and tris[3*nt] (vertex indices of outward,
  * counter-clockwise triangles) are device arrays; out[2] (device) receives
  * the volume (sum over triangles of X0 . (X1 x X2) / 6) and the area.
- * Asynchronous on `stream` (a cudaStream_t, NULL = the default stream); the
- * caller owns every array.  A vertex index outside [0, nv) is skipped and
- * makes both outputs NaN.  nt = 0 gives zeros.
+ * Asynchronous on `stream` (a cudaStream_t); the caller owns every array.
+ * NULL means the legacy default stream, whose work synchronises implicitly
+ * with every blocking stream: a caller running while another thread
+ * captures a graph must pass a stream created with cudaStreamNonBlocking,
+ * or cudaStreamPerThread, or the implicit synchronisation invalidates that
+ * capture.  A vertex index outside [0, nv) is skipped and makes both
+ * outputs NaN.  nt = 0 gives zeros.
  *
  * Scratch: a 64 KiB file-scope device array (plus a counter), held on every
  * GPU that loads the library until the process exits, so nt is limited to
  * LBIB_NOALLOC_MAX_TRIS; larger nt returns LBIB_ETOOBIG, negative sizes or
- * NULL arrays LBIB_EINVAL, a failed CUDA call LBIB_ECUDA.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current: make that first call before any stream capture.
+ * NULL arrays LBIB_EINVAL, a failed CUDA call LBIB_ECUDA.  Every call looks
+ * up the array's device address in the current device's context
+ * (cudaGetSymbolAddress; nothing is cached, so a reset device is handled);
+ * the first call in a process may also load the library's device code, so
+ * make it before any stream capture.  Each call then issues one
+ * cudaMemsetAsync and one kernel launch on `stream`.
  * Every call shares the array (each clears its counter first), so calls
  * that overlap on the GPU -- on different streams, or from different host
  * threads -- race and must be serialised by the caller.  Allocates nothing:

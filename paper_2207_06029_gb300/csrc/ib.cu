@@ -151,7 +151,8 @@ struct MlsSmem {
 };
 
 // 1/d in FP64 from the FP32 reciprocal refined by two Newton steps
-// (relative error ~1e-7 -> ~1e-14 -> below the double rounding).
+// (relative error ~1e-7 -> ~1e-14 -> below the double rounding).  d must lie
+// in the FP32 normal range, or the seed is infinite or zero: callers bound it.
 __device__ __forceinline__ double recip64(double d) {
     double r = (double)__frcp_rn((float)d);
     r = fma(r, fma(-d, r, 1.0), r);
@@ -163,7 +164,14 @@ __device__ __forceinline__ double recip64(double d) {
 // triangle (00,01,02,03,11,12,13,22,23,33), as the adjugate over the
 // determinant, both from the 2x2 minors of the top and bottom row pairs
 // (a shallow dependency chain: FP64 latency, not throughput, limits this
-// per-point solve).  Returns false unless the determinant is positive.
+// per-point solve).  Returns false unless kMinDet < determinant < kMaxDet:
+// the bounds keep the FP32 seed of recip64 finite and normal.  An MLS moment
+// matrix has entries of at most 27 * 1.5^2 (weights <= 1, offsets <= 1.5),
+// so det < 4e7 always, and the centre node with the three nearer face
+// neighbours (all within 1.22 of the point: weights >= 5e-5, unit offsets)
+// keep det above ~1e-16; a determinant outside the bounds marks a singular
+// support.
+constexpr double kMinDet = 1e-30, kMaxDet = 1e30;
 __device__ bool spd_inverse4(const double *a, double *inv) {
     const double m00 = a[0], m01 = a[1], m02 = a[2], m03 = a[3];
     const double m11 = a[4], m12 = a[5], m13 = a[6], m22 = a[7], m23 = a[8], m33 = a[9];
@@ -181,7 +189,7 @@ __device__ bool spd_inverse4(const double *a, double *inv) {
     const double c1 = m02 * m23 - m03 * m22;
     const double c0 = m02 * m13 - m03 * m12;
     const double det = s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
-    if (!(det > 0.0)) return false;
+    if (!(det > kMinDet && det < kMaxDet)) return false;
     const double id = recip64(det);
     // rows of the adjugate (the matrix is symmetric, so is its inverse)
     inv[0] = (m11 * c5 - m12 * c4 + m13 * c3) * id;
@@ -287,8 +295,12 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                     sm.vol[lane] = v6;
                 }
             }
-            bool bad = false;
+            bool bad = false, diverged = false;
             for (int a = 0; a < 3; ++a) {
+                if (!(fabs(P[a]) < kMaxMarkerCoord)) {  // non-finite or runaway: flag, keep indices sane
+                    diverged = true;
+                    P[a] = 0.0;
+                }
                 int b = __double2int_rd(P[a] + 0.5);  // floor(X + 1/2)
                 if (L.bc[a] == kWall && (b - 1 < 1 || b + 1 > n[a] - 2)) {
                     bad = true;
@@ -298,7 +310,10 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                 sm.frac[lane][a] = P[a] - (double)b;
                 sm.fracR[lane][a] = R(sm.frac[lane][a]);
             }
-            if (bad) atomicCAS(err, 0, -5);
+            if (diverged)
+                atomicCAS(err, 0, kErrDiverged);
+            else if (bad)
+                atomicCAS(err, 0, kErrBodyWall);
         }
     }
     __syncthreads();
@@ -703,6 +718,9 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
             const double ubdf = 1.5 * xt - 2.0 * x + 0.5 * xp;
             xn = x + ubdf + 0.5 * acc;
         }
+        // a vertex moving a lattice unit or more in one step (or a NaN) has
+        // diverged
+        if (!(fabs(xn - x) < kMaxMarkerStep)) atomicCAS(B.err, 0, kErrDiverged);
         B.Xnew[3 * vj + a] = xn;
         ((R *)B.Xrel_next)[3 * vj + a] = R(xn - B.origin[a]);
         B.Ub[3 * vj + a] = Ub;
@@ -1012,6 +1030,9 @@ __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyV
         B.Fl[3 * vj + a] = Fla;
         const double *xb = B.Xbody + 3 * vj;
         const double xn = xc[a] + Rn[3 * a] * xb[0] + Rn[3 * a + 1] * xb[1] + Rn[3 * a + 2] * xb[2];
+        // a marker moving a lattice unit or more in one step (or a NaN) has
+        // diverged
+        if (!(fabs(xn - B.X[3 * vj + a]) < kMaxMarkerStep)) atomicCAS(B.err, 0, kErrDiverged);
         B.Xnew[3 * vj + a] = xn;
         ((R *)B.Xrel_next)[3 * vj + a] = R(xn - B.origin[a]);
         sbox.add(a, xn);

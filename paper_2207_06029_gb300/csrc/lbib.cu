@@ -71,6 +71,9 @@ struct Ctx {
     uint32_t step_host = 0;      // host mirror of *d_step
     uint32_t *d_sr = nullptr;    // two-word seed counter of the stochastic rounding (bfloat16 storage)
     double *d_tot = nullptr;     // partials, counter and result of the FP64 mass/momentum totals
+    double *d_watch = nullptr;   // divergence watchdog: mass of its first check, mass of its last
+    int watch_every = 1000;      // watchdog cadence in steps (0: off)
+    double watch_tol = 0.1;      // relative total-mass drift the watchdog tolerates
     // CUDA graphs of one step, one per phase of the buffer rotation (period 6)
     cudaStream_t s_cap = nullptr;
     cudaGraphExec_t gexec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -324,7 +327,7 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.vol_sum = b.vol_sum;
     v.vh_verts = b.vh_verts;
     v.vh_par = b.vh_par;
-    (void)c;
+    v.err = c->d_err;
     return v;
 }
 
@@ -333,6 +336,10 @@ int check_device_error(Ctx *c) {
         c->err = *c->h_err;
         if (c->err == LBIB_EBODY_WALL)
             fail(c, c->err, "an MLS support (marker or probe) reached a wall node");
+        else if (c->err == LBIB_EDIVERGED)
+            fail(c, c->err,
+                 "the run diverged: a non-finite, non-positive or supersonic node, a mass drift beyond the "
+                 "watchdog tolerance, or a marker moving a lattice unit in one step");
         else
             fail(c, c->err, "device error %d (singular MLS moment matrix)", c->err);
     }
@@ -346,6 +353,21 @@ int sync_ctx(Ctx *c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
     return check_device_error(c);
+}
+
+// Errors after which the state can still be read (the run stopped, the
+// device is fine).
+bool readable_error(int rc) { return rc == LBIB_EBODY_WALL || rc == LBIB_EDIVERGED; }
+
+// Queues the divergence watchdog on the populations of the last step
+// (c->fA), on stream st.  Shares the totals scratch (same stream order).
+int enqueue_watch(Ctx *c, cudaStream_t st) {
+    const int n = totals_scratch_doubles();
+    unsigned int *count = reinterpret_cast<unsigned int *>(c->d_tot + (n - 4));
+    cudaError_t e = launch_watch(c->prec, c->fA, c->L, c->d_tot, count, c->d_watch, c->watch_tol, c->d_err, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "watchdog kernel");
+    return LBIB_OK;
 }
 
 double *get_scratch(Ctx *c, size_t bytes) {
@@ -502,7 +524,9 @@ int lbib_create(const lbib_params *p, void **out) {
     c->d_step = (uint32_t *)dev_alloc(c, sizeof(uint32_t));
     c->d_sr = (uint32_t *)dev_alloc(c, 2 * sizeof(uint32_t));
     c->d_tot = (double *)dev_alloc(c, sizeof(double) * (size_t)totals_scratch_doubles());
-    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step || !c->d_sr || !c->d_tot) {
+    c->d_watch = (double *)dev_alloc(c, 2 * sizeof(double));
+    if (!c->fA || !c->fB || !c->force || !c->fields || !c->mom || !c->stamp || !c->d_err || !c->d_step || !c->d_sr ||
+        !c->d_tot || !c->d_watch) {
         g_create_error = "device allocation failed";
         lbib_destroy(c);
         return LBIB_ENOMEM;
@@ -520,6 +544,8 @@ int lbib_create(const lbib_params *p, void **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sr, 0, 2 * sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_tot, 0, sizeof(double) * (size_t)totals_scratch_doubles(), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_watch, 0, 2 * sizeof(double), c->stream);
     if (e == cudaSuccess) e = prepare_kernels();
     if (e == cudaSuccess) e = prepare_sweep_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking);
@@ -582,6 +608,7 @@ int lbib_set_fields(void *h, const double *rho, const double *u, int on_device) 
     }
     cudaError_t e = launch_init_equilibrium(c->prec, c->fA, c->L, drho, du, c->fields, c->stream);
     c->launches++;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_watch, 0, 2 * sizeof(double), c->stream);  // new reference mass
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     if (!on_device) {
         e = cudaStreamSynchronize(c->stream);  // the host buffers may be freed after return
@@ -604,6 +631,7 @@ int lbib_set_populations(void *h, const double *f, int on_device) {
     }
     cudaError_t e = launch_aos_to_pop(c->prec, df, c->L, c->fA, c->stream);
     c->launches++;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_watch, 0, 2 * sizeof(double), c->stream);  // new reference mass
     if (e != cudaSuccess) return cuda_fail(c, e, "populations kernel");
     if (!on_device) {
         e = cudaStreamSynchronize(c->stream);
@@ -1084,8 +1112,30 @@ int lbib_step(void *h, int nsteps) {
             cudaStreamWaitEvent(c->stream, c->ev_join, 0);
         }
         c->steps++;
+        if (c->watch_every > 0 && c->steps % c->watch_every == 0) {
+            int rc = enqueue_watch(c, c->stream);
+            if (rc) return rc;
+        }
     }
     return LBIB_OK;
+}
+
+int lbib_set_watchdog(void *h, int every, double mass_tol) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (every < 0 || !(mass_tol > 0.0)) return fail(c, LBIB_EINVAL, "watchdog: every >= 0 and mass_tol > 0");
+    c->watch_every = every;
+    c->watch_tol = mass_tol;
+    return LBIB_OK;
+}
+
+int lbib_check(void *h) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (c->err) return c->err;
+    int rc = enqueue_watch(c, c->stream);
+    if (rc) return rc;
+    return sync_ctx(c);
 }
 
 int lbib_sync(void *h) {
@@ -1098,7 +1148,7 @@ int lbib_get_fields(void *h, double *rho, double *u, int on_device) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;
     int rc = sync_ctx(c);
-    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    if (rc && !readable_error(rc)) return rc;
     const size_t n = (size_t)c->L.ncell;
     double *drho = rho, *du = u;
     if (!on_device) {
@@ -1124,7 +1174,7 @@ int lbib_get_totals(void *h, double *out) {
     Ctx *c = as_ctx(h);
     if (!c || !out) return LBIB_EINVAL;
     int rc = sync_ctx(c);
-    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    if (rc && !readable_error(rc)) return rc;
     const int n = totals_scratch_doubles();
     double *part = c->d_tot, *res = c->d_tot + (n - 8);
     unsigned int *count = reinterpret_cast<unsigned int *>(c->d_tot + (n - 4));
@@ -1140,7 +1190,7 @@ int lbib_get_populations(void *h, double *f, int on_device) {
     Ctx *c = as_ctx(h);
     if (!c || !f) return LBIB_EINVAL;
     int rc = sync_ctx(c);
-    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    if (rc && !readable_error(rc)) return rc;
     const size_t n = (size_t)c->L.ncell * Q;
     double *df = f;
     if (!on_device) {
@@ -1163,7 +1213,7 @@ int lbib_get_markers_async(void *h, int body, double *X, double *V, double *F) {
     Ctx *c = as_ctx(h);
     if (!c) return LBIB_EINVAL;
     if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
-    if (c->err && c->err != LBIB_EBODY_WALL) return c->err;
+    if (c->err && !readable_error(c->err)) return c->err;
     DevBody &b = c->bodies[body];
     const size_t bytes = 3 * (size_t)b.nv * sizeof(double);
     cudaError_t e = cudaSuccess;
@@ -1190,7 +1240,7 @@ int lbib_step_markers(void *h, int nsteps, int body, double *X, double *V, doubl
     if (!c || nsteps < 0) return LBIB_EINVAL;
     if (body < 0 || body >= (int)c->bodies.size()) return fail(c, LBIB_EINVAL, "no such body");
     if (nsteps == 0) return LBIB_OK;
-    if (c->err && c->err != LBIB_EBODY_WALL) return c->err;
+    if (c->err && !readable_error(c->err)) return c->err;
     const size_t n3 = 3 * (size_t)c->bodies[body].nv;
     const size_t plane = n3 * (size_t)nsteps, need = 3 * plane * sizeof(double);
     if (need > c->mstage_bytes) {
@@ -1244,7 +1294,7 @@ int lbib_get_body(void *h, int body, lbib_body_state *out) {
     DevBody &b = c->bodies[body];
     std::vector<double> X(3 * (size_t)b.nv), Ub(3 * (size_t)b.nv);
     int rc = lbib_get_markers(h, body, X.data(), Ub.data(), nullptr);
-    if (rc && rc != LBIB_EBODY_WALL) return rc;
+    if (rc && !readable_error(rc)) return rc;
     std::memset(out, 0, sizeof(*out));
     if (b.rigid) {
         double st[RigidState::SIZE];
@@ -1858,6 +1908,15 @@ int lbib_batch_step(void *h, int nsteps) {
     }
     batch_advance_contexts(b, nsteps);
     b->total_steps += nsteps;
+    for (Ctx *c : b->ctx) {
+        // the watchdog of each context whose cadence fell inside these steps,
+        // on the state after them
+        if (c->watch_every > 0 && c->steps / c->watch_every != (c->steps - nsteps) / c->watch_every) {
+            int rc = enqueue_watch(c, b->stream);
+            if (rc) return bfail(b, rc, c->msg.c_str());
+            b->launches++;
+        }
+    }
     // later work on each context's stream runs after the batch
     cudaError_t e = cudaEventRecord(b->done, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "batch event");

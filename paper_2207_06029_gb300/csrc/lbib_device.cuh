@@ -240,7 +240,19 @@ struct BodyView {
     int nvol_part;
     unsigned int *vol_count; // blocks of the MLS kernel done (reset by the last one)
     double *vol_sum;        // enclosed volume times 6, written by the last MLS block
+    int *err;               // device error word of the context (first error wins)
 };
+
+// Device error codes (the values of include/lbib.h).
+constexpr int kErrDiverged = -4;   // LBIB_EDIVERGED
+constexpr int kErrBodyWall = -5;   // LBIB_EBODY_WALL
+// A marker moving farther than this in one step (lattice units; dt = 1) has
+// left the scheme's range: lattice Boltzmann velocities stay well below the
+// speed of sound c_s = 0.577, and the MLS support assumes sub-cell motion.
+constexpr double kMaxMarkerStep = 1.0;
+// Marker coordinates beyond this magnitude (or non-finite) count as
+// diverged; the bound keeps node arithmetic far inside int range.
+constexpr double kMaxMarkerCoord = 1e9;
 
 // ---- batches: the lattices of several contexts advanced by common launches ----
 // Buffers of one lattice in one phase of the six-step rotation.

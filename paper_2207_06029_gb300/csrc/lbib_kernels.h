@@ -41,6 +41,11 @@ cudaError_t prepare_sweep_kernels();
 cudaError_t launch_totals(int prec, const void *fin, const Lattice &L, double *part, unsigned int *count,
                           double *out, cudaStream_t s);
 int totals_scratch_doubles();
+// divergence watchdog: part and count as for launch_totals (shared with it,
+// same stream), w 2 doubles (reference mass, last mass), err the context's
+// error word
+cudaError_t launch_watch(int prec, const void *fin, const Lattice &L, double *part, unsigned int *count, double *w,
+                         double tol, int *err, cudaStream_t s);
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
                                     void *fields, cudaStream_t s);
 cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s);

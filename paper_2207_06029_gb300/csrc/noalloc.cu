@@ -11,7 +11,6 @@
 
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/lbib.h"
 
@@ -28,25 +27,17 @@ constexpr size_t kScratchBytes = kPartBytes + 256;               // + block coun
 // comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_mesh_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_mesh_scratch on the current device, looked up once
-// per device (with that device current).
+// Device address of g_mesh_scratch in the current context.  Looked up on
+// every call, never cached: a cached address would outlive a
+// cudaDeviceReset or any re-creation of the device's primary context.  The
+// lookup allocates nothing; only the first one in a process may load the
+// module (lazy loading), which is why the first call must precede any
+// stream capture.
 cudaError_t scratch_address(unsigned char **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mesh_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_mesh_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 

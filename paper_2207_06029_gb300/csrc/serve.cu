@@ -276,7 +276,9 @@ void worker_loop(Server *s) {
                 s->cell_updates += (double)chunk * r->p.nx * r->p.ny * r->p.nz;
             }
             if (r->remaining <= 0) {
-                finish(s, r, LBIB_OK);
+                // a finished run passes the divergence watchdog once more on
+                // its final state (its cadence may not have fallen on it)
+                finish(s, r, lbib_check(r->ctx));
                 stale = true;
             } else {
                 keep.push_back(r);

@@ -804,6 +804,90 @@ cudaError_t launch_totals(int prec, const void *fin, const Lattice &L, double *p
 
 int totals_scratch_doubles() { return 4 * kTotBlocks + 8; }
 
+// Divergence watchdog (not part of the method): every node's density must
+// be finite and positive and its speed below the lattice speed of sound
+// c_s = 1/sqrt(3) (the equilibrium of Eq. eqfunc is a low-Mach expansion: a
+// node past c_s has left the range of the scheme), and the total mass, summed
+// in FP64 in a fixed order as in k_totals, must stay within tol (relative)
+// of the mass of the first check.  A violation sets the error word to
+// LBIB_EDIVERGED unless an earlier error holds it.  w[0]: mass of the first
+// check (0 until taken), w[1]: mass of the last check; part: 2 doubles per
+// block (mass partial, bad-node flag); count starts and ends at zero.
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_watch(const S *__restrict__ fin, Lattice L, double *__restrict__ part,
+                                               unsigned int *__restrict__ count, double *__restrict__ w, double tol,
+                                               int *__restrict__ err) {
+    __shared__ double red[256];
+    __shared__ bool last;
+    double acc = 0.0;
+    bool bad = false;
+    const long long st = L.stride;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.ncell; idx += gridDim.x * blockDim.x) {
+        R m = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R gi = Pop<S, R>::ld(fin + (long long)i * st + idx);
+            m += gi;
+            if (ex(i)) jx += R(ex(i)) * gi;
+            if (ey(i)) jy += R(ey(i)) * gi;
+            if (ez(i)) jz += R(ez(i)) * gi;
+        }
+        const R rho = R(1) + m;
+        // written so that a NaN anywhere makes the test fail
+        const bool ok = rho > R(0) && rho < R(1e30) && R(3) * (jx * jx + jy * jy + jz * jz) < rho * rho;
+        bad = bad || !ok;
+        acc += (double)m;
+    }
+    bad = __syncthreads_or(bad) != 0;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = red[0];
+        part[2 * blockIdx.x + 1] = bad ? 1.0 : 0.0;
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double mass = 0.0, nbad = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        mass += __ldcg(part + 2 * b);
+        nbad += __ldcg(part + 2 * b + 1);
+    }
+    mass += (double)L.ncell;
+    const double m0 = w[0];
+    bool diverged = nbad > 0.0 || !(fabs(mass) < 1e300);
+    if (!diverged && m0 != 0.0) diverged = !(fabs(mass - m0) <= tol * fabs(m0));
+    if (!diverged && m0 == 0.0) w[0] = mass;
+    w[1] = mass;
+    if (diverged) atomicCAS(err, 0, kErrDiverged);
+    *count = 0u;
+}
+
+template <typename S, typename R>
+static cudaError_t watch_t(const void *fin, const Lattice &L, double *part, unsigned int *count, double *w,
+                           double tol, int *err, cudaStream_t s) {
+    int g = (L.ncell + 255) / 256;
+    if (g > kTotBlocks) g = kTotBlocks;
+    k_watch<S, R><<<g, 256, 0, s>>>((const S *)fin, L, part, count, w, tol, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_watch(int prec, const void *fin, const Lattice &L, double *part, unsigned int *count, double *w,
+                         double tol, int *err, cudaStream_t s) {
+    switch (prec) {
+        case 0: return watch_t<double, double>(fin, L, part, count, w, tol, err, s);
+        case 1: return watch_t<float, float>(fin, L, part, count, w, tol, err, s);
+        case 2: return watch_t<__half, float>(fin, L, part, count, w, tol, err, s);
+        default: return watch_t<__nv_bfloat16, float>(fin, L, part, count, w, tol, err, s);
+    }
+}
+
 // Kernel attributes set once before any launch or capture.
 cudaError_t prepare_sweep_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_sweep_tile<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

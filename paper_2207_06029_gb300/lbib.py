@@ -79,6 +79,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
+           "lbib_set_watchdog", "lbib_check",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_markers_async", "lbib_step_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
            "lbib_device_bytes", "lbib_save", "lbib_load", "lbib_mesh_measures_noalloc",
@@ -108,6 +109,8 @@ def load():
         L.lbib_add_body.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.POINTER(lbib_body_params), ip]
         L.lbib_step.argtypes = [vp, C.c_int]
         L.lbib_sync.argtypes = [vp]
+        L.lbib_set_watchdog.argtypes = [vp, C.c_int, C.c_double]
+        L.lbib_check.argtypes = [vp]
         L.lbib_get_fields.argtypes = [vp, vp, vp, C.c_int]
         L.lbib_get_populations.argtypes = [vp, vp, C.c_int]
         L.lbib_get_totals.argtypes = [vp, dp]
@@ -216,6 +219,14 @@ def lbib_step(ctx, nsteps):
 
 def lbib_sync(ctx):
     return _check(ctx, load().lbib_sync(ctx))
+
+
+def lbib_set_watchdog(ctx, every, mass_tol=0.1):
+    return _check(ctx, load().lbib_set_watchdog(ctx, int(every), float(mass_tol)))
+
+
+def lbib_check(ctx):
+    return _check(ctx, load().lbib_check(ctx))
 
 
 def lbib_get_fields(ctx, rho, u):
@@ -468,13 +479,36 @@ _NOALLOC_MESSAGES = {
 }
 
 
-def lbib_mesh_measures_noalloc(X, nv, tris, nt, out, stream=None):
+CUDA_STREAM_PER_THREAD = 2  # cudaStreamPerThread
+
+
+def lbib_mesh_measures_noalloc(X, nv, tris, nt, out, stream=CUDA_STREAM_PER_THREAD):
     """Volume and area of a closed mesh into out[2], allocating nothing.
-    X, tris and out are device pointers (ints) or CUDA tensors; stream is a
-    cudaStream_t handle (int) or None for the default stream."""
-    def addr(a):
-        return C.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a)
-    rc = load().lbib_mesh_measures_noalloc(addr(X), int(nv), addr(tris), int(nt), addr(out),
+    X (nv x 3 float64), tris (nt x 3 int32) and out (2 float64) are CUDA
+    tensors on the current device, contiguous, or raw device pointers
+    (ints, unchecked).  stream is a cudaStream_t handle (int); the default
+    is the per-thread default stream, which never synchronises implicitly
+    with other streams (None passes NULL, the legacy default stream)."""
+    import torch
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+
+    def addr(a, dtype, name):
+        if not hasattr(a, "data_ptr"):
+            return C.c_void_p(a)
+        if a.dtype != dtype or not a.is_cuda or not a.is_contiguous() or a.device.index != dev:
+            raise LbibError(LBIB_EINVAL, f"{name} must be a contiguous {dtype} CUDA tensor on device {dev} "
+                                         f"(got {a.dtype}, {a.device}, contiguous={a.is_contiguous()})")
+        return C.c_void_p(a.data_ptr())
+    pX = addr(X, torch.float64, "X")
+    pT = addr(tris, torch.int32, "tris")
+    pO = addr(out, torch.float64, "out")
+    if hasattr(X, "numel") and X.numel() < 3 * int(nv):
+        raise LbibError(LBIB_EINVAL, f"X holds {X.numel()} values, fewer than 3 * nv = {3 * int(nv)}")
+    if hasattr(tris, "numel") and int(nt) > 0 and tris.numel() < 3 * int(nt):
+        raise LbibError(LBIB_EINVAL, f"tris holds {tris.numel()} values, fewer than 3 * nt = {3 * int(nt)}")
+    if hasattr(out, "numel") and out.numel() < 2:
+        raise LbibError(LBIB_EINVAL, "out must hold 2 values")
+    rc = load().lbib_mesh_measures_noalloc(pX, int(nv), pT, int(nt), pO,
                                            C.c_void_p(stream) if stream else None)
     if rc != LBIB_OK:
         raise LbibError(rc, _NOALLOC_MESSAGES.get(rc, "error"))
