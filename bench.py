@@ -2,10 +2,13 @@
 """Benchmark: D3Q19 + dynamic-IB lattice updates per second on GB300.
 
 Workload (one step = the whole hot path: MLS interpolation at markers and
-hydrodynamic probes, membrane forces + Verlet + spreading, fused
-stream/wall/collide sweep): the 96^3 deformable-capsule Couette cell,
-tau 0.8, shear rate 1e-4, capsule radius 10 (2562 markers, 5120
-triangles), Ca 0.05, FP32 populations.  Prints one JSON line.
+hydrodynamic probes, structure forces + update + spreading, fused
+stream/wall/collide sweep): the largest single-GPU configuration, a rigid
+sphere (radius 8, 10242 markers) settling in a closed 160 x 160 x 480 box
+(12.3 M cells), tau 0.7, FP32 populations.  The line also carries the
+96^3 deformable-capsule Couette cell (tau 0.8, shear rate 1e-4, capsule
+radius 10, 2562 markers, Ca 0.05) measured the same way, under
+"capsule96".  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbib|reference]
 
@@ -33,6 +36,9 @@ sys.path.insert(0, ROOT)
 METRIC = "D3Q19+IB MLUPS & % HBM peak; served runs/h, p50/p99 latency vs plain"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
+# the end-to-end leg runs at least this many steps: a run's set-up (fields
+# from the host, mesh upload, graph capture) is paid once per run
+E2E_MIN_STEPS = 300
 
 
 WORKLOADS = {
@@ -189,10 +195,11 @@ def torch_allocator(torch):
     return lbib.ALLOC_FN(_alloc), lbib.FREE_FN(_free), live
 
 
-def run_gpu(args, rank, world):
+def run_gpu(args, rank, world, workload=None):
     import torch
 
     from paper_2207_06029_gb300 import lbib
+    workload = workload or args.workload
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -200,7 +207,7 @@ def run_gpu(args, rank, world):
     # L2 flush are all ordered on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    case = workload_case(args.workload)
+    case = workload_case(workload)
     alloc_fn, free_fn, live = torch_allocator(torch)
     params = lbib.make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
                               stream=stream.cuda_stream)
@@ -222,6 +229,10 @@ def run_gpu(args, rank, world):
         tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0, tuned[3], tuned[4])
     lbib.lbib_sync(h)
     lbib.lbib_set_output(h, -1)  # no macroscopic-field output inside the timed loop
+    # the launch configuration is final: capture the six phase graphs of the
+    # timed step (one per phase of the buffer rotation) before timing
+    lbib.lbib_step(h, 12)
+    lbib.lbib_sync(h)
     # L2 flush between timed steps: write a buffer larger than the 129 MB L2,
     # then read another one, so that the write-back of the flush's dirty
     # lines happens before the step and the step starts on a cold, clean L2
@@ -294,7 +305,7 @@ def run_gpu(args, rank, world):
     u_h = torch.empty(3 * ncell, dtype=torch.float64, pin_memory=True)
     rho_in = torch.from_numpy(rho0).pin_memory()
     u_in = torch.from_numpy(np.ascontiguousarray(u0.reshape(-1))).pin_memory()
-    e2e_steps = max(1, args.steps)
+    e2e_steps = max(args.steps, E2E_MIN_STEPS)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p2 = lbib.make_params(case.n, case.tau, bc=case.bc, wall_u=case.wall_u, precision=case.precision,
@@ -534,6 +545,80 @@ def cpu_baseline_one_core(seconds=6.0, workload="capsule96"):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def measured_line(args, r, world, ms, workload):
+    """The JSON line's figures for one measured workload (run_gpu's result r,
+    the slowest rank's timed milliseconds ms)."""
+    value = job_mlups(r["ncell"], args.steps, world, ms)
+    peak, peak_kind = hbm_peak()
+    fp64 = workload.endswith("fp64")
+    _, elem, ctype = storage(workload)
+    bytes_per_cell = 38.0 * elem  # 19 reads + 19 writes of one stored value per cell
+    bytes_per_launch = bytes_per_cell * r["ncell"]
+    achieved = bytes_per_launch / (r["iso_sweep_us"] * 1e-6) / 1e9
+    concurrent_s = r["sweep_ms"] * 1e-3 / max(r["nprof"], 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {8: "f64", 4: "fp32", 2: "fp32 (fp16/bf16 storage)"}[elem], "data": "synthetic",
+        "config": {"workload": WORKLOADS[workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
+                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
+                   "fields_output": "off in the timed loop (e2e reads them)",
+                   "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
+                                 "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
+                   "populations": ("fp64 deviations f_i - w_i, fp64 arithmetic" if fp64 else
+                                   f"{ctype} deviations f_i - w_i, fp32 arithmetic; markers and MLS solve fp64")},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(workload),
+                     "kernel": ("k_sweep_tile<{0},{1}> (shared-memory row tiles, 128-bit loads/stores)"
+                                if r["tuned"][3] else "k_sweep<{0},{1}>").format(ctype, "double" if fp64 else "float"),
+                     "peak_source": peak_kind, "sweep_us": r["iso_sweep_us"],
+                     "sweep_in_step_us": 1e6 * concurrent_s,
+                     "sweep_in_step_frac": bytes_per_launch / concurrent_s / 1e9 / peak,
+                     "mls_us_per_step": 1e3 * r["mls_ms"] / max(r["nprof"], 1),
+                     "structure_us_per_step": 1e3 * r["struct_ms"] / max(r["nprof"], 1),
+                     "step_us_per_step": 1e3 * r["step_ms"] / max(r["nprof"], 1),
+                     "note": f"achieved = {bytes_per_cell:.0f} B/cell x cells / the mean CUDA-event duration of the whole-lattice "
+                             "k_sweep launch (one per step, overlap off, L2 flushed before each step); "
+                             "sweep_in_step_* and the stage times come from a profiled loop of the tuned step, "
+                             "where the sweep runs as two launches, the far field concurrently with the IB "
+                             "stage"},
+        "e2e": {"value": r["ncell"] * r["e2e_steps"] * world / r["e2e_s"] / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"]),
+                "steps": r["e2e_steps"], "setup_ms": 1e3 * r["e2e_setup_s"],
+                "note": "context creation from host fields, mesh upload and graph capture included; the markers "
+                        "of every step staged on the device behind the step, copied to pinned host buffers after "
+                        "each chunk of ten steps and checked on the host while the next chunk runs; the fields "
+                        "read at the end"},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    if fp64:
+        # the FP64 sweep issues its arithmetic on GB300's narrow FP64 pipe:
+        # its roofline is the measured FP64 FMA rate, the FP64 operations per
+        # cell counted by ncu (committed summary) times the cells per launch
+        flop_cell = profile_figure(workload, "fp64_flop_per_cell")
+        inst_cell = profile_figure(workload, "fp64_inst_per_cell")
+        from paper_2207_06029_gb300 import lbib
+        fma64 = lbib.lbib_measure_fma(True)
+        # the pipe issues one FP64 instruction per slot: 2 flops as an FMA,
+        # 1 as an add or a multiply; the peak for the sweep's mix
+        peak = fma64 / 1e12 * (flop_cell / inst_cell / 2.0 if flop_cell and inst_cell else 1.0)
+        hbm = line["roofline"]
+        line["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                            "peak_source": "measured FP64 FMA rate (lbib_measure_fma) x the sweep's flop per "
+                                           "FP64 instruction / 2 (ncu instruction counts, committed summary)",
+                            "fma_tflops": fma64 / 1e12,
+                            "flop_per_cell": flop_cell, "kernel": hbm["kernel"], "sweep_us": r["iso_sweep_us"],
+                            "achieved": (flop_cell * r["ncell"] / (r["iso_sweep_us"] * 1e-6) / 1e12
+                                         if flop_cell else None),
+                            "traffic": None, "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
+        for k in ("sweep_in_step_us", "mls_us_per_step", "structure_us_per_step", "step_us_per_step"):
+            line["roofline"][k] = hbm[k]
+        line["roofline"]["frac"] = (line["roofline"]["achieved"] / line["roofline"]["peak"]
+                                    if flop_cell else None)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,7 +627,9 @@ def main():
     ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="capsule96", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="settling", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the 96^3 capsule figure beside the settling workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch configuration")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-lattices leg")
@@ -605,74 +692,13 @@ def main():
             torch.distributed.destroy_process_group()
         return
     ms = ms_all[0]
-    value = job_mlups(r["ncell"], args.steps, world, ms)
-    peak, peak_kind = hbm_peak()
-    fp64 = args.workload.endswith("fp64")
-    _, elem, ctype = storage(args.workload)
-    bytes_per_cell = 38.0 * elem  # 19 reads + 19 writes of one stored value per cell
-    bytes_per_launch = bytes_per_cell * r["ncell"]
-    achieved = bytes_per_launch / (r["iso_sweep_us"] * 1e-6) / 1e9
-    concurrent_s = r["sweep_ms"] * 1e-3 / max(r["nprof"], 1)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {8: "f64", 4: "fp32", 2: "fp32 (fp16/bf16 storage)"}[elem], "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "cells": r["ncell"], "markers": r["nv"], "triangles": r["nt"],
-                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
-                   "fields_output": "off in the timed loop (e2e reads them)",
-                   "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
-                                 "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
-                   "populations": ("fp64 deviations f_i - w_i, fp64 arithmetic" if fp64 else
-                                   f"{ctype} deviations f_i - w_i, fp32 arithmetic; markers and MLS solve fp64")},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
-                     "kernel": ("k_sweep_tile<{0},{1}> (shared-memory row tiles, 128-bit loads/stores)"
-                                if r["tuned"][3] else "k_sweep<{0},{1}>").format(ctype, "double" if fp64 else "float"),
-                     "peak_source": peak_kind, "sweep_us": r["iso_sweep_us"],
-                     "sweep_in_step_us": 1e6 * concurrent_s,
-                     "sweep_in_step_frac": bytes_per_launch / concurrent_s / 1e9 / peak,
-                     "mls_us_per_step": 1e3 * r["mls_ms"] / max(r["nprof"], 1),
-                     "structure_us_per_step": 1e3 * r["struct_ms"] / max(r["nprof"], 1),
-                     "step_us_per_step": 1e3 * r["step_ms"] / max(r["nprof"], 1),
-                     "note": f"achieved = {bytes_per_cell:.0f} B/cell x cells / the mean CUDA-event duration of the whole-lattice "
-                             "k_sweep launch (one per step, overlap off, L2 flushed before each step); "
-                             "sweep_in_step_* and the stage times come from a profiled loop of the tuned step, "
-                             "where the sweep runs as two launches, the far field concurrently with the IB "
-                             "stage"},
-        "e2e": {"value": r["ncell"] * r["e2e_steps"] * world / r["e2e_s"] / 1e6, "unit": UNIT,
-                "h2d_bytes_per_step": int(r["h2d"]), "d2h_bytes_per_step": int(r["d2h"]),
-                "steps": r["e2e_steps"], "setup_ms": 1e3 * r["e2e_setup_s"],
-                "note": "context creation from host fields, mesh upload and graph capture included; the markers "
-                        "of every step staged on the device behind the step, copied to pinned host buffers after "
-                        "each chunk of ten steps and checked on the host while the next chunk runs; the fields "
-                        "read at the end"},
-        "gpu_launches": r["launches"],
-        "clocks": r["clocks"],
-    }
-    if fp64:
-        # the FP64 sweep issues its arithmetic on GB300's narrow FP64 pipe:
-        # its roofline is the measured FP64 FMA rate, the FP64 operations per
-        # cell counted by ncu (committed summary) times the cells per launch
-        flop_cell = profile_figure(args.workload, "fp64_flop_per_cell")
-        inst_cell = profile_figure(args.workload, "fp64_inst_per_cell")
-        from paper_2207_06029_gb300 import lbib
-        fma64 = lbib.lbib_measure_fma(True)
-        # the pipe issues one FP64 instruction per slot: 2 flops as an FMA,
-        # 1 as an add or a multiply; the peak for the sweep's mix
-        peak = fma64 / 1e12 * (flop_cell / inst_cell / 2.0 if flop_cell and inst_cell else 1.0)
-        hbm = line["roofline"]
-        line["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-                            "peak_source": "measured FP64 FMA rate (lbib_measure_fma) x the sweep's flop per "
-                                           "FP64 instruction / 2 (ncu instruction counts, committed summary)",
-                            "fma_tflops": fma64 / 1e12,
-                            "flop_per_cell": flop_cell, "kernel": hbm["kernel"], "sweep_us": r["iso_sweep_us"],
-                            "achieved": (flop_cell * r["ncell"] / (r["iso_sweep_us"] * 1e-6) / 1e12
-                                         if flop_cell else None),
-                            "traffic": None, "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
-        for k in ("sweep_in_step_us", "mls_us_per_step", "structure_us_per_step", "step_us_per_step"):
-            line["roofline"][k] = hbm[k]
-        line["roofline"]["frac"] = (line["roofline"]["achieved"] / line["roofline"]["peak"]
-                                    if flop_cell else None)
+    line = measured_line(args, r, world, ms, args.workload)
+    if rank == 0 and world == 1 and args.workload == "settling" and args.extra:
+        # the 96^3 capsule, measured the same way, as a second figure
+        rc = run_gpu(args, rank, world, "capsule96")
+        lc = measured_line(args, rc, world, rc["ms"], "capsule96")
+        line["capsule96"] = {k: lc[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "e2e",
+                                               "gpu_launches", "clocks")}
     if rank == 0 and world == 1 and args.workload == "capsule96":
         line["roofline_large_lattice"] = large_sweep_leg(args)
     if args.batch and rank == 0 and world == 1:
