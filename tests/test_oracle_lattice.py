@@ -207,6 +207,34 @@ def test_corner_rule_at_rest(paper_e):
         assert np.abs(g - fe).max() < 1e-16
 
 
+@pytest.mark.parametrize("axes,signs", [((0, 2), (1, -1)), ((1, 2), (-1, 1)), ((0, 1), (-1, -1)),
+                                        ((0, 1, 2), (-1, 1, 1)), ((0, 1, 2), (1, -1, -1))])
+def test_corner_rule_moving_walls_keep_their_equilibrium(paper_e, axes, signs):
+    """Edge/corner rule with moving walls: each face moves tangentially with
+    its own velocity; when the known populations are at the equilibrium of
+    the mean wall velocity, f^eq(1, u_mean), the rule returns exactly that
+    equilibrium, so the node's density is 1 and its momentum u_mean.  Holds
+    because f^eq_i - f^eq_opp(i) = 6 w_i (e_i . u) (the odd part of Eq.
+    eqfunc) is the moving-wall bounce-back term, and buried links take
+    f^eq(1, u_mean) itself; a wrong sign or factor of that term, a sum in
+    place of the mean, or a wrong opposite fails it."""
+    rng = np.random.default_rng(60 + len(axes) + 3 * axes[0])
+    uw = 0.03 * rng.standard_normal((len(axes), 3))
+    for j, a in enumerate(axes):
+        uw[j, a] = 0.0  # tangential motion of face j
+    um = uw.mean(axis=0)
+    fe = oracle.feq(1.0, um)
+    f = fe.copy()
+    unknown = np.zeros(19, bool)
+    for a, s in zip(axes, signs):
+        unknown |= s * paper_e[:, a] > 0
+    f[unknown] = -5.0
+    g = oracle.wall_multi(f, axes, signs, uw.ravel())
+    assert np.abs(g - fe).max() < 1e-16
+    assert abs(g.sum() - 1.0) < 1e-15
+    assert np.abs(paper_e.T @ g - um).max() < 1e-16
+
+
 @pytest.mark.parametrize("tau", [1.0, 0.8, 0.6])
 def test_couette_linear_profile_is_exact(tau):
     """Linear shear between z walls moving at -+U is an exact discrete steady
