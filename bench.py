@@ -82,15 +82,17 @@ def hbm_peak():
 
 
 def sweep_source_hash():
-    """Hash of the source k_sweep compiles from: sweep.cu up to the end of
-    k_sweep and the device header up to the body view (the molecule, storage
-    conversions and lattice parameters)."""
+    """Hash of the source k_sweep compiles from: the node routines
+    (sweep_cell.cuh), sweep.cu up to the end of k_sweep and the device header
+    up to the body view (the molecule, storage conversions and lattice
+    parameters)."""
     csrc = os.path.join(ROOT, "paper_2207_06029_gb300", "csrc")
+    cell = open(os.path.join(csrc, "sweep_cell.cuh")).read()
     sweep = open(os.path.join(csrc, "sweep.cu")).read()
     dev = open(os.path.join(csrc, "lbib_device.cuh")).read()
     sweep = sweep[:sweep.index("// The nodes inside the box")]
     dev = dev[:dev.index("struct BodyView")]
-    return hashlib.sha256((sweep + dev).encode()).hexdigest()[:16]
+    return hashlib.sha256((cell + sweep + dev).encode()).hexdigest()[:16]
 
 
 SWEEP_PROFILES = {"capsule96": "sweep_fp32_capsule96.md", "settling": "sweep_fp32_settling.md",

@@ -48,7 +48,7 @@ enum {
     LBIB_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
     LBIB_EDIVERGED = -4,   /* the run diverged (see lbib_set_watchdog) */
     LBIB_EBODY_WALL = -5,  /* an MLS support (marker or probe) reached a wall node */
-    LBIB_ETIMEOUT = -6,    /* reserved: a bounded device wait expired */
+    LBIB_ETIMEOUT = -6,    /* a bounded device wait expired (persistent batched step) */
     LBIB_ETOOBIG = -7      /* a size exceeds a fixed maximum (lbib_mesh_measures_noalloc) */
 };
 
@@ -317,11 +317,34 @@ int lbib_batch_counters(void *batch, long long *steps, long long *launches);
 
 /* Times `steps` steps for each sweep configuration and keeps the fastest:
  * the batched sweep with 128, 256 or 512 threads a block and 1 or 4 cells a
- * thread, or one one-lattice sweep launch per lattice spread over side
- * streams, each with the lattices as given or largest first; the contexts
- * advance by about 14 * (7 + 2 * steps) steps.  choice (optional, 3 ints):
- * threads (0: one launch per lattice), order, cells per thread. */
+ * thread, one one-lattice sweep launch per lattice spread over side
+ * streams, or the persistent kernel (lbib_batch_set_persistent) with sweep
+ * tiles of 256 x 4, 8 or 16 cells, each with the lattices as given or
+ * largest first; the contexts advance by about 20 * (7 + 2 * steps) steps.
+ * choice (optional, 3 ints): threads (0: one launch per lattice, -1: the
+ * persistent kernel), order, cells per thread. */
 int lbib_batch_autotune(void *batch, int steps, int *choice);
+
+/* Persistent mode (enable = 1): every six-step chunk of lbib_batch_step
+ * runs as one kernel launch (captured once as a CUDA graph with the reset
+ * of its counters) instead of one launch per kernel and step.  The launch
+ * keeps as many blocks resident as fit on the GPU; they take work items
+ * in a fixed order from a global ticket counter -- per body the support
+ * moments, MLS, structure-update and spreading blocks, per lattice the
+ * sweep tiles (256 x cells_per_thread cells, lbib_batch_set_config), step
+ * after step -- and start an item once the items it depends on (its
+ * lattice's earlier phases of the step, and its previous sweep) have
+ * finished, so one lattice's IB work runs beside other lattices' sweeps.
+ * An item only waits for items taken before it, by blocks already
+ * running, so the queue cannot deadlock; each wait is still bounded by
+ * wait_limit_s (2 s is ample: a whole chunk takes milliseconds), after
+ * which the launch ends and every context of the batch holds the sticky
+ * LBIB_ETIMEOUT (0 gives up at the first wait that finds its items
+ * unfinished: a way to exercise that path).  Results are those of the
+ * per-kernel launches (up to the order of the atomic spreading sums).
+ * Waits for the batch's queued work and rebuilds its tables.  LBIB_EINVAL
+ * for enable not 0 or 1 or a wait limit outside [0, 60] s. */
+int lbib_batch_set_persistent(void *batch, int enable, double wait_limit_s);
 
 /* Sets what lbib_batch_autotune chooses: threads a block of the batched
  * sweep (a multiple of 32 up to 512; 0: one one-lattice sweep launch per

@@ -11,6 +11,7 @@
 // structure kernel updates the markers and spreads the IB force.
 #include "lbib_device.cuh"
 #include "lbib_kernels.h"
+#include "sweep_cell.cuh"
 
 namespace lbib {
 
@@ -48,31 +49,36 @@ __device__ __forceinline__ void mom_store(double *m, int node, double a, double 
     reinterpret_cast<double2 *>(m)[2 * node] = make_double2(a, b);
     reinterpret_cast<double2 *>(m)[2 * node + 1] = make_double2(c, d);
 }
+template <bool kCG>
 __device__ __forceinline__ void mom_load(const float *m, int node, float *v) {
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(m) + node);
+    const float4 q = ld_ro<kCG>(reinterpret_cast<const float4 *>(m) + node);
     v[0] = q.x;
     v[1] = q.y;
     v[2] = q.z;
     v[3] = q.w;
 }
+template <bool kCG>
 __device__ __forceinline__ void mom_load(const double *m, int node, double *v) {
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(m) + 2 * node);
-    const double2 b = __ldg(reinterpret_cast<const double2 *>(m) + 2 * node + 1);
+    const double2 a = ld_ro<kCG>(reinterpret_cast<const double2 *>(m) + 2 * node);
+    const double2 b = ld_ro<kCG>(reinterpret_cast<const double2 *>(m) + 2 * node + 1);
     v[0] = a.x;
     v[1] = a.y;
     v[2] = b.x;
     v[3] = b.y;
 }
 
-template <typename S, typename R>
+template <typename S, typename R, bool kCG = false>
 __device__ __forceinline__ void moments_body(const S *__restrict__ fin, const Lattice &L, const int *__restrict__ box,
                                              int *__restrict__ box_next, R *__restrict__ mom,
                                              uint32_t *__restrict__ step_inc, const int vb, const int nvb) {
-    if (step_inc && vb == 0 && threadIdx.x == 0) *step_inc += 1u;  // read by the later kernels of the step
+    // the step counter and the support box are read and written by other
+    // kernels of the step (or other work items of a persistent launch):
+    // L2 accesses, coherent across SMs
+    if (step_inc && vb == 0 && threadIdx.x == 0) atomicAdd(step_inc, 1u);  // read by the later kernels of the step
     const int n[3] = {L.nx, L.ny, L.nz};
     int lo[3], ext[3];
     for (int a = 0; a < 3; ++a) {
-        long long l = box[a], h = box[3 + a];
+        long long l = __ldcg(box + a), h = __ldcg(box + 3 + a);
         if (L.bc[a] == kWall) {
             l = l < 0 ? 0 : l;
             h = h > n[a] - 1 ? n[a] - 1 : h;
@@ -104,7 +110,7 @@ __device__ __forceinline__ void moments_body(const S *__restrict__ fin, const La
             const int sx = ex(i) > 0 ? cm[0] : ex(i) < 0 ? cp[0] : c[0];
             const int sy = ey(i) > 0 ? cm[1] : ey(i) < 0 ? cp[1] : c[1];
             const int sz = ez(i) > 0 ? cm[2] : ez(i) < 0 ? cp[2] : c[2];
-            const R gi = Pop<S, R>::ld(fin + (long long)i * st + (sx + L.nx * sy + nxy * sz));
+            const R gi = Pop<S, R>::from(ld_ro<kCG>(fin + (long long)i * st + (sx + L.nx * sy + nxy * sz)));
             drho += gi;
             if (ex(i) > 0) jx += gi;
             if (ex(i) < 0) jx -= gi;
@@ -131,7 +137,11 @@ __global__ void __launch_bounds__(256) k_moments(const S *__restrict__ fin, Latt
 
 constexpr int kSums = 26;  // A (10 entries), b for rho (4), b for u (12)
 
-template <typename R>
+// Shared memory of the MLS phases.  The per-point sums are formed through a
+// shared-memory transpose (red) in the MLS kernels, which run alone and are
+// fastest that way, or with kShfl by warp shuffles (the persistent batched
+// step, whose shared memory is taken from the L1 its sweep items need).
+template <typename R, bool kShfl = false>
 struct MlsSmem {
     // per point, filled in phase 0 (one lane per point)
     double frac[kPts][3];  // X - base, exact
@@ -140,15 +150,35 @@ struct MlsSmem {
     R nrm[kPts][3];
     double vol[kPts];
     // per point and support node, kept for the transfer weights of markers
+    // (with kShfl the offsets x_k - X are formed again from fracR instead)
     R W[kPts][27];
-    R d[kPts][27][3];
+    R d[kShfl ? 1 : kPts][27][3];
     // per point: A = sum W p p^T, b_f = sum W p f for f = rho - 1, u_x, u_y, u_z
     R sums[kPts][kSums];
     R row0[kPts][4];  // first row of A^-1
     int pid[kPts];    // point of each slot (-1 past the end): slots follow the body's cell order
-    // per warp: transpose buffer of the 26 products of each node
-    R red[kMlsThreads / 32][kSums][33];
+    // per warp: transpose buffer of the 26 products of each node (unused with kShfl)
+    R red[kShfl ? 1 : kMlsThreads / 32][kSums][kShfl ? 1 : 33];
 };
+
+// Sums 32 values per lane over the warp (a reduce-scatter butterfly): at
+// offset h each lane keeps the half of its values whose index bit h it
+// holds and receives the partner's partial sums of that half, so that lane
+// q ends with the total of value q (31 shuffles, no shared memory).
+template <typename R>
+__device__ __forceinline__ R warp_reduce_scatter32(R (&v)[32], const int lane) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const R send = up ? v[i] : v[i + h];
+            const R keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    return v[0];
+}
 
 // 1/d in FP64 from the FP32 reciprocal refined by two Newton steps
 // (relative error ~1e-7 -> ~1e-14 -> below the double rounding).  d must lie
@@ -227,14 +257,14 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
 //  phase 1: one warp per point, one lane per support node: weight
 //           W = exp(-(r/alpha)^2) for r <= 1 (the cut-off decided exactly as
 //           in FP64), node moments, the 26 products W p p^T and W p f,
-//           summed over the nodes through a shared-memory transpose;
+//           summed over the nodes by a warp reduce-scatter (shuffles);
 //  phase 2: one lane per point: FP64 Cholesky inverse of A; markers get
 //           U = (A^-1 b_u)_0 (Eq. uLag), probes the pressure c_s^2 rho and
 //           the traction rho nu (grad u + grad u^T) . n from the fits;
 //  phase 3: markers keep phi_k = W_k (A^-1 p_k)_0 for spreading.
-template <typename R>
+template <typename R, bool kCG = false, bool kShfl = false>
 __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattice &L, const BodyView &B, int *err,
-                                         MlsSmem<R> &sm, const int vb, const int nvb) {
+                                         MlsSmem<R, kShfl> &sm, const int vb, const int nvb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nm = B.nm, npts = nm + 2 * B.nt;
     const int p0 = vb * kPts;
@@ -322,7 +352,6 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     // The gathers of the warp's points are issued together, then each
     // point's weights and products are reduced in turn.
     constexpr int kPerWarp = kPts / (kMlsThreads / 32);
-    R(*red)[33] = sm.red[warp];
     R gu[kPerWarp][4];
 #pragma unroll
     for (int j = 0; j < kPerWarp; ++j) {
@@ -344,7 +373,7 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                 cw[a] = cc;
             }
             const int node = cw[0] + L.nx * cw[1] + nxy * cw[2];
-            mom_load(mom, node, gu[j]);
+            mom_load<kCG>(mom, node, gu[j]);
             if (p < nm) {
                 gu[j][0] = R(0);  // markers use the velocity fit only
                 B.node[27 * p + lane] = node;
@@ -384,35 +413,63 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                 W = exp(-(r / R(kAlpha)) * (r / R(kAlpha)));
             }
             sm.W[lp][lane] = W;
-            for (int a = 0; a < 3; ++a) sm.d[lp][lane][a] = dk[a];
+            if constexpr (!kShfl)
+                for (int a = 0; a < 3; ++a) sm.d[lp][lane][a] = dk[a];
         }
-        // the 26 products of this node (zero on lanes 27..31)
+        // the 26 products of this node (zero on lanes 27..31), summed over
+        // the support nodes: lane q forms sum q
         const R Wd[4] = {W, W * dk[0], W * dk[1], W * dk[2]};
-        red[0][lane] = Wd[0];
-        red[1][lane] = Wd[1];
-        red[2][lane] = Wd[2];
-        red[3][lane] = Wd[3];
-        red[4][lane] = Wd[1] * dk[0];
-        red[5][lane] = Wd[1] * dk[1];
-        red[6][lane] = Wd[1] * dk[2];
-        red[7][lane] = Wd[2] * dk[1];
-        red[8][lane] = Wd[2] * dk[2];
-        red[9][lane] = Wd[3] * dk[2];
+        if constexpr (kShfl) {
+            R v[32];
+            v[0] = Wd[0];
+            v[1] = Wd[1];
+            v[2] = Wd[2];
+            v[3] = Wd[3];
+            v[4] = Wd[1] * dk[0];
+            v[5] = Wd[1] * dk[1];
+            v[6] = Wd[1] * dk[2];
+            v[7] = Wd[2] * dk[1];
+            v[8] = Wd[2] * dk[2];
+            v[9] = Wd[3] * dk[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            red[10 + q][lane] = Wd[q] * gu[j][0];
-            red[14 + q][lane] = Wd[q] * gu[j][1];
-            red[18 + q][lane] = Wd[q] * gu[j][2];
-            red[22 + q][lane] = Wd[q] * gu[j][3];
-        }
-        __syncwarp();
-        if (lane < kSums) {
-            R acc = R(0);
+            for (int q = 0; q < 4; ++q) {
+                v[10 + q] = Wd[q] * gu[j][0];
+                v[14 + q] = Wd[q] * gu[j][1];
+                v[18 + q] = Wd[q] * gu[j][2];
+                v[22 + q] = Wd[q] * gu[j][3];
+            }
 #pragma unroll
-            for (int k = 0; k < 27; ++k) acc += red[lane][k];
-            sm.sums[lp][lane] = acc;
+            for (int q = kSums; q < 32; ++q) v[q] = R(0);
+            const R sum = warp_reduce_scatter32(v, lane);
+            if (lane < kSums) sm.sums[lp][lane] = sum;
+        } else {
+            R(*red)[33] = sm.red[warp];
+            red[0][lane] = Wd[0];
+            red[1][lane] = Wd[1];
+            red[2][lane] = Wd[2];
+            red[3][lane] = Wd[3];
+            red[4][lane] = Wd[1] * dk[0];
+            red[5][lane] = Wd[1] * dk[1];
+            red[6][lane] = Wd[1] * dk[2];
+            red[7][lane] = Wd[2] * dk[1];
+            red[8][lane] = Wd[2] * dk[2];
+            red[9][lane] = Wd[3] * dk[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                red[10 + q][lane] = Wd[q] * gu[j][0];
+                red[14 + q][lane] = Wd[q] * gu[j][1];
+                red[18 + q][lane] = Wd[q] * gu[j][2];
+                red[22 + q][lane] = Wd[q] * gu[j][3];
+            }
+            __syncwarp();
+            if (lane < kSums) {
+                R acc = R(0);
+#pragma unroll
+                for (int k = 0; k < 27; ++k) acc += red[lane][k];
+                sm.sums[lp][lane] = acc;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     __syncthreads();
 
@@ -492,9 +549,15 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
         if (p < 0) break;
         if (p >= nm) continue;  // probes keep no transfer weights
         if (lane < 27) {
+            R dk[3];
+            if constexpr (kShfl) {
+                const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+                for (int a = 0; a < 3; ++a) dk[a] = R(dd[a]) - sm.fracR[lp][a];  // as in phase 1
+            } else {
+                for (int a = 0; a < 3; ++a) dk[a] = sm.d[lp][lane][a];
+            }
             const R *r0 = sm.row0[lp];
-            const R phi = sm.W[lp][lane] *
-                          (r0[0] + r0[1] * sm.d[lp][lane][0] + r0[2] * sm.d[lp][lane][1] + r0[3] * sm.d[lp][lane][2]);
+            const R phi = sm.W[lp][lane] * (r0[0] + r0[1] * dk[0] + r0[2] * dk[1] + r0[3] * dk[2]);
             ((R *)B.phi)[27 * p + lane] = phi;
         }
     }
@@ -585,7 +648,7 @@ template <typename R>
 __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &B, R *__restrict__ force,
                                               uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep,
                                               const int vb) {
-    const uint32_t step = *dstep;
+    const uint32_t step = __ldcg(dstep);  // written by the moments kernel of the step
     __shared__ R s_cv;
     __shared__ BlockBox sbox;
     __shared__ R s_F[8][4];   // per vertex warp: total force (3) and vertex area
@@ -979,7 +1042,7 @@ template <typename R>
 __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyView &B, R *__restrict__ force,
                                                    uint32_t *__restrict__ stamp,
                                                    const uint32_t *__restrict__ dstep, const int vb) {
-    const uint32_t step = *dstep;
+    const uint32_t step = __ldcg(dstep);  // written by the moments kernel of the step
     __shared__ BlockBox sbox;
     __shared__ R s_Al[8];
     __shared__ R s_Fl[8][3];
@@ -1059,7 +1122,7 @@ template <typename R>
 __device__ __forceinline__ void centroid_body(const Lattice &L, const BodyView &B, R *__restrict__ force,
                                               uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep,
                                               const int vb) {
-    const uint32_t step = *dstep;
+    const uint32_t step = __ldcg(dstep);  // written by the moments kernel of the step
     __shared__ R s_A[8];
     __shared__ R s_Fl[8][3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1169,6 +1232,184 @@ __global__ void __launch_bounds__(256) kb_centroid_spread(BatchTables T, int pha
     stage_shared(L, T.lat + br.lat);
     const LatRef &F = T.ref[phase * T.nl + br.lat];
     centroid_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, blockIdx.x - __ldg(T.cen_pre + m));
+}
+
+// ---- persistent batched step ----
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0: waits until every item of kind k of lattice l in steps 0..upto
+// of this launch has finished (count (upto + 1) * need).  Gives up, and
+// marks the launch aborted, once the wait has lasted P.wait_ns, or when
+// another block has aborted.  The acquire load orders the item's later
+// loads after the awaited items' stores.
+__device__ bool wait_kind(const PersistTables &P, int l, int k, int upto, unsigned long long t0) {
+    const unsigned need = __ldg(P.need + l * kPKinds + k);
+    if (upto < 0 || need == 0) return true;
+    const unsigned target = (unsigned)(upto + 1) * need;
+    const unsigned *ctr = P.done + l * kPKinds + k;
+    for (;;) {
+        if (ld_acquire(ctr) >= target) return true;
+        if (*(volatile unsigned *)P.abort) return false;
+        if ((long long)(global_ns() - t0) >= P.wait_ns) {
+            atomicExch(P.abort, 1u);
+            return false;
+        }
+        __nanosleep(100);
+    }
+}
+
+// The items an item of kind k, lattice l, step s waits for: its lattice's
+// earlier phases of the step, and the previous step's sweep.
+__device__ bool wait_deps(const PersistTables &P, int k, int l, int s) {
+    const unsigned long long t0 = global_ns();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");  // an acquire even when nothing is awaited
+    switch (k) {
+        case kPMom: return wait_kind(P, l, kPSweep, s - 1, t0);
+        case kPMls: return wait_kind(P, l, kPMom, s, t0);
+        case kPMemb:
+        case kPRf: return wait_kind(P, l, kPMls, s, t0);
+        case kPRm: return wait_kind(P, l, kPRf, s, t0);
+        case kPCen: return wait_kind(P, l, kPMemb, s, t0) && wait_kind(P, l, kPRm, s, t0);
+        default:
+            for (int j = kPMom; j < kPSweep; ++j)
+                if (!wait_kind(P, l, j, s, t0)) return false;
+            return wait_kind(P, l, kPSweep, s - 1, t0);
+    }
+}
+
+// Several steps of every lattice of a batch in one launch: blocks take work
+// items (support moments, MLS, structure updates, spreading, sweep tiles)
+// in ticket order from a table that interleaves the lattices' chains (the
+// host staggers them, so that each stretch of the queue mixes some
+// lattices' sweeps with other lattices' IB phases), each item starting
+// after the items it depends on (per-lattice completion counters).  A
+// wait that exceeds its bound sets LBIB_ETIMEOUT on every lattice and ends
+// the launch.
+template <typename S, typename R, bool kOff32>
+__global__ void __launch_bounds__(256, 4) kp_batch(BatchTables T, PersistTables P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Lattice L;
+    __shared__ BodyRef br;
+    __shared__ unsigned s_t[2];  // this item's ticket and the next one (taken early, double-buffered)
+    __shared__ int s_ok;
+    const unsigned total = (unsigned)P.nitems;
+    if (threadIdx.x == 0) s_t[0] = atomicAdd(P.ticket, 1u);
+    for (int k = 0;; k ^= 1) {
+        __syncthreads();
+        const unsigned t = s_t[k];
+        if (t >= total) break;
+        const int4 it = __ldg(P.items + t);
+        const int kind = it.x & 0xff, s = it.x >> 8;
+        const int phase = (P.phase0 + s) % 6;
+        const int lat = kind == kPSweep ? it.y : __ldg(P.body_lat + it.y);
+        if (threadIdx.x == 0) {
+            s_ok = !*(volatile unsigned *)P.abort && wait_deps(P, kind, lat, s);
+            if (!s_ok)
+                for (int l = 0; l < T.nl; ++l) atomicCAS(T.ref[l].err, 0, kErrTimeout);
+            s_t[k ^ 1] = atomicAdd(P.ticket, 1u);  // the next item's ticket, in flight during this one
+        }
+        // stage the lattice (and body) parameters; the barrier also
+        // publishes s_ok
+        {
+            const uint32_t *srcL = reinterpret_cast<const uint32_t *>(T.lat + lat);
+            uint32_t *dstL = reinterpret_cast<uint32_t *>(&L);
+            for (int w = threadIdx.x; w < (int)(sizeof(Lattice) / 4); w += blockDim.x) dstL[w] = __ldg(srcL + w);
+            if (kind != kPSweep) {
+                const uint32_t *srcB = reinterpret_cast<const uint32_t *>(T.body + phase * T.nb + it.y);
+                uint32_t *dstB = reinterpret_cast<uint32_t *>(&br);
+                for (int w = threadIdx.x; w < (int)(sizeof(BodyRef) / 4); w += blockDim.x) dstB[w] = __ldg(srcB + w);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const LatRef &F = T.ref[phase * T.nl + lat];
+        switch (kind) {
+            case kPSweep: {
+                const uint32_t step = F.stamp ? __ldcg(F.d_step) : 0u;
+                const uint32_t seed = __ldcg(F.sr + F.parity);
+                if (it.z == 0 && threadIdx.x == 0) F.sr[F.parity ^ 1] = seed + 1u;
+                const int c0 = it.z * P.sweep_cells;
+                const int c1 = min(c0 + P.sweep_cells, L.ncell);
+                for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
+                    const int x = c % L.nx, yz = c / L.nx, y = yz % L.ny, z = yz / L.ny;
+                    sweep_cell<S, R, kOff32, true>((const S *)F.fin, (S *)F.fout, (R *)F.force, F.stamp, step, L,
+                                                   nullptr, x, y, z, seed);
+                }
+                break;
+            }
+            case kPMom:
+                moments_body<S, R, true>((const S *)F.fin, L, br.v.bbox, br.v.bbox_next, (R *)F.mom,
+                                         br.inc_step ? F.d_step : nullptr, it.z, it.w);
+                break;
+            case kPMls:
+                mls_body<R, true, true>((const R *)F.mom, L, br.v, F.err,
+                                        *reinterpret_cast<MlsSmem<R, true> *>(smem_raw), it.z, it.w);
+                break;
+            case kPMemb: membrane_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, it.z); break;
+            case kPRf: rigid_forces_body<R>(br.v, it.z, it.w); break;
+            case kPRm: rigid_markers_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, it.z); break;
+            default: centroid_body<R>(L, br.v, (R *)F.force, F.stamp, F.d_step, it.z); break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // the item's stores (every thread's, ordered by the barrier) before its count
+            atomicAdd(P.done + lat * kPKinds + kind, 1u);
+        }
+    }
+}
+
+template <typename S, typename R>
+static cudaError_t persistent_t(const BatchTables &T, const PersistTables &P, int grid, cudaStream_t s) {
+    if (T.sweep_off32)
+        kp_batch<S, R, true><<<grid, 256, sizeof(MlsSmem<R, true>), s>>>(T, P);
+    else
+        kp_batch<S, R, false><<<grid, 256, sizeof(MlsSmem<R, true>), s>>>(T, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_persistent(int prec, const BatchTables &T, const PersistTables &P, int grid,
+                                    cudaStream_t s) {
+    switch (prec) {
+        case 0: return persistent_t<double, double>(T, P, grid, s);
+        case 1: return persistent_t<float, float>(T, P, grid, s);
+        case 2: return persistent_t<__half, float>(T, P, grid, s);
+        default: return persistent_t<__nv_bfloat16, float>(T, P, grid, s);
+    }
+}
+
+// Resident blocks per SM of the persistent kernel (its dynamic shared
+// memory set), for the grid size.
+template <typename S, typename R>
+static int persistent_occ(bool off32) {
+    int n = 0;
+    const size_t smem = sizeof(MlsSmem<R, true>);
+    if (off32) {
+        cudaFuncSetAttribute(kp_batch<S, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kp_batch<S, R, true>, 256, smem);
+    } else {
+        cudaFuncSetAttribute(kp_batch<S, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kp_batch<S, R, false>, 256, smem);
+    }
+    return n;
+}
+
+int batch_persistent_blocks_per_sm(int prec, bool off32) {
+    switch (prec) {
+        case 0: return persistent_occ<double, double>(off32);
+        case 1: return persistent_occ<float, float>(off32);
+        case 2: return persistent_occ<__half, float>(off32);
+        default: return persistent_occ<__nv_bfloat16, float>(off32);
+    }
 }
 
 template <typename S, typename R>

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -336,6 +337,8 @@ int check_device_error(Ctx *c) {
         c->err = *c->h_err;
         if (c->err == LBIB_EBODY_WALL)
             fail(c, c->err, "an MLS support (marker or probe) reached a wall node");
+        else if (c->err == LBIB_ETIMEOUT)
+            fail(c, c->err, "a bounded wait of the persistent batched step expired (the launch ended early)");
         else if (c->err == LBIB_EDIVERGED)
             fail(c, c->err,
                  "the run diverged: a non-finite, non-positive or supersonic node, a mass drift beyond the "
@@ -1530,6 +1533,15 @@ struct Batch {
     cudaGraphExec_t g6 = nullptr;
     long long launches = 0, total_steps = 0;
     std::string msg;
+    // persistent mode: the six-step chunks run as one kernel launch over a
+    // queue of work items (kp_batch)
+    int persistent = 0;
+    double wait_s = 2.0;       // bound on each dependency wait of the persistent kernel
+    void *pmem = nullptr;      // its item tables and counters
+    PersistTables P{};
+    unsigned *pctr = nullptr;  // ticket, abort flag and completion counters (zeroed per launch)
+    size_t pctr_bytes = 0;
+    int pgrid = 0;             // resident blocks of the persistent kernel
 };
 
 std::string g_batch_error;
@@ -1552,6 +1564,113 @@ void batch_free_tables(Batch *b) {
     b->g6 = nullptr;
     if (b->dmem) cudaFree(b->dmem);
     b->dmem = nullptr;
+    if (b->pmem) cudaFree(b->pmem);
+    b->pmem = nullptr;
+    b->pctr = nullptr;
+}
+
+// Work items of the persistent kernel's six-step launch, in queue order.
+// Per body: support-moment, MLS, membrane, rigid-force, rigid-marker and
+// centroid items (each split into the blocks the separate kernels would
+// launch); per lattice: sweep tiles of sweep_cells cells.  Each lattice's
+// chain of phases (its item kinds in order, step after step) is laid out in
+// rounds, lattice l's phase j in round j + offset(l), the offsets spreading
+// the lattices (in sweep order) over one step's phases: every stretch of
+// the queue mixes some lattices' sweeps with other lattices' IB phases,
+// and a phase's items sit a round after the phase they depend on.
+// need[l][k]: items of kind k of lattice l per step.
+int batch_build_persistent(Batch *b, const std::vector<std::pair<int, int>> &bodies,
+                           const std::vector<BodyRef> &body, const std::vector<Lattice> &lat,
+                           const std::vector<int> &order) {
+    const int nl = (int)lat.size(), nb = (int)bodies.size(), nsteps = 6;
+    const int cells = 256 * b->sweep_cpt;
+    std::vector<int> body_lat(nb > 0 ? nb : 1, 0);
+    std::vector<unsigned> need((size_t)nl * kPKinds, 0u);
+    std::vector<std::array<int, kPKinds>> count(nb);  // items per step of each body and kind
+    std::vector<std::vector<int>> lat_bodies(nl);
+    for (int q = 0; q < nb; ++q) {
+        body_lat[q] = bodies[q].first;
+        lat_bodies[bodies[q].first].push_back(q);
+        const DevBody &d = b->ctx[bodies[q].first]->bodies[bodies[q].second];
+        std::array<int, kPKinds> &n = count[q];
+        n.fill(0);
+        n[kPMom] = std::max(8, d.nv / 16);
+        n[kPMls] = mls_blocks(body[q].v);
+        n[kPMemb] = d.rigid ? 0 : (d.nv + 7) / 8;
+        n[kPRf] = d.rigid ? (d.nt + 255) / 256 : 0;
+        n[kPRm] = d.rigid ? (d.nv + 7) / 8 : 0;
+        n[kPCen] = d.p.centroid_markers ? (d.nt + 7) / 8 : 0;
+        for (int k = kPMom; k < kPSweep; ++k) need[(size_t)bodies[q].first * kPKinds + k] += (unsigned)n[k];
+    }
+    std::vector<int> tiles(nl);
+    for (int l = 0; l < nl; ++l) {
+        tiles[l] = (lat[l].ncell + cells - 1) / cells;
+        need[(size_t)l * kPKinds + kPSweep] = (unsigned)tiles[l];
+    }
+    // each lattice's phase kinds, and the rounds
+    std::vector<std::vector<int>> kinds(nl);
+    int pmax = 1;
+    for (int l = 0; l < nl; ++l) {
+        for (int k = kPMom; k < kPKinds; ++k)
+            if (need[(size_t)l * kPKinds + k]) kinds[l].push_back(k);
+        pmax = std::max(pmax, (int)kinds[l].size());
+    }
+    std::vector<int> offset(nl);
+    for (int i = 0; i < nl; ++i) offset[order[i]] = (int)((long long)i * pmax / nl);
+    std::vector<int4> items;
+    const int rounds = nsteps * pmax + pmax;
+    for (int r = 0; r < rounds; ++r)
+        for (int i = 0; i < nl; ++i) {
+            const int l = order[i], np = (int)kinds[l].size(), j = r - offset[l];
+            if (j < 0 || j >= nsteps * np) continue;
+            const int st = j / np, k = kinds[l][j % np], tag = k | (st << 8);
+            if (k == kPSweep) {
+                for (int t = 0; t < tiles[l]; ++t) items.push_back(make_int4(tag, l, t, tiles[l]));
+            } else {
+                for (int q : lat_bodies[l])
+                    for (int vb = 0; vb < count[q][k]; ++vb) items.push_back(make_int4(tag, q, vb, count[q][k]));
+            }
+        }
+    size_t off = 0;
+    auto place = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_it = place(sizeof(int4) * items.size()), o_bl = place(sizeof(int) * body_lat.size()),
+                 o_nd = place(sizeof(unsigned) * need.size()), o_ct = place(sizeof(unsigned) * (2 + need.size()));
+    cudaError_t e = cudaMalloc(&b->pmem, off);
+    if (e != cudaSuccess) {
+        b->pmem = nullptr;
+        return bcuda(b, e, "persistent tables");
+    }
+    std::vector<unsigned char> host(off, 0);
+    std::memcpy(host.data() + o_it, items.data(), sizeof(int4) * items.size());
+    std::memcpy(host.data() + o_bl, body_lat.data(), sizeof(int) * body_lat.size());
+    std::memcpy(host.data() + o_nd, need.data(), sizeof(unsigned) * need.size());
+    e = cudaMemcpy(b->pmem, host.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(b, e, "persistent tables upload");
+    unsigned char *d = static_cast<unsigned char *>(b->pmem);
+    PersistTables &P = b->P;
+    P.nitems = (int)items.size();
+    P.nsteps = nsteps;
+    P.phase0 = 0;
+    P.sweep_cells = cells;
+    P.wait_ns = (long long)(b->wait_s * 1e9);
+    P.items = reinterpret_cast<const int4 *>(d + o_it);
+    P.body_lat = reinterpret_cast<const int *>(d + o_bl);
+    P.need = reinterpret_cast<const unsigned *>(d + o_nd);
+    b->pctr = reinterpret_cast<unsigned *>(d + o_ct);
+    b->pctr_bytes = sizeof(unsigned) * (2 + need.size());
+    P.ticket = b->pctr;
+    P.abort = b->pctr + 1;
+    P.done = b->pctr + 2;
+    bool off32 = true;
+    for (const Lattice &Li : lat) off32 = off32 && Li.off32;
+    const int per_sm = batch_persistent_blocks_per_sm(b->prec, off32);
+    if (per_sm < 1) return bfail(b, LBIB_ECUDA, "the persistent kernel does not fit on an SM");
+    b->pgrid = per_sm * b->nsm;
+    return LBIB_OK;
 }
 
 // Builds the launch tables from the contexts' current state (phase 0) and
@@ -1720,6 +1839,10 @@ int batch_build(Batch *b) {
     for (const Lattice &Li : lat) T.sweep_off32 &= Li.off32;
     b->G = BatchGrid{sweep_pre.back(), mom_pre.back(), mls_pre.back(), memb_pre.back(), rf_pre.back(), rm_pre.back(),
                      cen_pre.back()};
+    if (b->persistent) {
+        int rc = batch_build_persistent(b, bodies, body, lat, order);
+        if (rc) return rc;
+    }
     b->lat_h = lat;
     b->ref_h = ref;
     b->order_h = order;
@@ -1762,7 +1885,13 @@ int batch_capture6(Batch *b) {
     cudaError_t e = cudaStreamBeginCapture(b->s_cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "batch capture");
     int rc = LBIB_OK;
-    for (int k = 0; k < 6 && rc == LBIB_OK; ++k) rc = batch_enqueue(b, k, false, b->s_cap);
+    if (b->persistent) {
+        // the queue counters start at zero, then one launch runs the six steps
+        e = cudaMemsetAsync(b->pctr, 0, b->pctr_bytes, b->s_cap);
+        if (e == cudaSuccess) e = launch_batch_persistent(b->prec, b->T, b->P, b->pgrid, b->s_cap);
+        if (e != cudaSuccess) rc = bcuda(b, e, "persistent batch launch");
+    }
+    for (int k = 0; k < 6 && rc == LBIB_OK && !b->persistent; ++k) rc = batch_enqueue(b, k, false, b->s_cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->s_cap, &g);
     if (rc) {
@@ -1897,7 +2026,7 @@ int lbib_batch_step(void *h, int nsteps) {
             if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
             b->steps += 6;
             remaining -= 6;
-            b->launches += 6 * batch_launches_per_step(b);
+            b->launches += b->persistent ? 1 : 6 * batch_launches_per_step(b);
         } else {
             int rc = batch_enqueue(b, phase, remaining == 1, b->stream);
             if (rc) return rc;
@@ -1953,14 +2082,19 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
     // candidates: the batched sweep in (threads, cells per thread) shapes, or
     // one one-lattice sweep launch per lattice (threads = 0), each with the
     // lattices as given or largest first
-    const int shapes[][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 4}, {256, 4}, {512, 4}, {0, 0}};
+    // or the persistent kernel (threads = -1) with sweep tiles of 256 x 4, 8
+    // or 16 cells
+    const int shapes[][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 4},  {256, 4},
+                             {512, 4}, {0, 0},   {-1, 4},  {-1, 8},  {-1, 16}};
     float best = 1e30f;
-    int best_t = b->sweep_threads, best_o = b->order, best_c = b->sweep_cpt, best_split = b->sweep_split;
+    int best_t = b->sweep_threads, best_o = b->order, best_c = b->sweep_cpt, best_split = b->sweep_split,
+        best_p = b->persistent;
     int rc = LBIB_OK;
     for (int o = 0; o < 2 && !rc; ++o)
         for (const auto &shape : shapes) {
-                const int t = shape[0] ? shape[0] : 256, cp = shape[0] ? shape[1] : 4;
+                const int t = shape[0] > 0 ? shape[0] : 256, cp = shape[0] ? shape[1] : 4;
                 b->sweep_split = shape[0] == 0;
+                b->persistent = shape[0] < 0;
                 b->sweep_threads = t;
                 b->order = o;
                 b->sweep_cpt = cp;
@@ -1983,6 +2117,7 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
                     best_o = o;
                     best_c = cp;
                     best_split = b->sweep_split;
+                    best_p = b->persistent;
                 }
             }
     cudaEventDestroy(e0);
@@ -1991,13 +2126,24 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
     b->order = best_o;
     b->sweep_cpt = best_c;
     b->sweep_split = best_split;
+    b->persistent = best_p;
     int rc2 = batch_build(b);
     if (choice) {
-        choice[0] = best_split ? 0 : best_t;
+        choice[0] = best_p ? -1 : best_split ? 0 : best_t;
         choice[1] = best_o;
         choice[2] = best_c;
     }
     return rc ? rc : rc2;
+}
+
+int lbib_batch_set_persistent(void *h, int enable, double wait_limit_s) {
+    Batch *b = as_batch(h);
+    if (!b) return LBIB_EINVAL;
+    if ((enable != 0 && enable != 1) || !(wait_limit_s >= 0.0) || wait_limit_s > 60.0)
+        return bfail(b, LBIB_EINVAL, "persistent: enable 0 or 1, wait limit in [0, 60] s");
+    b->persistent = enable;
+    b->wait_s = wait_limit_s;
+    return batch_build(b);
 }
 
 int lbib_batch_set_config(void *h, int threads, int order, int cells_per_thread) {

@@ -63,6 +63,61 @@ constexpr bool lattice_is_consistent() {
 }
 static_assert(lattice_is_consistent(), "D3Q19 table");
 
+// Loads of data that a launch never writes take the read-only path (__ldg).
+// A launch that reads data other blocks of the same launch wrote (the
+// persistent batched step: one work item's populations, flags and moments
+// are written by earlier items) must not use that path, which lies outside
+// the memory model: with kCG it issues plain weak loads (ld.global.ca,
+// cached in L1 like the read-only path), which the memory model orders
+// after the item's acquire of its dependency counter and the block barrier
+// that follows it, so they see the awaited items' stores.  Inline PTX keeps
+// the compiler from turning them into read-only loads.
+__device__ __forceinline__ float ld_ca(const float *p) {
+    float v;
+    asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_ca(const double *p) {
+    double v;
+    asm volatile("ld.global.ca.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_ca(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.global.ca.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ __half ld_ca(const __half *p) {
+    unsigned short v;
+    asm volatile("ld.global.ca.b16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+    return __ushort_as_half(v);
+}
+__device__ __forceinline__ __nv_bfloat16 ld_ca(const __nv_bfloat16 *p) {
+    unsigned short v;
+    asm volatile("ld.global.ca.b16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+    return __ushort_as_bfloat16(v);
+}
+__device__ __forceinline__ float4 ld_ca(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.ca.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ double2 ld_ca(const double2 *p) {
+    double2 v;
+    asm volatile("ld.global.ca.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p) : "memory");
+    return v;
+}
+template <bool kCG, typename T>
+__device__ __forceinline__ T ld_ro(const T *p) {
+    if constexpr (kCG)
+        return ld_ca(p);
+    else
+        return __ldg(p);
+}
+
 // ---- population storage: S is the stored type, arithmetic is float or double ----
 // Populations are stored as deviations g_i = f_i - w_i from the resting
 // equilibrium; half and bfloat16 storage scale them by kHalfScale to stay
@@ -246,6 +301,7 @@ struct BodyView {
 // Device error codes (the values of include/lbib.h).
 constexpr int kErrDiverged = -4;   // LBIB_EDIVERGED
 constexpr int kErrBodyWall = -5;   // LBIB_EBODY_WALL
+constexpr int kErrTimeout = -6;    // LBIB_ETIMEOUT
 // A marker moving farther than this in one step (lattice units; dt = 1) has
 // left the scheme's range: lattice Boltzmann velocities stay well below the
 // speed of sound c_s = 0.577, and the MLS support assumes sub-cell motion.
@@ -294,6 +350,29 @@ struct BatchTables {
     int sweep_threads;     // threads per sweep block
     int sweep_cpt;         // cells per sweep thread (blocks per lattice = cells / (threads * cpt))
     int sweep_off32;       // 1: every lattice of the batch has off32 set
+};
+
+// ---- persistent batched step: one launch runs several steps of every
+// lattice of a batch as a queue of work items ----
+// Item kinds in their order within a step.  Every item waits only for
+// items of earlier kinds of its own step, or of earlier steps, of its own
+// lattice, and the queue holds those earlier: items are taken in ticket
+// order, so whatever an item waits for was taken earlier by a running
+// block, and the queue cannot deadlock.
+enum PKind { kPMom = 0, kPMls, kPMemb, kPRf, kPRm, kPCen, kPSweep, kPKinds };
+struct PersistTables {
+    int nitems;              // items of the launch (all its steps)
+    int nsteps;              // steps per launch
+    int phase0;              // rotation phase of the launch's first step
+    int sweep_cells;         // lattice cells per sweep item
+    long long wait_ns;       // bound on each dependency wait (ns)
+    const int4 *items;       // [nitems] in queue order: kind | step << 8, body (IB kinds) or lattice
+                             // (sweep), virtual block, block count
+    const int *body_lat;     // [nb]: lattice of each body
+    const unsigned *need;    // [nl * kPKinds]: items of each kind per step and lattice
+    unsigned *ticket;        // next ticket (zero at launch)
+    unsigned *abort;         // nonzero once a wait has expired (zero at launch)
+    unsigned *done;          // [nl * kPKinds]: items finished in this launch (zero at launch)
 };
 
 // Copies a table entry into shared memory with the whole block (the batch

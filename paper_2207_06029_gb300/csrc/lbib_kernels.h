@@ -72,5 +72,12 @@ struct BatchGrid {
 cudaError_t launch_batch_ib(int prec, const BatchTables &T, const BatchGrid &G, int phase, cudaStream_t s);
 cudaError_t launch_batch_sweep(int prec, const BatchTables &T, const BatchGrid &G, int phase, int store_fields,
                                cudaStream_t s);
+// persistent batched step (ib.cu): P.nsteps steps of every lattice in one
+// launch of `grid` blocks of 256 threads; the counters P.ticket, P.abort and
+// P.done must be zero at launch
+cudaError_t launch_batch_persistent(int prec, const BatchTables &T, const PersistTables &P, int grid, cudaStream_t s);
+// resident blocks per SM of the persistent kernel (sets its shared-memory
+// attribute; call before any capture)
+int batch_persistent_blocks_per_sm(int prec, bool off32);
 
 }  // namespace lbib

@@ -84,7 +84,7 @@ EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_b
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
            "lbib_device_bytes", "lbib_save", "lbib_load", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
-           "lbib_batch_set_config",
+           "lbib_batch_set_config", "lbib_batch_set_persistent",
            "lbib_batch_destroy", "lbib_batch_last_error",
            "lbib_request_create", "lbib_request_add_body", "lbib_request_destroy", "lbib_serve_create",
            "lbib_serve_submit", "lbib_serve_wait", "lbib_serve_take", "lbib_serve_stats", "lbib_serve_destroy",
@@ -137,6 +137,7 @@ def load():
         L.lbib_batch_counters.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.lbib_batch_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_batch_set_config.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.lbib_batch_set_persistent.argtypes = [vp, C.c_int, C.c_double]
         L.lbib_batch_destroy.argtypes = [vp]
         L.lbib_batch_destroy.restype = None
         L.lbib_batch_last_error.argtypes = [vp]
@@ -552,6 +553,10 @@ def lbib_batch_autotune(batch, steps):
     return tuple(ch)
 
 
+def lbib_batch_set_persistent(batch, enable, wait_limit_s=2.0):
+    return _bcheck(batch, load().lbib_batch_set_persistent(batch, int(enable), float(wait_limit_s)))
+
+
 def lbib_batch_set_config(batch, threads, order, cells_per_thread):
     _bcheck(batch, load().lbib_batch_set_config(batch, int(threads), int(order), int(cells_per_thread)))
 
@@ -583,6 +588,9 @@ class Batch:
 
     def set_config(self, threads, order, cells_per_thread):
         lbib_batch_set_config(self.h, threads, order, cells_per_thread)
+
+    def set_persistent(self, enable, wait_limit_s=2.0):
+        lbib_batch_set_persistent(self.h, enable, wait_limit_s)
 
     def counters(self):
         return lbib_batch_counters(self.h)
