@@ -457,17 +457,33 @@ def batch_leg(args):
     return out
 
 
-def serve_leg(args, mode, precision, max_active=64, batch_cells=0, small=False, batch_order=0):
-    """A seeded Poisson stream (4 requests/s) of capsule-in-shear and
-    settling-sphere runs through the serving engine; latency from submission
-    to completion."""
+SERVE_STREAMS = {
+    # the serving configuration as stated: Poisson 4/s, cubic N 32..192,
+    # 2000..30000 steps, capsules (N >= 48) in the validated parameter box
+    "baseline": dict(count=64, seed=4, rate=4.0, n_range=(32, 192), step_range=(2000, 30000)),
+    # the same stream with the capsule parameter box as stated (Ca 0.005..0.3,
+    # Eb 0..0.05, mass ratio 0.5/1/2) and capsules from N = 32: runs that
+    # diverge fail with LBIB_EDIVERGED and leave the batch
+    "baseline_full": dict(count=64, seed=4, rate=4.0, n_range=(32, 192), step_range=(2000, 30000),
+                          capsule_min_n=32),
+    # many small lattices, where one run alone leaves the GPU idle
+    "small": dict(count=64, seed=9, rate=40.0, n_range=(32, 64), step_range=(500, 2000)),
+}
+
+
+def serve_leg(args, mode, precision, max_active=64, batch_cells=0, stream_kind="baseline", batch_order=0):
+    """A seeded Poisson stream of capsule-in-shear and settling-sphere runs
+    through the serving engine; latency from submission to completion.  The
+    step counts of the stated streams are scaled by args.serve_steps_scale."""
     from paper_2207_06029_gb300 import lbib
     from paper_2207_06029_gb300 import workloads as W
-    if small:
-        stream = W.serve_stream(count=64, seed=9, rate=40.0, n_range=(32, 64), step_range=(500, 2000),
-                                precision=precision)
-    else:
-        stream = W.serve_stream(count=args.serve_requests, precision=precision)
+    kw = dict(SERVE_STREAMS[stream_kind])
+    if stream_kind.startswith("baseline"):
+        scale = getattr(args, "serve_steps_scale", 1.0)
+        kw["step_range"] = tuple(max(1, int(round(scale * x))) for x in kw["step_range"])
+    if stream_kind == "baseline_full":
+        kw.update(Ca_range=W.FULL_CA, Eb_range=W.FULL_EB, mass_ratios=W.FULL_MASS_RATIOS)
+    stream = W.serve_stream(precision=precision, **kw)
     server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=max_active, mode=mode,
                                     batch_cells=batch_cells, batch_order=batch_order)
     reqs = [(t, lbib.request_from_case(case, steps), case, steps) for t, case, steps in stream]
@@ -493,7 +509,10 @@ def serve_leg(args, mode, precision, max_active=64, batch_cells=0, small=False, 
     lbib.lbib_serve_destroy(server)
     lat = sorted(lat)
     pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
-    return {"runs": len(lat), "failed": failed, "makespan_s": makespan,
+    codes = {}
+    for f in failed:
+        codes[str(f["code"])] = codes.get(str(f["code"]), 0) + 1
+    return {"runs": len(lat), "failed": len(failed), "failed_by_code": codes, "makespan_s": makespan,
             "runs_per_h": len(lat) / makespan * 3600.0, "p50_s": pct(0.5), "p99_s": pct(0.99),
             "mlups": stats["cell_updates"] / makespan / 1e6,
             "busy_mlups": stats["cell_updates"] / max(stats["busy_s"], 1e-9) / 1e6,
@@ -638,7 +657,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=60)
     ap.add_argument("--batch-count", type=int, default=64, help="lattices in the batched leg")
     ap.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving leg")
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-steps-scale", type=float, default=0.25,
+                    help="step counts of the stated serving stream (2000..30000) times this (1: full length, "
+                         "about 90 s a leg)")
     ap.add_argument("--overlap", default="auto", choices=["auto", "on", "off"],
                     help="far-field sweep concurrent with the IB stage (auto: as tuned)")
     ap.add_argument("--cpu-sample", type=float, default=0.0,
@@ -708,22 +729,25 @@ def main():
     if args.serve and rank == 0 and world == 1:
         from paper_2207_06029_gb300 import lbib
         from paper_2207_06029_gb300 import workloads as W
+        lo, hi = (max(1, int(round(args.serve_steps_scale * x))) for x in SERVE_STREAMS["baseline"]["step_range"])
+        stream = (f"64 requests, Poisson 4/s, half capsule-in-shear half settling sphere, cubic N~U{{32..192}}, "
+                  f"steps~U{{{lo}..{hi}}} (the stated 2000..30000 x {args.serve_steps_scale:g}), budget 150 GB")
         line["serve"] = {
-            "stream": f"{args.serve_requests} requests, Poisson 4/s, half capsule-in-shear half settling sphere, "
-                      "cubic N~U{32..160} (capsules N>=48), steps~U{1000..6000}, budget 150 GB",
-            "batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32),
+            "stream": stream + "; capsules N >= 48 in the validated parameter box",
+            "plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32),
             "batched_fp32_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, batch_cells=1 << 20,
                                                 batch_order=lbib.LBIB_SERVE_OLDEST),
-            "batched_fp32_srpt_2M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, batch_cells=2 << 20),
-            "plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32),
             "batched_fp16_dev_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP16_DEV,
                                                     batch_cells=1 << 20, batch_order=lbib.LBIB_SERVE_OLDEST),
+            "full_box_stream": stream + "; capsules from N = 32 in the stated box (Ca 0.005..0.3, Eb 0..0.05, "
+                                        "mass ratio 0.5/1/2): diverging runs fail with LBIB_EDIVERGED (-4)",
+            "full_box_batched_fp32_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32,
+                                                         batch_cells=1 << 20, batch_order=lbib.LBIB_SERVE_OLDEST,
+                                                         stream_kind="baseline_full"),
             "small_stream": "64 requests, Poisson 40/s, same mix, cubic N~U{32..64} (capsules 48..64), "
                             "steps~U{500..2000}",
-            "small_batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, small=True),
-            "small_batched_fp32_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, small=True,
-                                                      batch_cells=1 << 20, batch_order=lbib.LBIB_SERVE_OLDEST),
-            "small_plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32, small=True),
+            "small_batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, stream_kind="small"),
+            "small_plain_fp32": serve_leg(args, lbib.LBIB_SERVE_PLAIN, W.PREC_FP32, stream_kind="small"),
         }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, workload=args.workload)

@@ -276,11 +276,19 @@ def case_batch(count=64, seed=2207, n_range=(48, 112), Ca_range=BATCH_CA, Eb_ran
     return cases, params
 
 
+# the capsule parameter box of the batched sweep as stated for it (Ca
+# log-uniform, bending ratio uniform, membrane mass ratio): its stiff, light
+# and bending-dominated corners diverge under the explicit marker update
+FULL_CA = (0.005, 0.3)
+FULL_EB = (0.0, 0.05)
+FULL_MASS_RATIOS = (0.5, 1.0, 2.0)
+
+
 def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000, 6000), precision=PREC_FP32,
-                 Ca_range=BATCH_CA, Eb_range=BATCH_EB, mass_ratios=BATCH_MASS_RATIOS):
+                 Ca_range=BATCH_CA, Eb_range=BATCH_EB, mass_ratios=BATCH_MASS_RATIOS, capsule_min_n=48):
     """A seeded Poisson arrival stream (mean `rate` requests per second) of
     capsule-in-shear and settling-sphere runs, half each: cubic lattices
-    N ~ U{n_range} (capsules at least 48), steps ~ U{step_range}, capsule
+    N ~ U{n_range} (capsules at least capsule_min_n), steps ~ U{step_range}, capsule
     parameters drawn as in case_batch (radius N/10), settling spheres of radius N/10 (icosphere level 3 or 4) at
     density ratio U[1.1, 1.5] with gravity for a terminal Re U[1, 20] (capped
     so that the sphere stays clear of the floor for its steps).
@@ -295,7 +303,7 @@ def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000
             # capsules keep the validated box of case_batch: N >= 48, radius
             # N/10 (smaller or more confined capsules lose the stability of
             # the explicit marker update within a few thousand steps)
-            n = max(n, 48)
+            n = max(n, capsule_min_n)
         radius = n / 10.0
         c = (n - 1) / 2.0
         if k % 2 == 0:
