@@ -50,7 +50,7 @@ class BodyParams(C.Structure):
                 ("ref_radius", C.c_double),
                 ("gravity", C.c_double * 3), ("u0", C.c_double * 3), ("omega0", C.c_double * 3),
                 ("bend_variant", C.c_int), ("kinematic", C.c_int), ("rigid_force", C.c_int),
-                ("centroid_markers", C.c_int)]
+                ("centroid_markers", C.c_int), ("mass_model", C.c_int)]
 
 
 def lib():
@@ -317,12 +317,12 @@ class Sim:
 
     def add_body(self, verts, tris, *, rigid=False, ks0=0.0, Eb=0.0, kv=0.0, thickness=1.0,
                  density_ratio=1.0, ref_radius=1.0, gravity=(0, 0, 0), u0=(0, 0, 0), omega0=(0, 0, 0),
-                 bend_variant=0, kinematic=0, rigid_force=0, centroid_markers=0):
+                 bend_variant=0, kinematic=0, rigid_force=0, centroid_markers=0, mass_model=0):
         verts = _d(verts)
         tris = _i(tris)
         p = BodyParams(int(rigid), ks0, Eb, kv, thickness, density_ratio, ref_radius,
                        (C.c_double * 3)(*gravity), (C.c_double * 3)(*u0), (C.c_double * 3)(*omega0),
-                       int(bend_variant), int(kinematic), int(rigid_force), int(centroid_markers))
+                       int(bend_variant), int(kinematic), int(rigid_force), int(centroid_markers), int(mass_model))
         bid = lib().orc_sim_add_body(self._h, verts, verts.shape[0], tris, tris.shape[0], C.byref(p))
         if bid < 0:
             raise ValueError(f"orc_sim_add_body failed ({bid})")

@@ -581,6 +581,8 @@ typedef struct {
     int kinematic; /* membrane: markers advected with the fluid (kinematic IB) */
     int rigid_force; /* rigid: 0 probe stress jump (as printed), 1 momentum exchange */
     int centroid_markers; /* 1: the IB markers are the triangle centroids (as printed in Sec. 2.3) */
+    int mass_model; /* membrane mass: 0 a shell of thickness T and density rho_s (Sec. 3.5),
+                       1 a capsule of density rho_s, i.e. rho_s times the enclosed volume (Sec. 3.4) */
 } orc_body_params;
 
 typedef struct {
@@ -776,7 +778,10 @@ int orc_sim_add_body(orc_sim *s, const double *verts, int nv, const int *tris, i
         body_free(&b);
         return ORC_EINVAL;
     }
-    b.mv = p->density_ratio * p->thickness * b.A0 / nv;
+    /* membrane mass, uniform over the vertices (Eq. newtonSoft): the shell
+     * of unit thickness of Sec. 3.5, or the capsule of unit density ratio of
+     * Sec. 3.4, whose mass is that of its enclosed volume */
+    b.mv = p->mass_model == 1 ? p->density_ratio * b.V0 / nv : p->density_ratio * p->thickness * b.A0 / nv;
     b.Ub = (double *)calloc(3 * (size_t)nv, sizeof(double));
     b.U = (double *)calloc(3 * (size_t)nv, sizeof(double));
     b.Fl = (double *)calloc(3 * (size_t)nv, sizeof(double));

@@ -184,3 +184,24 @@ def test_rest_membrane_parameters(paper_const):
     assert np.abs(r["ks"] - ks).max() < 1e-15 and np.abs(r["l0"] - l0).max() < 1e-15
     assert np.abs(r["kb"] - kb).max() < 1e-15
     assert abs(r["mv"] - 2.0 * oracle.area(v, f) / len(v)) < 1e-14
+
+
+@pytest.mark.parametrize("radius,level", [(4.0, 3), (10.0, 4)])
+def test_capsule_mass_model_is_that_of_the_enclosed_volume(radius, level):
+    """Sec. 3.4 defines the capsule's mass by a solid-to-fluid density ratio:
+    with mass_model 1 the vertices share rho_s V0 (V0 the enclosed volume),
+    with mass_model 0 (the shell of unit thickness of Sec. 3.5) rho_s T A0.
+    For a sphere the ratio of the two is V0 / (T A0) -> r / 3 as the mesh is
+    refined (exact for the sphere's volume and area)."""
+    v, f = W.icosphere(level, radius, (16.0, 16.0, 16.0))
+    masses = {}
+    for model in (0, 1):
+        s = oracle.Sim((34, 34, 34), 0.8)
+        s.add_body(v, f, ks0=0.01, Eb=0.0, kv=1.0, thickness=1.0, density_ratio=1.5, ref_radius=radius,
+                   mass_model=model)
+        masses[model] = s.body_rest(0)["mv"] * len(v)
+        s.close()
+    assert abs(masses[0] - 1.5 * oracle.area(v, f)) < 1e-12 * masses[0]
+    assert abs(masses[1] - 1.5 * oracle.volume(v, f)) < 1e-12 * masses[1]
+    sphere = (4.0 / 3.0 * np.pi * radius ** 3) / (4.0 * np.pi * radius ** 2)
+    assert abs(masses[1] / masses[0] / sphere - 1.0) < 0.03
