@@ -102,6 +102,10 @@ typedef struct {
                               * printed in Sec. 2.3), each carrying its triangle's area, the vertices
                               * moving with the area-weighted mean of their triangles' centroid
                               * velocities */
+    int mass_model;          /* membrane: the mass spread uniformly over the vertices (Eq. newtonSoft)
+                              * is 0 that of a shell of thickness T and density rho_s, rho_s T A / N_v
+                              * (Sec. 3.5), or 1 that of a capsule of density rho_s, rho_s V / N_v with
+                              * V the enclosed volume (Sec. 3.4) */
 } lbib_body_params;
 
 typedef struct {

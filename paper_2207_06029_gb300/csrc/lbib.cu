@@ -662,7 +662,7 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
         if (!(bp->density_ratio > 0)) return fail(c, LBIB_EINVAL, "rigid body needs density_ratio > 0");
     } else {
         if (!(bp->thickness > 0) || !(bp->density_ratio > 0) || bp->ks0 < 0 || bp->Eb < 0 || bp->kv < 0 ||
-            (bp->Eb > 0 && !(bp->ref_radius > 0)))
+            (bp->Eb > 0 && !(bp->ref_radius > 0)) || (bp->mass_model != 0 && bp->mass_model != 1))
             return fail(c, LBIB_EINVAL, "invalid membrane parameters");
     }
     DevBody b;
@@ -718,7 +718,7 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     if (!(V0 > 0.0)) return fail(c, LBIB_EINVAL, "mesh encloses no positive volume (inward orientation?)");
     b.V0 = V0;
     b.A0 = A0;
-    b.mv = bp->density_ratio * bp->thickness * A0 / nv;
+    b.mv = bp->mass_model == 1 ? bp->density_ratio * V0 / nv : bp->density_ratio * bp->thickness * A0 / nv;
     for (int v = 0; v < nv; ++v)
         for (int a = 0; a < 3; ++a) b.origin[a] += verts[3 * v + a] / nv;
     // vertex -> (hinge, role) and vertex -> (triangle, corner) lists

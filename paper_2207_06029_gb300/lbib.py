@@ -39,7 +39,7 @@ class lbib_body_params(C.Structure):
                 ("thickness", C.c_double), ("density_ratio", C.c_double), ("ref_radius", C.c_double),
                 ("gravity", C.c_double * 3), ("u0", C.c_double * 3), ("omega0", C.c_double * 3),
                 ("bend_variant", C.c_int), ("kinematic", C.c_int), ("rigid_force", C.c_int),
-                ("centroid_markers", C.c_int)]
+                ("centroid_markers", C.c_int), ("mass_model", C.c_int)]
 
 
 class lbib_body_state(C.Structure):
@@ -371,7 +371,7 @@ def make_params(n, tau, *, bc=(0, 0, 0), wall_u=None, body_force=(0, 0, 0), prec
 
 def make_body_params(*, rigid=False, ks0=0.0, Eb=0.0, kv=0.0, thickness=1.0, density_ratio=1.0, ref_radius=1.0,
                      gravity=(0, 0, 0), u0=(0, 0, 0), omega0=(0, 0, 0), bend_variant=0, kinematic=0, rigid_force=0,
-                     centroid_markers=0):
+                     centroid_markers=0, mass_model=0):
     bp = lbib_body_params()
     bp.rigid = int(rigid)
     bp.ks0, bp.Eb, bp.kv = float(ks0), float(Eb), float(kv)
@@ -384,6 +384,7 @@ def make_body_params(*, rigid=False, ks0=0.0, Eb=0.0, kv=0.0, thickness=1.0, den
     bp.kinematic = int(kinematic)
     bp.rigid_force = int(rigid_force)
     bp.centroid_markers = int(centroid_markers)
+    bp.mass_model = int(mass_model)
     return bp
 
 

@@ -151,12 +151,14 @@ class Body:
     kinematic: int = 0
     rigid_force: int = 0
     centroid_markers: int = 0
+    mass_model: int = 0  # membrane mass: 0 shell of thickness T (Sec. 3.5), 1 capsule of density rho_s (Sec. 3.4)
 
     def kwargs(self):
         return dict(rigid=self.rigid, ks0=self.ks0, Eb=self.Eb, kv=self.kv, thickness=self.thickness,
                     density_ratio=self.density_ratio, ref_radius=self.ref_radius, gravity=self.gravity,
                     u0=self.u0, omega0=self.omega0, bend_variant=self.bend_variant, kinematic=self.kinematic,
-                    rigid_force=self.rigid_force, centroid_markers=self.centroid_markers)
+                    rigid_force=self.rigid_force, centroid_markers=self.centroid_markers,
+                    mass_model=self.mass_model)
 
 
 @dataclasses.dataclass
@@ -212,14 +214,15 @@ def case_couette_sphere(n=32, tau=1.0, U=0.01, level=3, radius=4.0, steps=200, p
 
 
 def case_capsule_shear(n=96, tau=0.8, shear_rate=1e-4, radius=10.0, level=4, Ca=0.05, Eb=0.01, kv=10.0,
-                       density_ratio=1.0, steps=20000, precision=PREC_FP32, center=None):
+                       density_ratio=1.0, steps=20000, precision=PREC_FP32, center=None, mass_model=1):
     """Deformable capsule in a Couette cell: 96^3, tau 0.8, shear rate 1e-4,
-    radius 10 (2562 markers, 5120 triangles), k_v = 10, mass ratio 1."""
+    radius 10 (2562 markers, 5120 triangles), solid-to-fluid density ratio 1
+    with the capsule's mass that of its enclosed volume (Sec. 3.4)."""
     U = shear_rate * (n - 1) / 2.0
     c = (n - 1) / 2.0
     v, f = icosphere(level, radius, center if center is not None else (c, c, c))
     body = Body(v, f, rigid=False, ks0=ks0_from_capillary(Ca, tau, shear_rate, radius), Eb=Eb, kv=kv,
-                density_ratio=density_ratio, ref_radius=radius)
+                density_ratio=density_ratio, ref_radius=radius, mass_model=mass_model)
     return Case(f"capsule_shear_{n}_Ca{Ca:g}", (n, n, n), tau, (PERIODIC, PERIODIC, WALL), shear_walls(U),
                 precision=precision, steps=steps, bodies=[body], u0=couette_profile((n, n, n), U))
 
