@@ -425,7 +425,15 @@ def batch_leg(args):
         ctxs.append(ctx)
     torch.cuda.synchronize()
     batch = lbib.Batch(ctxs, stream=stream.cuda_stream)
-    tuned = batch.autotune(6) if args.autotune else (256, 0, 4)
+    if args.batch_mode == "persistent":  # the persistent kernel, sweep tiles of 4096 cells
+        batch.set_config(256, 1, 16)
+        batch.set_persistent(1)
+        tuned = (-1, 1, 16)
+    elif args.batch_mode == "split":  # one sweep launch per lattice
+        batch.set_config(0, 1, 4)
+        tuned = (0, 1, 4)
+    else:
+        tuned = batch.autotune(6) if args.autotune else (256, 0, 4)
     batch.step(12)
     batch.sync()
     steps = max(6, (args.batch_steps // 6) * 6)
@@ -445,7 +453,9 @@ def batch_leg(args):
            "value": cells * (steps + 1) / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps + 1,
            "ms_per_step": ms / (steps + 1), "cells": cells, "markers": sum(len(c.bodies[0].verts) for c in cases),
            "launches_per_step": (l1 - l0) / (steps + 1),
-           "autotuned": {"sweep": ("one launch per lattice" if tuned[0] == 0 else
+           "autotuned": {"sweep": ("persistent kernel, six steps a launch, sweep tiles of "
+                                   f"{256 * tuned[2]} cells" if tuned[0] == -1 else
+                                   "one launch per lattice" if tuned[0] == 0 else
                                    f"batched, {tuned[0]} threads, {tuned[2]} cells per thread"),
                          "lattice_order": ["as given", "largest first"][tuned[1]]},
            "hbm_frac_sweep_bytes": cells * 152.0 * (steps + 1) / (ms * 1e-3) / 1e9 / hbm_peak()[0],
@@ -656,6 +666,11 @@ def main():
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-lattices leg")
     ap.add_argument("--batch-steps", type=int, default=60)
     ap.add_argument("--batch-count", type=int, default=64, help="lattices in the batched leg")
+    ap.add_argument("--batch-mode", default="auto", choices=["auto", "persistent", "split"],
+                    help="batched leg: autotuned launch configuration, the persistent kernel, or one sweep "
+                         "launch per lattice")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only run the batched leg and print its figures (a diagnostic line)")
     ap.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving leg")
     ap.add_argument("--serve-steps-scale", type=float, default=0.25,
                     help="step counts of the stated serving stream (2000..30000) times this (1: full length, "
@@ -701,6 +716,12 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.batch_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_stream(torch.cuda.Stream())
+        print(json.dumps({"batch": batch_leg(args)}))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
