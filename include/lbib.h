@@ -66,7 +66,9 @@ typedef struct {
     double tau;              /* BGK relaxation time, > 0.5; nu = (tau - 1/2)/3 (Sec. 2.1) */
     double body_force[3];    /* uniform fluid body force g_ext (not applied on wall nodes) */
     int bc[3];               /* lbib_bc per axis */
-    double wall_u[6][3];     /* wall velocity per face: -x, +x, -y, +y, -z, +z */
+    double wall_u[6][3];     /* wall velocity per face: -x, +x, -y, +y, -z, +z; on an edge or
+                              * corner node the component along each of its faces' normals
+                              * is that face's own, the others the mean over its faces */
     int precision;           /* lbib_prec */
     void *stream;            /* cudaStream_t to run on, or NULL for a library-owned stream */
     /* optional device allocator (e.g. a PyTorch caching allocator); both NULL

@@ -150,17 +150,31 @@ void orc_zouhe_face(double *f, int a, int s, const double *uw) {
 }
 
 /* Edge and corner nodes of walled boxes; the paper gives no rule there.
- * reading: with the set of faces the node lies on, the wall velocity is the
- * mean of those faces' velocities and the reference density is rho0 = 1.
- * An unknown population (s_j e_ia_j > 0 for some face j) whose opposite is
- * known is bounced back with the moving-wall momentum term,
+ * reading: the node belongs to every face it lies on, so no fluid may cross
+ * any of them: the wall velocity's component along the normal of one of the
+ * node's faces is that face's own normal component, and a component along
+ * which none of its faces is normal is the mean of the faces' components.
+ * (A lid sliding into a resting side wall thus leaves that edge at rest;
+ * taking the plain mean there would give the edge a velocity through the
+ * side wall, a source and a sink of mass at the two ends of the lid whose
+ * strength shrinks only like the spacing.)  The reference density is
+ * rho0 = 1.  An unknown population (s_j e_ia_j > 0 for some face j) whose
+ * opposite is known is bounced back with the moving-wall momentum term,
  *     f_i = f_opp + 6 w_i rho0 (e_i . uw);
  * one whose opposite is unknown too (a buried link) is set to
  * f^eq_i(rho0, uw). */
 void orc_wall_multi(double *f, int nface, const int *axes, const int *signs, const double *uw_faces) {
     double uw[3] = {0.0, 0.0, 0.0};
-    for (int j = 0; j < nface; ++j)
-        for (int a = 0; a < 3; ++a) uw[a] += uw_faces[3 * j + a] / nface;
+    for (int a = 0; a < 3; ++a) {
+        int normal_face = -1;
+        for (int j = 0; j < nface; ++j)
+            if (axes[j] == a) normal_face = j;
+        if (normal_face >= 0) {
+            uw[a] = uw_faces[3 * normal_face + a];
+        } else {
+            for (int j = 0; j < nface; ++j) uw[a] += uw_faces[3 * j + a] / nface;
+        }
+    }
     int unknown[Q];
     for (int i = 0; i < Q; ++i) {
         unknown[i] = 0;

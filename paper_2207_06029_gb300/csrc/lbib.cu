@@ -464,7 +464,9 @@ int lbib_create(const lbib_params *p, void **out) {
         L.gext_f[a] = (float)p->body_force[a];
     }
     // wall velocity per combination of faces: the face's own velocity on a
-    // face node, the mean of the faces' velocities on edges and corners
+    // face node; on edges and corners no flow through any of the node's
+    // faces (a component along a face normal is that face's own), the mean
+    // of the faces' velocities in the remaining directions
     for (int cz = 0; cz < 3; ++cz)
         for (int cy = 0; cy < 3; ++cy)
             for (int cx = 0; cx < 3; ++cx) {
@@ -473,8 +475,13 @@ int lbib_create(const lbib_params *p, void **out) {
                 for (int a = 0; a < 3; ++a)
                     if (code[a]) faces[nf++] = 2 * a + (code[a] == 2);
                 double uw[3] = {0.0, 0.0, 0.0};
-                for (int j = 0; j < nf; ++j)
-                    for (int a = 0; a < 3; ++a) uw[a] += p->wall_u[faces[j]][a] / nf;
+                for (int a = 0; a < 3; ++a) {
+                    if (code[a]) {
+                        uw[a] = p->wall_u[2 * a + (code[a] == 2)][a];
+                        continue;
+                    }
+                    for (int j = 0; j < nf; ++j) uw[a] += p->wall_u[faces[j]][a] / nf;
+                }
                 const int wc = wall_code(cx, cy, cz);
                 for (int a = 0; a < 3; ++a) {
                     L.uw_d[wc][a] = uw[a];

@@ -1,15 +1,16 @@
 """Lid-driven cavity (Sec. 3.1): the moving-lid walls with their edges and
 corners against the oracle, with and without an immersed sphere, and the
-self-convergence of the steady centreline velocity (the paper's
+self-convergence of the steady centreline velocities (the paper's
 Napolitano-Pascazio reference data are not available; a convergence study
 needs none).
 
-The lid's velocity jumps to zero at its edges.  With walls on the nodes and
-the edge rule of the walls (edge nodes take the mean velocity of their
-faces), the lid's effective width is fixed only to within a node, so the
-centreline converges at first order here (observed ratio 2.0 of successive
-differences), not at the second order the paper reports for its own wall
-treatment."""
+The lid slides along z into the resting z faces.  The edge nodes it shares
+with them belong to those walls too and are at rest (no flow through a
+wall); with that edge rule the centreline velocities converge at second
+order (measured ratio of successive differences 6.0 for u_z and 4.3 for
+u_y from 25/49/97 nodes; against 193 nodes the L2 error falls by 4.9 and
+3.6, 4.7 and 7.2 per halving, and is 7e-4 of the profile's norm at 49
+nodes)."""
 import numpy as np
 import pytest
 
@@ -54,7 +55,8 @@ def test_fp64_cavity_matches_oracle(lbib, sphere):
 
 
 def centreline(lbib, n):
-    """Steady u_z / u_lid along y at x = z = L/2 (diffusive scaling, Re 10)."""
+    """Steady u_z / u_lid along y at x = z = L/2 and u_y / u_lid along z at
+    x = y = L/2 (diffusive scaling, Re 10)."""
     case = W.case_cavity(n=n, Re=10.0, tau=0.8, precision=W.PREC_FP32)
     ctx = lbib.Context.from_case(case)
     lbib.lbib_set_output(ctx.h, -1)
@@ -64,15 +66,19 @@ def centreline(lbib, n):
     u = ctx.fields()[1].reshape(n, n, n, 3)  # [z, y, x, component]
     ctx.close()
     c = (n - 1) // 2
-    return u[c, :, c, 2] / case.wall_u[3, 2]
+    return u[c, :, c, 2] / case.wall_u[3, 2], u[:, c, c, 1] / case.wall_u[3, 2]
 
 
-def test_centreline_converges(lbib):
+def test_centreline_converges_at_second_order(lbib):
     """n = 25, 49, 97 nodes: the coarse nodes coincide with every other
-    finer node; the differences between successive profiles shrink at least
-    at first order (ratio >= 1.8 per halving of the spacing)."""
+    finer node; the differences between successive profiles shrink at
+    second order (ratio > 3.5 per halving of the spacing; first order gives
+    2), and at 49 nodes differ from 97 by under 1 % of the profile's L2
+    norm."""
     p25, p49, p97 = (centreline(lbib, n) for n in (25, 49, 97))
-    e1 = np.abs(p25 - p49[::2]).max()
-    e2 = np.abs(p49 - p97[::2]).max()
-    assert p25.min() < -0.05 and abs(p97[-1] - 1.0) < 1e-6  # recirculation; lid node moves with the lid
-    assert e1 / e2 > 1.8, (e1, e2)
+    assert p25[0].min() < -0.05 and abs(p97[0][-1] - 1.0) < 1e-6  # recirculation; lid node moves with the lid
+    for k in range(2):
+        e1 = np.abs(p25[k] - p49[k][::2]).max()
+        e2 = np.abs(p49[k] - p97[k][::2]).max()
+        assert e1 / e2 > 3.5, (k, e1, e2)
+        assert np.linalg.norm(p49[k] - p97[k][::2]) < 1e-2 * np.linalg.norm(p97[k][::2])

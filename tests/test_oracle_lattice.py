@@ -207,23 +207,39 @@ def test_corner_rule_at_rest(paper_e):
         assert np.abs(g - fe).max() < 1e-16
 
 
+def edge_velocity(axes, uw):
+    """The edge/corner wall velocity the rule is stated with: along the
+    normal of one of the node's faces, that face's own normal component (no
+    flow through any of its walls); along the other axes, the mean of the
+    faces' components."""
+    ue = uw.mean(axis=0)
+    for j, a in enumerate(axes):
+        ue[a] = uw[j, a]
+    return ue
+
+
+@pytest.mark.parametrize("tangential", [True, False])
 @pytest.mark.parametrize("axes,signs", [((0, 2), (1, -1)), ((1, 2), (-1, 1)), ((0, 1), (-1, -1)),
                                         ((0, 1, 2), (-1, 1, 1)), ((0, 1, 2), (1, -1, -1))])
-def test_corner_rule_moving_walls_keep_their_equilibrium(paper_e, axes, signs):
-    """Edge/corner rule with moving walls: each face moves tangentially with
-    its own velocity; when the known populations are at the equilibrium of
-    the mean wall velocity, f^eq(1, u_mean), the rule returns exactly that
-    equilibrium, so the node's density is 1 and its momentum u_mean.  Holds
+def test_corner_rule_moving_walls_keep_their_equilibrium(paper_e, axes, signs, tangential):
+    """Edge/corner rule with moving walls (sliding, or also moving along
+    their normals): when the known populations are at the equilibrium of the
+    edge velocity u_e, f^eq(1, u_e), the rule returns exactly that
+    equilibrium, so the node's density is 1 and its momentum u_e.  Holds
     because f^eq_i - f^eq_opp(i) = 6 w_i (e_i . u) (the odd part of Eq.
     eqfunc) is the moving-wall bounce-back term, and buried links take
-    f^eq(1, u_mean) itself; a wrong sign or factor of that term, a sum in
-    place of the mean, or a wrong opposite fails it."""
-    rng = np.random.default_rng(60 + len(axes) + 3 * axes[0])
+    f^eq(1, u_e) itself; a wrong sign or factor of that term, a sum in
+    place of the mean, a face's normal component taken from another face, or
+    a wrong opposite fails it."""
+    rng = np.random.default_rng(60 + len(axes) + 3 * axes[0] + 7 * tangential)
     uw = 0.03 * rng.standard_normal((len(axes), 3))
-    for j, a in enumerate(axes):
-        uw[j, a] = 0.0  # tangential motion of face j
-    um = uw.mean(axis=0)
-    fe = oracle.feq(1.0, um)
+    if tangential:
+        for j, a in enumerate(axes):
+            uw[j, a] = 0.0
+    ue = edge_velocity(axes, uw)
+    if tangential:
+        assert all(ue[a] == 0.0 for a in axes)  # sliding walls: nothing crosses any face
+    fe = oracle.feq(1.0, ue)
     f = fe.copy()
     unknown = np.zeros(19, bool)
     for a, s in zip(axes, signs):
@@ -232,7 +248,30 @@ def test_corner_rule_moving_walls_keep_their_equilibrium(paper_e, axes, signs):
     g = oracle.wall_multi(f, axes, signs, uw.ravel())
     assert np.abs(g - fe).max() < 1e-16
     assert abs(g.sum() - 1.0) < 1e-15
-    assert np.abs(paper_e.T @ g - um).max() < 1e-16
+    assert np.abs(paper_e.T @ g - ue).max() < 1e-16
+
+
+def test_lid_edge_on_a_resting_wall_stays_at_rest(paper_e):
+    """A lid (the +y face) sliding along z into the resting z faces: the
+    edge node it shares with a z face belongs to that resting wall too, so
+    from the resting equilibrium the rule returns the resting equilibrium (no
+    mass pushed through the z wall); on the edge with a resting x face,
+    sliding parallel to it, the node moves at half the lid speed along z."""
+    u = 0.02
+    fe0 = oracle.feq(1.0, np.zeros(3))
+    for zs in (1, -1):
+        uw = np.array([[0.0, 0.0, u], [0.0, 0.0, 0.0]])  # +y lid, resting z face
+        f = fe0.copy()
+        unknown = (-paper_e[:, 1] > 0) | (zs * paper_e[:, 2] > 0)
+        f[unknown] = 9.0
+        g = oracle.wall_multi(f, (1, 2), (-1, zs), uw.ravel())
+        assert np.abs(g - fe0).max() < 1e-16
+    fe = oracle.feq(1.0, np.array([0.0, 0.0, u / 2]))
+    f = fe.copy()
+    unknown = (-paper_e[:, 1] > 0) | (paper_e[:, 0] > 0)
+    f[unknown] = 9.0
+    g = oracle.wall_multi(f, (1, 0), (-1, 1), np.array([[0.0, 0.0, u], [0.0, 0.0, 0.0]]).ravel())
+    assert np.abs(g - fe).max() < 1e-16
 
 
 @pytest.mark.parametrize("tau", [1.0, 0.8, 0.6])
