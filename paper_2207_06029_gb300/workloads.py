@@ -335,19 +335,29 @@ def serve_stream(count=32, seed=4, rate=4.0, n_range=(32, 160), step_range=(1000
     return out
 
 
-def case_cavity(n=25, Re=10.0, tau=0.8, precision=PREC_FP32, sphere=False, steps=None):
+def case_cavity(n=25, Re=10.0, tau=0.8, precision=PREC_FP32, sphere=False, steps=None, obstacle=False):
     """Lid-driven cubic cavity (Sec. 3.1): walls on every face, the +y face
     moving along +z at u_lid = Re nu / (n - 1) (diffusive scaling: fixed tau,
     u_lid ~ 1/n).  With sphere=True a neutrally buoyant rigid sphere of
-    radius n/8 (icosphere level 3) sits at (0.5, 0.35, 0.5) L."""
+    radius n/8 (icosphere level 3) sits at (0.5, 0.35, 0.5) L.  With
+    obstacle=True a fixed sphere of diameter 0.2 L sits at the centre (the
+    obstacle of Sec. 3.1), held in place as the limit of a very dense rigid
+    body (density ratio 1e12: it moves by less than 1e-6 lattice units over a
+    run); its icosphere level grows with n so that there are about nine
+    markers per lattice cell of surface (level 3 at 25 nodes, 4 at 49, 5 at
+    97, 6 at 193)."""
     u_lid = Re * viscosity(tau) / (n - 1)
     wall_u = np.zeros((6, 3))
     wall_u[3, 2] = u_lid  # +y face moves along z
     bodies = []
+    L = n - 1
     if sphere:
-        L = n - 1
         v, f = icosphere(3, n / 8.0, (0.5 * L, 0.35 * L, 0.5 * L))
         bodies.append(Body(v, f, rigid=True, density_ratio=1.0, ref_radius=n / 8.0))
+    if obstacle:
+        level = max(1, int(round(3 + np.log2(L / 24.0))))
+        v, f = icosphere(level, 0.1 * L, (0.5 * L, 0.5 * L, 0.5 * L))
+        bodies.append(Body(v, f, rigid=True, density_ratio=1e12, ref_radius=0.1 * L))
     if steps is None:
         steps = int(2.0 * (n - 1) ** 2 / viscosity(tau))
     return Case(f"cavity_{n}_Re{Re:g}", (n, n, n), tau, (WALL, WALL, WALL), wall_u, precision=precision,
