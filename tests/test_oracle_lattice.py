@@ -321,3 +321,37 @@ def test_walled_box_mass_at_rest():
     s.step(10)
     rho, u = s.fields()
     assert np.abs(rho - 1).max() < 1e-15 and np.abs(u).max() < 1e-16
+
+
+def cavity_2d_centrelines(n, tau=0.8, Re=10.0):
+    """Steady lid-driven square cavity of the oracle, one periodic node
+    thick along x: the +y lid slides along z into the resting z walls (the
+    edge of Sec. 3.1's cavity).  Returns u_z / u_lid along y at z = L/2 and
+    u_y / u_lid along z at y = L/2, after 0.8 L^2 / nu steps (the slowest
+    transient has decayed by e^-15)."""
+    nu = (tau - 0.5) / 3.0
+    L = n - 1
+    u_lid = Re * nu / L
+    wall_u = np.zeros((6, 3))
+    wall_u[3, 2] = u_lid
+    s = oracle.Sim((1, n, n), tau, bc=(0, 1, 1), wall_u=wall_u.ravel())
+    assert s.step(int(0.8 * L * L / nu)) == 0
+    u = s.fields()[1].reshape(n, n, 3)  # [z, y, component]
+    s.close()
+    c = L // 2
+    return u[c, :, 2] / u_lid, u[:, c, 1] / u_lid
+
+
+def test_cavity_centreline_converges_at_second_order():
+    """13, 25, 49 nodes (every coarse node is every other finer one): the
+    differences between successive centreline profiles shrink by more than
+    3 per halving of the spacing (measured 5.8 for u_z, 3.7 for u_y).  The
+    edge rule is what makes it second order: with the plain mean of the
+    faces' velocities at the lid's edges (half the lid speed through the
+    resting z walls) the same study gives 2.2 and 1.5."""
+    p = [cavity_2d_centrelines(n) for n in (13, 25, 49)]
+    assert p[0][0].min() < -0.05  # the recirculation under the lid
+    for k in range(2):
+        e1 = np.abs(p[0][k] - p[1][k][::2]).max()
+        e2 = np.abs(p[1][k] - p[2][k][::2]).max()
+        assert e1 / e2 > 3.0, (k, e1, e2)
