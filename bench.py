@@ -433,7 +433,7 @@ def batch_leg(args):
         batch.set_config(0, 1, 4)
         tuned = (0, 1, 4)
     else:
-        tuned = batch.autotune(6) if args.autotune else (256, 0, 4)
+        tuned = batch.autotune(2) if args.autotune else (256, 0, 4)
     batch.step(12)
     batch.sync()
     steps = max(6, (args.batch_steps // 6) * 6)

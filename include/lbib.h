@@ -321,12 +321,14 @@ int lbib_batch_sync(void *batch);
 /* Steps taken through the batch and kernels launched by it. */
 int lbib_batch_counters(void *batch, long long *steps, long long *launches);
 
-/* Times `steps` steps for each sweep configuration and keeps the fastest:
+/* Times `steps` six-step graph launches and one field-storing step (what
+ * a long lbib_batch_step runs) for each sweep configuration and keeps the
+ * fastest:
  * the batched sweep with 128, 256 or 512 threads a block and 1 or 4 cells a
  * thread, one one-lattice sweep launch per lattice spread over side
  * streams, or the persistent kernel (lbib_batch_set_persistent) with sweep
  * tiles of 256 x 4, 8 or 16 cells, each with the lattices as given or
- * largest first; the contexts advance by about 20 * (7 + 2 * steps) steps.
+ * largest first; the contexts advance by 20 * (24 + 12 * steps) steps.
  * choice (optional, 3 ints): threads (0: one launch per lattice, -1: the
  * persistent kernel), order, cells per thread. */
 int lbib_batch_autotune(void *batch, int steps, int *choice);

@@ -17,6 +17,7 @@ namespace lbib {
 
 constexpr int kPts = 32;          // MLS points per block
 constexpr int kMlsThreads = 256;  // 8 warps, 4 points each
+static_assert(kPts <= 32 && kPts % (kMlsThreads / 32) == 0, "one lane per point in phases 0 and 2");
 constexpr double kAlpha = 0.3;    // Eq. (intKernel)
 constexpr double kRw = 1.3;       // support size r_w (Sec. 2.2)
 constexpr double kProbe = 1.2;    // probe length (Sec. 2.3)
@@ -241,6 +242,55 @@ __device__ bool spd_inverse4(const double *a, double *inv) {
     return true;
 }
 
+// Inverse of a symmetric positive definite 4x4 matrix (upper triangle as for
+// spd_inverse4) in FP32, by Cholesky: A = L L^T, M = L^-1 by forward
+// substitution, A^-1 = M^T M.  Backward stable, so for moment sums that are
+// themselves FP32 it is as accurate as an FP64 inverse of the same sums
+// (both leave errors of the order of the sums' own rounding in the fits),
+// at FP32 issue rates.  Returns false unless every pivot is positive and
+// finite (a singular support).
+__device__ bool spd_inverse4_chol(const float *a, float *inv) {
+    const float d0 = a[0];
+    if (!(d0 > 0.f && d0 < 1e30f)) return false;
+    const float l00 = sqrtf(d0), r0 = 1.f / l00;
+    const float l10 = a[1] * r0, l20 = a[2] * r0, l30 = a[3] * r0;
+    const float d1 = a[4] - l10 * l10;
+    if (!(d1 > 0.f)) return false;
+    const float l11 = sqrtf(d1), r1 = 1.f / l11;
+    const float l21 = (a[5] - l20 * l10) * r1, l31 = (a[6] - l30 * l10) * r1;
+    const float d2 = a[7] - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.f)) return false;
+    const float l22 = sqrtf(d2), r2 = 1.f / l22;
+    const float l32 = (a[8] - l30 * l20 - l31 * l21) * r2;
+    const float d3 = a[9] - l30 * l30 - l31 * l31 - l32 * l32;
+    if (!(d3 > 0.f)) return false;
+    const float r3 = 1.f / sqrtf(d3);
+    // M = L^-1 (lower triangular)
+    const float m00 = r0;
+    const float m10 = -l10 * m00 * r1, m11 = r1;
+    const float m20 = -(l20 * m00 + l21 * m10) * r2, m21 = -l21 * m11 * r2, m22 = r2;
+    const float m30 = -(l30 * m00 + l31 * m10 + l32 * m20) * r3, m31 = -(l31 * m11 + l32 * m21) * r3,
+                m32 = -l32 * m22 * r3, m33 = r3;
+    // (M^T M)_ij = sum_{k >= max(i, j)} m_ki m_kj
+    inv[0] = m00 * m00 + m10 * m10 + m20 * m20 + m30 * m30;
+    inv[1] = m10 * m11 + m20 * m21 + m30 * m31;
+    inv[2] = m20 * m22 + m30 * m32;
+    inv[3] = m30 * m33;
+    inv[5] = m11 * m11 + m21 * m21 + m31 * m31;
+    inv[6] = m21 * m22 + m31 * m32;
+    inv[7] = m31 * m33;
+    inv[10] = m22 * m22 + m32 * m32;
+    inv[11] = m32 * m33;
+    inv[15] = m33 * m33;
+    inv[4] = inv[1];
+    inv[8] = inv[2];
+    inv[9] = inv[6];
+    inv[12] = inv[3];
+    inv[13] = inv[7];
+    inv[14] = inv[11];
+    return true;
+}
+
 // Squared distance with the products and sums rounded one by one in the
 // order (x^2 + y^2) + z^2, as a plain sum of squares is.
 __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
@@ -258,7 +308,8 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
 //           W = exp(-(r/alpha)^2) for r <= 1 (the cut-off decided exactly as
 //           in FP64), node moments, the 26 products W p p^T and W p f,
 //           summed over the nodes by a warp reduce-scatter (shuffles);
-//  phase 2: one lane per point: FP64 Cholesky inverse of A; markers get
+//  phase 2: one lane per point: inverse of A (FP64 adjugate in the FP64
+//           path, FP32 Cholesky in the FP32 one); markers get
 //           U = (A^-1 b_u)_0 (Eq. uLag), probes the pressure c_s^2 rho and
 //           the traction rho nu (grad u + grad u^T) . n from the fits;
 //  phase 3: markers keep phi_k = W_k (A^-1 p_k)_0 for spreading.
@@ -277,7 +328,7 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     const int w0 = vb & 3, w2 = (vb + 2) & 3;
 
     // ---------------- phase 0: one lane per point ----------------
-    if (warp == w0) {
+    if (warp == w0 && lane < kPts) {
         const int slot = p0 + lane;
         const int p = slot < npts ? (B.perm ? B.perm[slot] : slot) : -1;
         sm.pid[lane] = p;
@@ -474,14 +525,20 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     __syncthreads();
 
     // ---------------- phase 2: one lane per point ----------------
-    if (warp == w2 && sm.pid[lane] >= 0) {
+    if (warp == w2 && lane < kPts && sm.pid[lane] >= 0) {
         const int p = sm.pid[lane];
         const R *S = sm.sums[lane];
-        double a[10], inv[16];
-        for (int q = 0; q < 10; ++q) a[q] = (double)S[q];
-        if (!spd_inverse4(a, inv)) atomicCAS(err, 0, -1);
         R Ai[16];
-        for (int q = 0; q < 16; ++q) Ai[q] = R(inv[q]);
+        if constexpr (sizeof(R) == 8) {
+            double a[10], inv[16];
+            for (int q = 0; q < 10; ++q) a[q] = (double)S[q];
+            if (!spd_inverse4(a, inv)) atomicCAS(err, 0, -1);
+            for (int q = 0; q < 16; ++q) Ai[q] = R(inv[q]);
+        } else {
+            float a[10];
+            for (int q = 0; q < 10; ++q) a[q] = (float)S[q];
+            if (!spd_inverse4_chol(a, (float *)Ai)) atomicCAS(err, 0, -1);
+        }
         if (p < nm) {
             for (int q = 0; q < 4; ++q) sm.row0[lane][q] = Ai[q];
             double *Uo = B.centroid ? B.Uc : B.U;

@@ -2106,12 +2106,17 @@ int lbib_batch_autotune(void *h, int steps, int *choice) {
                 b->order = o;
                 b->sweep_cpt = cp;
                 if ((rc = batch_build(b))) break;
-                if ((rc = lbib_batch_step(h, 7))) break;  // captures the graph, untimed
+                // untimed: one six-step graph launch (captures the graph), then
+                // back to phase 0, so that the timed calls run `steps` graph
+                // launches and the field-storing last step, as a long
+                // lbib_batch_step does
+                if ((rc = lbib_batch_step(h, 12))) break;
                 float ms = 1e30f;
                 for (int rep = 0; rep < 2 && !rc; ++rep) {
                     cudaEventRecord(e0, b->stream);
-                    rc = lbib_batch_step(h, steps);
+                    rc = lbib_batch_step(h, 6 * steps + 1);
                     cudaEventRecord(e1, b->stream);
+                    if (!rc) rc = lbib_batch_step(h, 5);  // back to phase 0, untimed
                     cudaEventSynchronize(e1);
                     float t_ms = 0.f;
                     cudaEventElapsedTime(&t_ms, e0, e1);

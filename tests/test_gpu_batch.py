@@ -148,7 +148,7 @@ def test_fp64_autotuned_batch_matches_oracle(lbib):
     """Every configuration the batch autotuner tries computes the same steps,
     and the one it keeps matches the oracle.
 
-    Tuning advances the runs by ~190 steps through every candidate (the
+    Tuning advances the runs by 720 steps through every candidate (the
     persistent kernel included).  Over that many steps the coupled bodies
     amplify FP64 rounding: the cases stepped alone with lbib_step differ
     from the oracle by 1.5e-12 (capsule) and 8.1e-12 (membrane and rigid
@@ -178,7 +178,7 @@ def test_fp64_autotuned_batch_matches_oracle(lbib):
         ctx.close()
     ctxs = [lbib.Context.from_case(c) for c in cases]
     batch = lbib.Batch(ctxs)
-    batch.set_config(max(threads, 0), order, cpt)
+    batch.set_config(256 if threads == -1 else threads, order, cpt)
     batch.set_persistent(1 if threads == -1 else 0)
     batch.step(13)
     for ctx, case in zip(ctxs, cases):
@@ -225,7 +225,7 @@ def test_batch_configurations_compute_the_same_steps(lbib, config):
         assert rel(s["f"], a["f"]) < 1e-13
         for x, y in zip(s["X"], a["X"]):
             assert rel(x, y) < 1e-13
-    for bad in [(100, 0, 4), (1024, 0, 4), (256, 2, 4), (256, 0, 0), (256, 0, 17)]:
+    for bad in [(100, 0, 4), (1024, 0, 4), (256, 2, 4), (256, 0, 0), (256, 0, 17), (-1, 0, 4)]:
         with pytest.raises(lbib.LbibError) as ei:
             batch.set_config(*bad)
         assert ei.value.code == lbib.LBIB_EINVAL
