@@ -156,6 +156,7 @@ struct MlsSmem {
     R d[kShfl ? 1 : kPts][27][3];
     // per point: A = sum W p p^T, b_f = sum W p f for f = rho - 1, u_x, u_y, u_z
     R sums[kPts][kSums];
+    R ref[kPts][4];   // the fitted fields at the support's centre node (the fits are of f - ref)
     R row0[kPts][4];  // first row of A^-1
     int pid[kPts];    // point of each slot (-1 past the end): slots follow the body's cell order
     // per warp: transpose buffer of the 26 products of each node (unused with kShfl)
@@ -306,8 +307,8 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
 //           nearest node base = floor(X + 1/2) and the exact offset X - base;
 //  phase 1: one warp per point, one lane per support node: weight
 //           W = exp(-(r/alpha)^2) for r <= 1 (the cut-off decided exactly as
-//           in FP64), node moments, the 26 products W p p^T and W p f,
-//           summed over the nodes by a warp reduce-scatter (shuffles);
+//           in FP64), node moments less those of the centre node, the 26
+//           products W p p^T and W p f, summed over the nodes;
 //  phase 2: one lane per point: inverse of A (FP64 adjugate in the FP64
 //           path, FP32 Cholesky in the FP32 one); markers get
 //           U = (A^-1 b_u)_0 (Eq. uLag), probes the pressure c_s^2 rho and
@@ -436,6 +437,17 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
         const int lp = warp * kPerWarp + j;
         const int p = sm.pid[lp];
         if (p < 0) break;
+        // fit f - f_c, f_c the moments of the centre node (lane 13, always in
+        // the support): the same fit, since MLS reproduces constants, but
+        // the sums and the solve then carry the field's variation over the
+        // support rather than its size, which the gradients at the probes
+        // (small differences of the fitted values) need
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const R fc = __shfl_sync(0xffffffffu, gu[j][c], 13);
+            gu[j][c] -= fc;
+            if (lane == 0) sm.ref[lp][c] = fc;
+        }
         R W = R(0), dk[3] = {R(0), R(0), R(0)};
         if (lane < 27) {
             const int dd[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
@@ -539,15 +551,17 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
             for (int q = 0; q < 10; ++q) a[q] = (float)S[q];
             if (!spd_inverse4_chol(a, (float *)Ai)) atomicCAS(err, 0, -1);
         }
+        const R *fc = sm.ref[lane];
         if (p < nm) {
             for (int q = 0; q < 4; ++q) sm.row0[lane][q] = Ai[q];
             double *Uo = B.centroid ? B.Uc : B.U;
             for (int jj = 0; jj < 3; ++jj) {
                 const R *bu = S + 14 + 4 * jj;
-                Uo[3 * p + jj] = (double)(Ai[0] * bu[0] + Ai[1] * bu[1] + Ai[2] * bu[2] + Ai[3] * bu[3]);
+                Uo[3 * p + jj] = (double)(Ai[0] * bu[0] + Ai[1] * bu[1] + Ai[2] * bu[2] + Ai[3] * bu[3] + fc[1 + jj]);
             }
         } else {
-            // fits: c_f[i] = sum_m Ai[i][m] b_f[m]
+            // fits: c_f[i] = sum_m Ai[i][m] b_f[m], plus the centre value for
+            // the value (i = 0)
             R cr[4], cu[3][4];
             for (int i = 0; i < 4; ++i) {
                 cr[i] = Ai[4 * i] * S[10] + Ai[4 * i + 1] * S[11] + Ai[4 * i + 2] * S[12] + Ai[4 * i + 3] * S[13];
@@ -556,6 +570,8 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
                     cu[jj][i] = Ai[4 * i] * bu[0] + Ai[4 * i + 1] * bu[1] + Ai[4 * i + 2] * bu[2] + Ai[4 * i + 3] * bu[3];
                 }
             }
+            cr[0] += fc[0];
+            for (int jj = 0; jj < 3; ++jj) cu[jj][0] += fc[1 + jj];
             const int t = (p - nm) >> 1, side = (p - nm) & 1;
             const R rho = R(1) + cr[0];
             const R nu = pick<R>(L.nu_d, L.nu_f);
@@ -740,6 +756,19 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
             ac[a] = Xr[3 * H.z + a] - xa;
             ad[a] = Xr[3 * H.w + a] - xa;
         }
+        if constexpr (sizeof(R) == 4) {
+            // the FP32 coordinates carry an absolute error of half an ulp of
+            // the body's size; their residuals restore the edges' own relative
+            // precision, which the spring extensions l - l0 and the dihedral
+            // angles (small differences of the edges) need
+            const float *Xl = B.Xlo;
+            for (int a = 0; a < 3; ++a) {
+                const float la = Xl[3 * H.x + a];
+                e[a] += Xl[3 * H.y + a] - la;
+                ac[a] += Xl[3 * H.z + a] - la;
+                ad[a] += Xl[3 * H.w + a] - la;
+            }
+        }
         const R le2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
         const R le = sqrt(le2), ile = rcp(le);
         if (role < 2) {
@@ -842,7 +871,9 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
         // diverged
         if (!(fabs(xn - x) < kMaxMarkerStep)) atomicCAS(B.err, 0, kErrDiverged);
         B.Xnew[3 * vj + a] = xn;
-        ((R *)B.Xrel_next)[3 * vj + a] = R(xn - B.origin[a]);
+        const double rel = xn - B.origin[a];
+        ((R *)B.Xrel_next)[3 * vj + a] = R(rel);
+        if constexpr (sizeof(R) == 4) B.Xlo_next[3 * vj + a] = float(rel - double(float(rel)));
         B.Ub[3 * vj + a] = Ub;
         B.Fl[3 * vj + a] = Fla;
         sbox.add(a, xn);

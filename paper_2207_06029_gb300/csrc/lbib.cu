@@ -32,6 +32,7 @@ struct DevBody {
     double *Uc = nullptr, *Flc = nullptr;  // centroid markers
     void *phi = nullptr, *tri_geo = nullptr, *probe = nullptr;  // arithmetic precision R
     void *Xrel[2] = {nullptr, nullptr};                          // R: X - origin, current and next
+    float *Xlo[2] = {nullptr, nullptr};  // FP32 membranes: (X - origin) - Xrel, current and next
     int *perm = nullptr;  // MLS points (markers, probes) in cell order
     int *node = nullptr, *tri = nullptr, *vh_ptr = nullptr, *vh_list = nullptr, *vt_ptr = nullptr,
         *vt_list = nullptr;
@@ -300,6 +301,8 @@ BodyView make_view(Ctx *c, DevBody &b) {
     v.probe = b.probe;
     v.Xrel = b.Xrel[b.bcur];
     v.Xrel_next = b.Xrel[1 - b.bcur];
+    v.Xlo = b.Xlo[b.bcur];
+    v.Xlo_next = b.Xlo[1 - b.bcur];
     v.vh_ptr = b.vh_ptr;
     v.vh_list = b.vh_list;
     v.vt_ptr = b.vt_ptr;
@@ -458,6 +461,12 @@ int lbib_create(const lbib_params *p, void **out) {
     L.nu_d = (p->tau - 0.5) / 3.0;
     L.omega_f = (float)L.omega_d;
     L.cF_f = (float)L.cF_d;
+    // c_dg = omega/12 rounded, c_ax = (omega - 8 c_dg)/2: 8 c_dg lies within
+    // a factor two of omega, so the difference and the halving are exact
+    L.codd_d[1] = L.omega_d / 12.0;
+    L.codd_d[0] = (L.omega_d - 8.0 * L.codd_d[1]) * 0.5;
+    L.codd_f[1] = L.omega_f / 12.0f;
+    L.codd_f[0] = (L.omega_f - 8.0f * L.codd_f[1]) * 0.5f;
     L.nu_f = (float)L.nu_d;
     for (int a = 0; a < 3; ++a) {
         L.gext_d[a] = p->body_force[a];
@@ -820,6 +829,14 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
             for (int a = 0; a < 3; ++a) xr[3 * v + a] = verts[3 * v + a] - b.origin[a];
         b.Xrel[0] = upload_r(c, xr, &rc);
         b.Xrel[1] = upload_r(c, xr, &rc);
+        if (!b.rigid && c->relem == 4) {
+            // the membrane's edge vectors are formed as (hi_j - hi_i) + (lo_j -
+            // lo_i): FP32 relative precision of the edge, not of the coordinate
+            std::vector<float> lo(xr.size());
+            for (size_t k = 0; k < xr.size(); ++k) lo[k] = (float)(xr[k] - (double)(float)xr[k]);
+            b.Xlo[0] = static_cast<float *>(upload(c, lo, &rc));
+            b.Xlo[1] = static_cast<float *>(upload(c, lo, &rc));
+        }
     }
     if (b.rigid) {
         double V, cen[3], I[9];

@@ -227,6 +227,12 @@ struct Lattice {
     // derived, double and float copies
     double omega_d, cF_d, nu_d, gext_d[3], uw_d[27][3];
     float omega_f, cF_f, nu_f, gext_f[3], uw_f[27][3], dist2_cut_f;
+    // odd (momentum) coefficients 3 w_i omega of the collision for the axis
+    // and the diagonal directions, chosen in each precision so that
+    // 2 c_ax + 8 c_dg = omega holds exactly: the odd parts then return the
+    // momentum they are given without a bias from rounded weights
+    double codd_d[2];
+    float codd_f[2];
 };
 
 template <typename R>
@@ -255,6 +261,10 @@ struct BodyView {
     double *Xnew;           // [3nv] positions of level n+1 (written)
     const void *Xrel;       // [3nv] R: X - origin of level n
     void *Xrel_next;        // [3nv] R: X - origin of level n+1 (written)
+    // [3nv] FP32 membranes: (X - origin) - Xrel, the residual of the rounding
+    // to FP32, of level n and n+1 (written); null otherwise
+    const float *Xlo;
+    float *Xlo_next;
     double *U;              // [3nv] interpolated fluid velocity
     double *Ub;             // [3nv] boundary velocity imposed by the IB force
     double *Fl;             // [3nv] Lagrangian IB force

@@ -177,16 +177,23 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
         }
     }
 
-    // BGK collision with the Guo term, u = (sum f e + f_lb/2)/rho.  Per
-    // direction, with a = 3 omega rho, b = 4.5 omega rho, c3 = 3 cF,
-    // c9 = 9 cF and A0 = omega (drho - 1.5 rho u.u) - 3 cF u.F:
-    //   g*_i = (1 - omega) g_i + w_i [A0 + E_i + O_i],
-    //   E_i = eu (b eu + c9 eF) (even in e_i),  O_i = a eu + c3 eF (odd),
+    // BGK collision with the Guo term, u = (sum f e + f_lb/2)/rho = j'/rho.
+    // Per direction, with b = 4.5 omega rho, c3 = 3 cF, c9 = 9 cF and
+    // A0 = omega (drho - 1.5 rho u.u) - 3 cF u.F:
+    //   g*_i = (1 - omega) g_i + w_i [A0 + E_i] + c_i e.j' + w_i c3 eF,
+    //   E_i = eu (b eu + c9 eF) (even in e_i), c_i = 3 w_i omega,
     // which is g - omega (g - (f^eq - w)) + F_i of Eqs. (evoleq, eqfunc,
-    // forcing) regrouped so that each pair (i, opp(i)) shares E and O.
+    // forcing) regrouped so that each pair (i, opp(i)) shares the even and
+    // the odd part.  The odd part takes the momentum j' itself (not rho
+    // times the rounded u) and coefficients c_i whose momentum sums to
+    // omega exactly (L.codd): the rounding of u or of the weights would
+    // otherwise shift the momentum the collision returns by the same
+    // relative amount step after step in a slowly changing flow, which acts
+    // like a small body force.
     const R inv = R(1) / rho;
     const R omega = pick<R>(L.omega_d, L.omega_f);
-    const R om1 = R(1) - omega, ca = R(3) * omega * rho, cb = R(4.5) * omega * rho;
+    const R om1 = R(1) - omega, cb = R(4.5) * omega * rho;
+    const R cax = pick<R>(L.codd_d[0], L.codd_f[0]) * kS, cdg = pick<R>(L.codd_d[1], L.codd_f[1]) * kS;
     if (F0 == R(0) && F1 == R(0) && F2 == R(0)) {
         // no body force on this node (the common case): the same update with
         // the Guo terms, which vanish exactly, left out
@@ -197,13 +204,13 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int i = pair_rep(k), o = opp(i);
-            R eu = R(0);
-            if (ex(i)) eu += R(ex(i)) * ux;
-            if (ey(i)) eu += R(ey(i)) * uy;
-            if (ez(i)) eu += R(ez(i)) * uz;
+            R eu = R(0), ej = R(0);
+            if (ex(i)) { eu += R(ex(i)) * ux; ej += R(ex(i)) * jx; }
+            if (ey(i)) { eu += R(ey(i)) * uy; ej += R(ey(i)) * jy; }
+            if (ez(i)) { eu += R(ez(i)) * uz; ej += R(ez(i)) * jz; }
             const R w = wq<R>(i) * kS;
-            const R E = eu * (cb * eu), Od = ca * eu;
-            const R base = w * (A0 + E), odd = w * Od;
+            const R E = eu * (cb * eu);
+            const R base = w * (A0 + E), odd = (i <= 6 ? cax : cdg) * ej;
             const R gi = om1 * g[i] + (base + odd), go = om1 * g[o] + (base - odd);
             g[i] = gi;
             g[o] = go;
@@ -214,7 +221,8 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
         uz_o = uz;
         return;
     }
-    const R ux = (jx + R(0.5) * F0) * inv, uy = (jy + R(0.5) * F1) * inv, uz = (jz + R(0.5) * F2) * inv;
+    const R jx2 = jx + R(0.5) * F0, jy2 = jy + R(0.5) * F1, jz2 = jz + R(0.5) * F2;
+    const R ux = jx2 * inv, uy = jy2 * inv, uz = jz2 * inv;
     const R cF = pick<R>(L.cF_d, L.cF_f);
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * F0 + uy * F1 + uz * F2;
@@ -225,13 +233,13 @@ __device__ __forceinline__ void collide_node(R (&g)[Q], R *__restrict__ force, c
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = pair_rep(k), o = opp(i);
-        R eu = R(0), eF = R(0);
-        if (ex(i)) { eu += R(ex(i)) * ux; eF += R(ex(i)) * F0; }
-        if (ey(i)) { eu += R(ey(i)) * uy; eF += R(ey(i)) * F1; }
-        if (ez(i)) { eu += R(ez(i)) * uz; eF += R(ez(i)) * F2; }
+        R eu = R(0), ej = R(0), eF = R(0);
+        if (ex(i)) { eu += R(ex(i)) * ux; ej += R(ex(i)) * jx2; eF += R(ex(i)) * F0; }
+        if (ey(i)) { eu += R(ey(i)) * uy; ej += R(ey(i)) * jy2; eF += R(ey(i)) * F1; }
+        if (ez(i)) { eu += R(ez(i)) * uz; ej += R(ez(i)) * jz2; eF += R(ez(i)) * F2; }
         const R w = wq<R>(i) * kS;
-        const R E = eu * (cb * eu + c9 * eF), Od = ca * eu + c3 * eF;
-        const R base = w * (A0 + E), odd = w * Od;
+        const R E = eu * (cb * eu + c9 * eF);
+        const R base = w * (A0 + E), odd = (i <= 6 ? cax : cdg) * ej + w * (c3 * eF);
         const R gi = om1 * g[i] + (base + odd), go = om1 * g[o] + (base - odd);
         g[i] = gi;
         g[o] = go;
