@@ -10,10 +10,10 @@ Aspect ratio 2, semi-axes (a, a/2, a/2) resolved by a = 6, 12 and 18 lattice
 units, at a fixed particle Reynolds number shear a^2 / nu = 0.2 and a fixed
 confinement 2a / H = 0.15 in a Couette cell H^3 with z walls, tau 0.8, FP32.
 Measured (quarter period / Jeffery's - 1): the printed stress-jump force
-(probes 1.2 dx off the surface) +8.6 %, +2.5 %, +0.97 % (and +0.41 % at
-a = 24): its excess is a body-resolution effect, the probes sitting 40 %
-of the minor semi-axis off the surface at a = 6; the momentum-exchange
-force -1.7 %, -0.5 %, -0.24 % (-0.14 % at a = 24).
+(probes 1.2 dx off the surface) +8.6 %, +2.5 %, +1.0 %: its excess is a
+body-resolution effect, the probes sitting 40 % of the minor semi-axis off
+the surface at a = 6; the momentum-exchange force -1.7 %, -0.46 %,
+-0.19 %.
 """
 import math
 
@@ -39,17 +39,17 @@ def lbib():
     return L
 
 
-def quarter_period(L, a, rigid_force):
+def quarter_period(L, a, rigid_force, n=None, every=None):
     """Quarter period of the spheroid with semi-major axis a over Jeffery's."""
     nu = (TAU - 0.5) / 3.0
     shear = RE * nu / a ** 2
-    n = int(round(2 * a / CONFINEMENT))
+    n = n or int(round(2 * a / CONFINEMENT))
     case = W.case_jeffery_spheroid(n=n, tau=TAU, shear_rate=shear, axes=(a, a / 2, a / 2), level=LEVEL[a],
                                    precision=W.PREC_FP32)
     case.bodies[0].rigid_force = rigid_force
     ctx = L.Context.from_case(case)
     jeffery = math.pi * 2.5 / (2.0 * shear)
-    every = max(10, int(jeffery / 400))
+    every = every or max(10, int(jeffery / 400))
     prev_t, prev_d, k = 0, 1.0, 0
     try:
         while k < 1.6 * jeffery:
@@ -78,3 +78,15 @@ def test_momentum_exchange_force_gives_the_jeffery_period(lbib, a):
     """The momentum-exchange rigid-body force: within 1 % of Jeffery's
     quarter period."""
     assert abs(quarter_period(lbib, a, 1) - 1.0) < 0.01
+
+
+def test_resolved_quarter_period_matches_the_oracle(lbib):
+    """The case tests/golden/make_jeffery_ref.py runs on the oracle (a = 12
+    in a 120^3 cell, Re 0.2, the printed stress-jump force, the axis
+    sampled every 50 steps): the GPU's FP32 quarter period within 1e-4 of
+    the stored oracle value, relative (measured 6e-7)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "jeffery_oracle_ref.txt")
+    ref = dict(line.split() for line in open(path) if line.strip() and not line.startswith("#"))
+    gpu = quarter_period(lbib, 12, 0, n=120, every=50)
+    assert abs(gpu / float(ref["ratio"]) - 1.0) < 1e-4, (gpu, ref["ratio"])

@@ -43,3 +43,40 @@ def test_quarter_period_approaches_jeffery():
         excess.append(quarter_period(n, g) / jeffery - 1.0)
     assert excess[0] > excess[1] > 0.0  # slower than Stokes flow, less so in the larger box
     assert excess[1] < 0.15
+
+
+def read_stored_quarter_period():
+    """tests/golden/jeffery_oracle_ref.txt, written by make_jeffery_ref.py
+    (oracle only): the quarter period of the resolved spheroid (semi-axes
+    12, 6, 6) at particle Reynolds number 0.2 in a 120^3 Couette cell."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "jeffery_oracle_ref.txt")
+    vals = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        vals[k] = float(v)
+    return vals
+
+
+def test_stored_resolved_quarter_period_is_jefferys():
+    """The oracle's coupled rigid body at a resolution and Reynolds number
+    where Jeffery's Stokes-flow result should hold (Sec. 3.3 validates the
+    rigid-body coupling on it): the stored quarter period lies within 3 %
+    of pi (r + 1/r) / (2 shear) and above it (the walls at confinement 0.2,
+    the finite Reynolds number and the probes' 1.2-cell offset all slow the
+    turn).  The stored Jeffery value is the closed form for the script's
+    shear rate."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_jeffery_ref as ref
+    vals = read_stored_quarter_period()
+    nu = (ref.TAU - 0.5) / 3.0
+    shear = ref.RE * nu / ref.A ** 2
+    jeffery = math.pi * (2.0 + 0.5) / (2.0 * shear)
+    assert abs(vals["jeffery_quarter_period_steps"] - jeffery) < 1e-6 * jeffery
+    ratio = vals["quarter_period_steps"] / jeffery
+    assert abs(ratio - vals["ratio"]) < 1e-7
+    assert 1.0 < ratio < 1.03
