@@ -228,7 +228,7 @@ def run_gpu(args, rank, world, workload=None):
         tuned = (0, 0, 1, 0, 0)
     if args.overlap != "auto":
         lbib.lbib_set_overlap(h, 1 if args.overlap == "on" else 0)
-        tuned = (tuned[0], tuned[1], 1 if args.overlap == "on" else 0, tuned[3], tuned[4])
+    tuned = lbib.lbib_get_launch_config(h)  # the five choices above and the IB kernels' blocks per SM
     lbib.lbib_sync(h)
     lbib.lbib_set_output(h, -1)  # no macroscopic-field output inside the timed loop
     # the launch configuration is final: capture the six phase graphs of the
@@ -595,9 +595,11 @@ def measured_line(args, r, world, ms, workload):
                    "parallelism": f"replicas{world}", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read)",
                    "fields_output": "off in the timed loop (e2e reads them)",
                    "autotuned": {"sweep_block": list(r["tuned"][:2]), "overlap": bool(r["tuned"][2]),
-                                 "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4]},
+                                 "sweep_row_tiles": bool(r["tuned"][3]), "far_field_blocks_per_sm": r["tuned"][4],
+                                 "ib_blocks_per_sm": r["tuned"][5]},
                    "populations": ("fp64 deviations f_i - w_i, fp64 arithmetic" if fp64 else
-                                   f"{ctype} deviations f_i - w_i, fp32 arithmetic; markers and MLS solve fp64")},
+                                   f"{ctype} deviations f_i - w_i, fp32 arithmetic; marker positions and rigid "
+                                   "states fp64")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(workload),
                      "kernel": ("k_sweep_tile<{0},{1}> (shared-memory row tiles, 128-bit loads/stores)"

@@ -241,7 +241,8 @@ int lbib_get_profile(void *ctx, double *ms, long long *nsteps);
  * 1 + 2 * `steps` real time steps, so the simulation advances by about
  * 16 * `steps` steps.  choice (optional, 5 ints) receives block x, block y (0, 0: whole
  * x-rows), the overlap flag, the row-tile flag and the far-field blocks per
- * SM (0: full grid). */
+ * SM (0: full grid).  With overlap it also chooses the IB kernels' blocks
+ * per SM (0, 1 or 2; lbib_get_launch_config reports it). */
 int lbib_autotune(void *ctx, int steps, int *choice);
 
 /* Sets the sweep launch configuration (what lbib_autotune chooses):
@@ -254,6 +255,19 @@ int lbib_autotune(void *ctx, int steps, int *choice);
  * that the IB kernels beside it find free SMs, 0 on its full grid.  Results
  * are the same in every configuration. */
 int lbib_set_sweep_config(void *ctx, int row_tiles, int block_x, int block_y, int far_per_sm);
+
+/* Resident blocks per SM of the IB kernels (MLS, structure update and
+ * spreading): 0 (default) launches their full grids; k > 0 launches at
+ * most k blocks per SM, each taking its share of the work in turn, so that
+ * a far-field sweep running beside them keeps the rest of every SM (the IB
+ * kernels hold up to all of an SM's registers otherwise).  Results are the
+ * same in every configuration.  LBIB_EINVAL outside [0, 64]. */
+int lbib_set_ib_blocks(void *ctx, int per_sm);
+
+/* The launch configuration in use, 6 ints: block_x, block_y, overlap,
+ * row_tiles, far_per_sm (as lbib_autotune's choice) and the IB blocks per
+ * SM (lbib_set_ib_blocks). */
+int lbib_get_launch_config(void *ctx, int *cfg);
 
 /* With a single body, the sweep of the nodes outside the body's support
  * box runs on a second stream concurrently with the IB stage (default 1);

@@ -636,12 +636,17 @@ __device__ __forceinline__ void mls_body(const R *__restrict__ mom, const Lattic
     }
 }
 
+// The blocks take the nvb groups of 32 points in turn (gridDim.x = nvb
+// unless the launch caps the grid).
 template <typename R>
 __global__ void __launch_bounds__(kMlsThreads) k_mls(const R *__restrict__ mom, Lattice L, BodyView B,
-                                                     int *err) {
+                                                     int *err, int nvb) {
     chain_wait();  // launched programmatically after the moments kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    mls_body<R>(mom, L, B, err, *reinterpret_cast<MlsSmem<R> *>(smem_raw), blockIdx.x, gridDim.x);
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        mls_body<R>(mom, L, B, err, *reinterpret_cast<MlsSmem<R> *>(smem_raw), vb, nvb);
+        __syncthreads();  // the next group reuses the shared memory
+    }
 }
 
 // Hydrodynamic force on triangle t from its two probes (Eqs. hydroForP,
@@ -888,8 +893,12 @@ __device__ __forceinline__ void membrane_body(const Lattice &L, const BodyView &
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_membrane(Lattice L, BodyView B, R *__restrict__ force,
-                                                  uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
-    membrane_body<R>(L, B, force, stamp, dstep, blockIdx.x);
+                                                  uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep,
+                                                  int nvb) {
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        membrane_body<R>(L, B, force, stamp, dstep, vb);
+        __syncthreads();  // the next group of vertices reuses the shared memory
+    }
 }
 
 // Rigid body: total force and moment of the element stresses, gravity
@@ -1197,8 +1206,12 @@ __device__ __forceinline__ void rigid_markers_body(const Lattice &L, const BodyV
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_rigid_markers(Lattice L, BodyView B, R *__restrict__ force,
-                                                       uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep) {
-    rigid_markers_body<R>(L, B, force, stamp, dstep, blockIdx.x);
+                                                       uint32_t *__restrict__ stamp, const uint32_t *__restrict__ dstep,
+                                                       int nvb) {
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        rigid_markers_body<R>(L, B, force, stamp, dstep, vb);
+        __syncthreads();  // the next group of markers reuses the shared memory
+    }
 }
 
 // IB force of centroid markers, one warp per triangle: the boundary
@@ -1523,17 +1536,21 @@ cudaError_t launch_batch_ib(int prec, const BatchTables &T, const BatchGrid &G, 
 // ---- launchers ----
 int mls_blocks(const BodyView &B) { return (B.nm + 2 * B.nt + kPts - 1) / kPts; }
 
+// Grid of n blocks' work under a cap (0: none).
+static int capped(int n, int cap) { return cap > 0 && cap < n ? cap : n; }
+
 template <typename S, typename R>
 static cudaError_t ib_front_t(const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm, int *err,
-                              uint32_t *step_inc, cudaStream_t s) {
+                              uint32_t *step_inc, int grid_cap, cudaStream_t s) {
     k_moments<S, R><<<2 * nsm, 256, 0, s>>>((const S *)fin, L, B.bbox, B.bbox_next, (R *)mom, step_inc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the MLS kernel is scheduled while the moments kernel ends (measured:
     // about 2 us off the 96^3 capsule step; the same launch for the other
     // kernels of the step made it slower)
-    return launch_chained(k_mls<R>, dim3(mls_blocks(B)), dim3(kMlsThreads), sizeof(MlsSmem<R>), s, (const R *)mom, L,
-                          B, err);
+    const int nvb = mls_blocks(B);
+    return launch_chained(k_mls<R>, dim3(capped(nvb, grid_cap)), dim3(kMlsThreads), sizeof(MlsSmem<R>), s,
+                          (const R *)mom, L, B, err, nvb);
 }
 
 // Kernel attributes that must be set before the first launch (and before
@@ -1554,12 +1571,12 @@ cudaError_t prepare_kernels() {
 }
 
 cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm,
-                            int *err, uint32_t *step_inc, cudaStream_t s) {
+                            int *err, uint32_t *step_inc, int grid_cap, cudaStream_t s) {
     switch (prec) {
-        case 0: return ib_front_t<double, double>(fin, L, B, mom, nsm, err, step_inc, s);
-        case 1: return ib_front_t<float, float>(fin, L, B, mom, nsm, err, step_inc, s);
-        case 2: return ib_front_t<__half, float>(fin, L, B, mom, nsm, err, step_inc, s);
-        default: return ib_front_t<__nv_bfloat16, float>(fin, L, B, mom, nsm, err, step_inc, s);
+        case 0: return ib_front_t<double, double>(fin, L, B, mom, nsm, err, step_inc, grid_cap, s);
+        case 1: return ib_front_t<float, float>(fin, L, B, mom, nsm, err, step_inc, grid_cap, s);
+        case 2: return ib_front_t<__half, float>(fin, L, B, mom, nsm, err, step_inc, grid_cap, s);
+        default: return ib_front_t<__nv_bfloat16, float>(fin, L, B, mom, nsm, err, step_inc, grid_cap, s);
     }
 }
 
@@ -1574,19 +1591,20 @@ static cudaError_t launch_centroid(int prec, const Lattice &L, const BodyView &B
 }
 
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                            const uint32_t *step, cudaStream_t s) {
-    const unsigned g = (unsigned)((B.nv + 7) / 8);  // 8 warps (vertices) per block
+                            const uint32_t *step, int grid_cap, cudaStream_t s) {
+    const int nvb = (B.nv + 7) / 8;  // 8 warps (vertices) per block
+    const unsigned g = (unsigned)capped(nvb, grid_cap);
     if (prec == 0)
-        k_membrane<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
+        k_membrane<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step, nvb);
     else
-        k_membrane<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step);
+        k_membrane<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step, nvb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !B.centroid) return e;
     return launch_centroid(prec, L, B, force, stamp, step, s);
 }
 
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                         const uint32_t *step, cudaStream_t s) {
+                         const uint32_t *step, int grid_cap, cudaStream_t s) {
     const unsigned gf = (unsigned)((B.nt + 255) / 256);
     if (prec == 0)
         k_rigid_forces<double><<<gf, 256, 0, s>>>(B);
@@ -1594,11 +1612,12 @@ cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *fo
         k_rigid_forces<float><<<gf, 256, 0, s>>>(B);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const unsigned g = (unsigned)((B.nv + 7) / 8);
+    const int nvb = (B.nv + 7) / 8;
+    const unsigned g = (unsigned)capped(nvb, grid_cap);
     if (prec == 0)
-        k_rigid_markers<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step);
+        k_rigid_markers<double><<<g, 256, 0, s>>>(L, B, (double *)force, stamp, step, nvb);
     else
-        k_rigid_markers<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step);
+        k_rigid_markers<float><<<g, 256, 0, s>>>(L, B, (float *)force, stamp, step, nvb);
     e = cudaGetLastError();
     if (e != cudaSuccess || !B.centroid) return e;
     return launch_centroid(prec, L, B, force, stamp, step, s);

@@ -67,6 +67,7 @@ struct Ctx {
     cudaStream_t s_hi = nullptr, s_lo = nullptr;  // step streams: IB + box sweep (high priority), far field (low)
     cudaEvent_t ev_fork = nullptr, ev_far = nullptr, ev_near = nullptr, ev_join = nullptr;
     bool split_sweep = true;
+    int ib_per_sm = 0;  // > 0: the IB kernels keep at most this many blocks per SM (lbib_set_ib_blocks)
     bool own_stream = false;
     std::vector<DevBody> bodies;
     uint32_t *d_step = nullptr;  // device step counter (tile flags of the IB force)
@@ -963,7 +964,7 @@ int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external, int 
     for (size_t k = 0; k < c->bodies.size(); ++k) {
         const BodyView v = make_view(c, c->bodies[k]);
         cudaError_t e = launch_ib_front(c->prec, c->fA, c->L, v, c->mom, c->nsm, c->d_err,
-                                        k == 0 ? c->d_step : nullptr, hi);
+                                        k == 0 ? c->d_step : nullptr, c->ib_per_sm * c->nsm, hi);
         c->launches += 2;
         if (e != cudaSuccess) return cuda_fail(c, e, "MLS kernels");
     }
@@ -973,10 +974,10 @@ int enqueue_step(Ctx *c, bool store_fields, cudaEvent_t *ev, bool external, int 
         const BodyView v = make_view(c, b);
         cudaError_t e;
         if (b.rigid) {
-            e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->d_step, hi);
+            e = launch_rigid(c->prec, c->L, v, c->force, c->stamp, c->d_step, c->ib_per_sm * c->nsm, hi);
             c->launches += 2 + v.centroid;
         } else {
-            e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->d_step, hi);
+            e = launch_membrane(c->prec, c->L, v, c->force, c->stamp, c->d_step, c->ib_per_sm * c->nsm, hi);
             c->launches += 1 + v.centroid;
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "structure kernel");
@@ -1453,25 +1454,34 @@ int lbib_autotune(void *h, int steps, int *choice) {
     c->L.sweep_vec = shapes[best_shape][2];
     invalidate_graphs(c);
     // overlap of the far-field sweep with the IB stage, the far-field sweep
-    // on its full grid or on a few resident blocks per SM
-    int overlap = 0, far = 0;
+    // on its full grid or on a few resident blocks per SM, the IB kernels on
+    // their full grids or on one or two resident blocks per SM
+    int overlap = 0, far = 0, ibs = 0;
+    const int saved_ibs = c->ib_per_sm;
+    c->ib_per_sm = 0;
     if (!rc && c->bodies.size() == 1) {
         c->split_sweep = true;
-        for (int fps : {0, 1, 2, 3}) {
-            float ms = 0.f;
-            c->L.far_per_sm = fps;
-            invalidate_graphs(c);
-            if ((rc = trial(&ms))) break;
-            if (ms < best) {
-                best = ms;
-                overlap = 1;
-                far = fps;
+        for (int fps : {0, 1, 2, 3})
+            for (int ib : {0, 1, 2}) {
+                if (rc) break;
+                float ms = 0.f;
+                c->L.far_per_sm = fps;
+                c->ib_per_sm = ib;
+                invalidate_graphs(c);
+                if ((rc = trial(&ms))) break;
+                if (ms < best) {
+                    best = ms;
+                    overlap = 1;
+                    far = fps;
+                    ibs = ib;
+                }
             }
-        }
     } else {
         (void)saved_split;
+        (void)saved_ibs;
     }
     c->L.far_per_sm = far;
+    c->ib_per_sm = ibs;
     c->split_sweep = overlap != 0;
     invalidate_graphs(c);
     cudaEventDestroy(e0);
@@ -1497,6 +1507,27 @@ int lbib_set_sweep_config(void *h, int row_tiles, int block_x, int block_y, int 
     c->L.sweep_bx = block_x;
     c->L.sweep_by = block_y;
     invalidate_graphs(c);
+    return LBIB_OK;
+}
+
+int lbib_set_ib_blocks(void *h, int per_sm) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (per_sm < 0 || per_sm > 64) return fail(c, LBIB_EINVAL, "IB blocks per SM must lie in [0, 64]");
+    if (c->ib_per_sm != per_sm) invalidate_graphs(c);
+    c->ib_per_sm = per_sm;
+    return LBIB_OK;
+}
+
+int lbib_get_launch_config(void *h, int *cfg) {
+    Ctx *c = as_ctx(h);
+    if (!c || !cfg) return LBIB_EINVAL;
+    cfg[0] = c->L.sweep_bx;
+    cfg[1] = c->L.sweep_by;
+    cfg[2] = c->split_sweep ? 1 : 0;
+    cfg[3] = c->L.sweep_vec;
+    cfg[4] = c->L.far_per_sm;
+    cfg[5] = c->ib_per_sm;
     return LBIB_OK;
 }
 

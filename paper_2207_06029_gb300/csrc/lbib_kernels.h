@@ -57,13 +57,15 @@ cudaError_t launch_fields_out(int prec, const void *fields, const Lattice &L, do
 int mls_blocks(const BodyView &B);
 cudaError_t prepare_kernels();
 // step_inc: device step counter incremented at the start of the step (first
-// body only), or nullptr
+// body only), or nullptr.  grid_cap > 0: the MLS, structure and spreading
+// kernels launch at most grid_cap blocks, each taking its share of their
+// blocks' work in turn (0: their full grids)
 cudaError_t launch_ib_front(int prec, const void *fin, const Lattice &L, const BodyView &B, void *mom, int nsm,
-                            int *err, uint32_t *step_inc, cudaStream_t s);
+                            int *err, uint32_t *step_inc, int grid_cap, cudaStream_t s);
 cudaError_t launch_membrane(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                            const uint32_t *step, cudaStream_t s);
+                            const uint32_t *step, int grid_cap, cudaStream_t s);
 cudaError_t launch_rigid(int prec, const Lattice &L, const BodyView &B, void *force, uint32_t *stamp,
-                         const uint32_t *step, cudaStream_t s);
+                         const uint32_t *step, int grid_cap, cudaStream_t s);
 
 // batches (sweep.cu and ib.cu); grid sizes are the totals of the prefix tables
 struct BatchGrid {

@@ -82,6 +82,7 @@ EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_b
            "lbib_set_watchdog", "lbib_check",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_markers_async", "lbib_step_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
+           "lbib_set_ib_blocks", "lbib_get_launch_config",
            "lbib_device_bytes", "lbib_save", "lbib_load", "lbib_mesh_measures_noalloc",
            "lbib_batch_create", "lbib_batch_step", "lbib_batch_sync", "lbib_batch_counters", "lbib_batch_autotune",
            "lbib_batch_set_config", "lbib_batch_set_persistent",
@@ -126,6 +127,8 @@ def load():
         L.lbib_set_overlap.argtypes = [vp, C.c_int]
         L.lbib_set_graphs.argtypes = [vp, C.c_int]
         L.lbib_set_sweep_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.lbib_set_ib_blocks.argtypes = [vp, C.c_int]
+        L.lbib_get_launch_config.argtypes = [vp, ip]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbib_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -326,6 +329,17 @@ def lbib_load(ctx, data):
 def lbib_set_sweep_config(ctx, row_tiles, block_x=0, block_y=0, far_per_sm=0):
     return _check(ctx, load().lbib_set_sweep_config(ctx, int(row_tiles), int(block_x), int(block_y),
                                                     int(far_per_sm)))
+
+
+def lbib_set_ib_blocks(ctx, per_sm):
+    return _check(ctx, load().lbib_set_ib_blocks(ctx, int(per_sm)))
+
+
+def lbib_get_launch_config(ctx):
+    """(block_x, block_y, overlap, row_tiles, far_per_sm, ib_per_sm) in use."""
+    cfg = (C.c_int * 6)()
+    _check(ctx, load().lbib_get_launch_config(ctx, cfg))
+    return tuple(cfg)
 
 
 def lbib_set_graphs(ctx, enable):
