@@ -314,6 +314,10 @@ def run_gpu(args, rank, world, workload=None):
                           stream=stream.cuda_stream)
     p2.alloc, p2.free = alloc_fn, free_fn
     h2 = lbib.lbib_create(p2)
+    # the launch configuration tuned above, through the public setters
+    lbib.lbib_set_sweep_config(h2, tuned[3], tuned[0], tuned[1], tuned[4])
+    lbib.lbib_set_overlap(h2, tuned[2])
+    lbib.lbib_set_ib_blocks(h2, tuned[5])
     L = lbib.load()
     L.lbib_set_fields(h2, C.c_void_p(rho_in.data_ptr()), C.c_void_p(u_in.data_ptr()), 0)
     lbib.lbib_add_body(h2, b.verts, b.tris, lbib.make_body_params(**b.kwargs()))

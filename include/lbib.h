@@ -210,9 +210,11 @@ int lbib_get_markers_async(void *ctx, int body, double *X, double *V, double *F)
  * device by one small kernel queued behind the step (in a context-owned
  * buffer of 3 * nsteps * 3 nv doubles, kept for later calls and grown when
  * needed); the device-to-host copies, one per requested array, are queued
- * after the last step.  The same rules as lbib_get_markers_async apply to
- * the host arrays.  Errors as lbib_step; LBIB_ENOMEM if the staging buffer
- * cannot be allocated. */
+ * after the last step.  The fields are stored as lbib_step(ctx, nsteps)
+ * stores them (lbib_set_output), and steps that store none run from the
+ * step graphs.  The same rules as lbib_get_markers_async apply to the host
+ * arrays.  Errors as lbib_step; LBIB_ENOMEM if the staging buffer cannot be
+ * allocated. */
 int lbib_step_markers(void *ctx, int nsteps, int body, double *X, double *V, double *F);
 
 /* Body summary after the last step.  Synchronises. */

@@ -576,14 +576,15 @@ int lbib_create(const lbib_params *p, void **out) {
         lbib_destroy(c);
         return LBIB_ECUDA;
     }
-    // fluid at rest
-    std::vector<double> rho((size_t)ncell, 1.0), u(3 * (size_t)ncell, 0.0);
-    int rc = lbib_set_fields(c, rho.data(), u.data(), 0);
-    if (rc) {
-        g_create_error = c->msg;
+    // fluid at rest, formed on the device (deviations f - w of zero)
+    e = launch_init_equilibrium(c->prec, c->fA, c->L, nullptr, nullptr, c->fields, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("initial state: ") + cudaGetErrorString(e);
         lbib_destroy(c);
-        return rc;
+        return LBIB_ECUDA;
     }
+    c->launches++;
     *out = c;
     return LBIB_OK;
 }
@@ -1079,12 +1080,9 @@ long long launches_per_step(const Ctx *c) {
     return n;
 }
 
-}  // namespace
-
-extern "C" {
-
-int lbib_step(void *h, int nsteps) {
-    Ctx *c = as_ctx(h);
+// nsteps steps; with fields_every = 0 the fields are stored on the last of
+// them when end_of_call (the last step of a public call)
+int step_steps(Ctx *c, int nsteps, bool end_of_call) {
     if (!c) return LBIB_EINVAL;
     if (c->err) return c->err;
     if (nsteps < 0) return fail(c, LBIB_EINVAL, "nsteps < 0");
@@ -1100,7 +1098,7 @@ int lbib_step(void *h, int nsteps) {
             if (e != cudaSuccess) return cuda_fail(c, e, "step counter reset");
             c->step_host = 1;
         }
-        const bool store = c->fields_every == 0 ? (it == nsteps - 1)
+        const bool store = c->fields_every == 0 ? (end_of_call && it == nsteps - 1)
                                                 : (c->fields_every > 0 && (c->steps + 1) % c->fields_every == 0);
         if (c->use_graphs && !store) {
             if (!c->graphs_valid || c->graphs_timed != c->profile) {
@@ -1147,6 +1145,12 @@ int lbib_step(void *h, int nsteps) {
     }
     return LBIB_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int lbib_step(void *h, int nsteps) { return step_steps(as_ctx(h), nsteps, true); }
 
 int lbib_set_watchdog(void *h, int every, double mass_tol) {
     Ctx *c = as_ctx(h);
@@ -1289,7 +1293,8 @@ int lbib_step_markers(void *h, int nsteps, int body, double *X, double *V, doubl
     // per requested array
     const int blocks = (int)std::min<size_t>((n3 + 255) / 256, 1024);
     for (int k = 0; k < nsteps; ++k) {
-        int rc = lbib_step(h, 1);
+        // one step at a time, the fields stored as lbib_step(h, nsteps) would
+        int rc = step_steps(c, 1, k == nsteps - 1);
         if (rc) return rc;
         DevBody &b = c->bodies[body];
         k_stage_markers<<<blocks, 256, 0, c->stream>>>(X ? b.X[b.cur] : nullptr, V ? b.Ub : nullptr,

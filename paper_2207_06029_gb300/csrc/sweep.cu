@@ -260,9 +260,9 @@ __global__ void k_init_equilibrium(S *__restrict__ fout, Lattice L, const double
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= L.ncell) return;
     // in the arithmetic precision R; the density excess is formed in double
-    // before rounding (rho - 1 is small)
-    const R dr = R(rho[idx] - 1.0), r = R(1) + dr;
-    const R ux = R(u[3 * idx]), uy = R(u[3 * idx + 1]), uz = R(u[3 * idx + 2]);
+    // before rounding (rho - 1 is small); rho and u null: the fluid at rest
+    const R dr = rho ? R(rho[idx] - 1.0) : R(0), r = R(1) + dr;
+    const R ux = u ? R(u[3 * idx]) : R(0), uy = u ? R(u[3 * idx + 1]) : R(0), uz = u ? R(u[3 * idx + 2]) : R(0);
     const R uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
