@@ -124,6 +124,14 @@ typedef struct {
  * an unknown precision or bc; LBIB_ENOMEM / LBIB_ECUDA otherwise. */
 int lbib_create(const lbib_params *p, void **out);
 
+/* Sets the fluid to density 1 and the linear shear profile
+ * u = (u_lo + (u_hi - u_lo) z / (nz - 1), 0, 0), the steady Couette flow
+ * between z walls moving along x at u_lo and u_hi, as equilibrium
+ * populations (Eq. eqfunc) formed on the device (nz = 1: at rest).
+ * Asynchronous on the context stream.  LBIB_EINVAL for non-finite
+ * velocities. */
+int lbib_set_shear_fields(void *ctx, double u_lo, double u_hi);
+
 /* Sets the fluid to equilibrium f = f^eq(rho(x), u(x)) (Eq. eqfunc).
  * rho[ncell], u[3*ncell] (x, y, z per cell), host or device doubles. */
 int lbib_set_fields(void *ctx, const double *rho, const double *u, int on_device);

@@ -612,6 +612,17 @@ void lbib_destroy(void *h) {
     delete c;
 }
 
+int lbib_set_shear_fields(void *h, double u_lo, double u_hi) {
+    Ctx *c = as_ctx(h);
+    if (!c) return LBIB_EINVAL;
+    if (!std::isfinite(u_lo) || !std::isfinite(u_hi)) return fail(c, LBIB_EINVAL, "shear velocities must be finite");
+    cudaError_t e = launch_init_equilibrium(c->prec, c->fA, c->L, nullptr, nullptr, c->fields, c->stream, u_lo, u_hi);
+    c->launches++;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_watch, 0, 2 * sizeof(double), c->stream);  // new reference mass
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    return LBIB_OK;
+}
+
 int lbib_set_fields(void *h, const double *rho, const double *u, int on_device) {
     Ctx *c = as_ctx(h);
     if (!c || !rho || !u) return LBIB_EINVAL;

@@ -46,8 +46,9 @@ int totals_scratch_doubles();
 // error word
 cudaError_t launch_watch(int prec, const void *fin, const Lattice &L, double *part, unsigned int *count, double *w,
                          double tol, int *err, cudaStream_t s);
+// rho and u null: density 1 and u_x = shear_lo + (shear_hi - shear_lo) z / (nz - 1)
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
-                                    void *fields, cudaStream_t s);
+                                    void *fields, cudaStream_t s, double shear_lo = 0.0, double shear_hi = 0.0);
 cudaError_t launch_pop_to_aos(int prec, const void *fin, const Lattice &L, double *out, cudaStream_t s);
 cudaError_t launch_aos_to_pop(int prec, const double *in, const Lattice &L, void *fout, cudaStream_t s);
 cudaError_t launch_fields_out(int prec, const void *fields, const Lattice &L, double *rho, double *u,

@@ -99,23 +99,8 @@ int start_request(Server *s, Request *r) {
     if (rc) return rc;
     if (r->init == 1) {
         // the exact Couette profile between the z walls (x velocity linear in z)
-        const size_t ncell = (size_t)p.nx * p.ny * p.nz;
-        std::vector<double> h(4 * ncell, 0.0);
-        const double ua = p.wall_u[4][0], ub = p.wall_u[5][0];
-        for (int z = 0; z < p.nz; ++z) {
-            const double ux = p.nz > 1 ? ua + (ub - ua) * z / (double)(p.nz - 1) : 0.0;
-            for (size_t k = (size_t)z * p.nx * p.ny; k < (size_t)(z + 1) * p.nx * p.ny; ++k) {
-                h[k] = 1.0;
-                h[ncell + 3 * k] = ux;
-            }
-        }
-        double *d = nullptr;
-        cudaError_t e = cudaMalloc(&d, h.size() * sizeof(double));
-        if (e == cudaSuccess) e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) rc = lbib_set_fields(r->ctx, d, d + ncell, 1);
-        if (e == cudaSuccess && rc == LBIB_OK) rc = lbib_sync(r->ctx);
-        if (d) cudaFree(d);
-        if (e != cudaSuccess) rc = LBIB_ECUDA;
+        rc = lbib_set_shear_fields(r->ctx, p.wall_u[4][0], p.wall_u[5][0]);
+        if (rc == LBIB_OK) rc = lbib_sync(r->ctx);
         if (rc) return rc;
     }
     for (ReqBody &rb : r->bodies) {

@@ -254,15 +254,22 @@ __global__ void __launch_bounds__(512) kb_sweep(BatchTables T, int phase, int st
 }
 
 // f = f^eq(rho, u) from double fields (Eq. eqfunc), stored as deviations.
+// rho and u null: density 1 and the linear shear profile u_x = lo + (hi -
+// lo) z / (nz - 1) (the fluid at rest for lo = hi = 0).
 template <typename S, typename R>
 __global__ void k_init_equilibrium(S *__restrict__ fout, Lattice L, const double *__restrict__ rho,
-                                   const double *__restrict__ u, R *__restrict__ fields) {
+                                   const double *__restrict__ u, R *__restrict__ fields, double lo, double hi) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= L.ncell) return;
     // in the arithmetic precision R; the density excess is formed in double
-    // before rounding (rho - 1 is small); rho and u null: the fluid at rest
+    // before rounding (rho - 1 is small)
+    double sx = 0.0;
+    if (!u && L.nz > 1) {
+        const int z = idx / (L.nx * L.ny);
+        sx = lo + (hi - lo) * z / (double)(L.nz - 1);
+    }
     const R dr = rho ? R(rho[idx] - 1.0) : R(0), r = R(1) + dr;
-    const R ux = u ? R(u[3 * idx]) : R(0), uy = u ? R(u[3 * idx + 1]) : R(0), uz = u ? R(u[3 * idx + 2]) : R(0);
+    const R ux = u ? R(u[3 * idx]) : R(sx), uy = u ? R(u[3 * idx + 1]) : R(0), uz = u ? R(u[3 * idx + 2]) : R(0);
     const R uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -589,15 +596,16 @@ cudaError_t prepare_sweep_kernels() {
 }
 
 cudaError_t launch_init_equilibrium(int prec, void *fout, const Lattice &L, const double *rho, const double *u,
-                                    void *fields, cudaStream_t s) {
+                                    void *fields, cudaStream_t s, double shear_lo, double shear_hi) {
     const unsigned g = grid_for(L.ncell, 256);
+    const double a = shear_lo, b = shear_hi;
     switch (prec) {
-        case 0: k_init_equilibrium<double, double><<<g, 256, 0, s>>>((double *)fout, L, rho, u, (double *)fields); break;
-        case 1: k_init_equilibrium<float, float><<<g, 256, 0, s>>>((float *)fout, L, rho, u, (float *)fields); break;
-        case 2: k_init_equilibrium<__half, float><<<g, 256, 0, s>>>((__half *)fout, L, rho, u, (float *)fields); break;
+        case 0: k_init_equilibrium<double, double><<<g, 256, 0, s>>>((double *)fout, L, rho, u, (double *)fields, a, b); break;
+        case 1: k_init_equilibrium<float, float><<<g, 256, 0, s>>>((float *)fout, L, rho, u, (float *)fields, a, b); break;
+        case 2: k_init_equilibrium<__half, float><<<g, 256, 0, s>>>((__half *)fout, L, rho, u, (float *)fields, a, b); break;
         default:
             k_init_equilibrium<__nv_bfloat16, float><<<g, 256, 0, s>>>((__nv_bfloat16 *)fout, L, rho, u,
-                                                                      (float *)fields);
+                                                                      (float *)fields, a, b);
     }
     return cudaGetLastError();
 }

@@ -78,7 +78,7 @@ class LbibError(RuntimeError):
 _lock = threading.Lock()
 _lib = None
 
-EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
+EXPORTS = ["lbib_create", "lbib_set_fields", "lbib_set_shear_fields", "lbib_set_populations", "lbib_add_body", "lbib_step", "lbib_sync",
            "lbib_set_watchdog", "lbib_check",
            "lbib_get_fields", "lbib_get_populations", "lbib_get_totals", "lbib_get_markers", "lbib_get_markers_async", "lbib_step_markers", "lbib_get_body", "lbib_counters",
            "lbib_profile", "lbib_get_profile", "lbib_set_output", "lbib_set_overlap", "lbib_set_graphs", "lbib_set_sweep_config", "lbib_autotune",
@@ -128,6 +128,7 @@ def load():
         L.lbib_set_graphs.argtypes = [vp, C.c_int]
         L.lbib_set_sweep_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.lbib_set_ib_blocks.argtypes = [vp, C.c_int]
+        L.lbib_set_shear_fields.argtypes = [vp, C.c_double, C.c_double]
         L.lbib_get_launch_config.argtypes = [vp, ip]
         L.lbib_autotune.argtypes = [vp, C.c_int, ip]
         L.lbib_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
@@ -329,6 +330,10 @@ def lbib_load(ctx, data):
 def lbib_set_sweep_config(ctx, row_tiles, block_x=0, block_y=0, far_per_sm=0):
     return _check(ctx, load().lbib_set_sweep_config(ctx, int(row_tiles), int(block_x), int(block_y),
                                                     int(far_per_sm)))
+
+
+def lbib_set_shear_fields(ctx, u_lo, u_hi):
+    return _check(ctx, load().lbib_set_shear_fields(ctx, float(u_lo), float(u_hi)))
 
 
 def lbib_set_ib_blocks(ctx, per_sm):

@@ -390,6 +390,28 @@ def test_ib_block_cap_keeps_parity(lbib, rigid):
         check_fp64(runs[1], run_oracle(case, 10))
 
 
+@pytest.mark.parametrize("prec,tol", [(W.PREC_FP64, 1e-15), (W.PREC_FP32, 1e-7)])
+def test_shear_fields_are_the_couette_equilibrium(lbib, prec, tol):
+    """lbib_set_shear_fields forms on the device the equilibrium of the
+    linear shear profile between the z walls, the same populations as
+    setting that profile as host fields; the state is then the exact
+    discrete steady state (100 steps leave it within rounding)."""
+    n, U = (6, 5, 24), 0.01
+    a = lbib.Context(n, 0.8, bc=(0, 0, 1), wall_u=W.shear_walls(U), precision=prec)
+    lbib.lbib_set_shear_fields(a.h, -U, U)
+    b = lbib.Context(n, 0.8, bc=(0, 0, 1), wall_u=W.shear_walls(U), precision=prec)
+    b.set_fields(np.ones(n[0] * n[1] * n[2]), W.couette_profile(n, U))
+    fa, fb = a.populations(), b.populations()
+    assert rel(fa, fb) < tol
+    a.step(100)
+    _, u = a.fields()
+    assert np.abs(u - W.couette_profile(n, U)).max() < 100 * tol * U
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_set_shear_fields(a.h, float("nan"), U)
+    a.close()
+    b.close()
+
+
 # ---------------------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------------------
