@@ -10,7 +10,6 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/lbib.h"
@@ -699,28 +698,38 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     b.nt = nt;
     b.rigid = bp->rigid ? 1 : 0;
     b.p = *bp;
-    // hinges: one per undirected edge a<b, T1 holds a->b, T2 holds b->a
-    std::unordered_map<unsigned long long, std::pair<int, int>> dir;  // (a,b) -> (triangle, third vertex)
-    dir.reserve((size_t)3 * nt * 2);
-    for (int t = 0; t < nt; ++t)
-        for (int s = 0; s < 3; ++s) {
-            const int a = tris[3 * t + s], bb = tris[3 * t + (s + 1) % 3], cc = tris[3 * t + (s + 2) % 3];
-            const unsigned long long key = (unsigned long long)a * (unsigned long long)nv + (unsigned long long)bb;
-            if (!dir.emplace(key, std::make_pair(t, cc)).second)
-                return fail(c, LBIB_EINVAL, "mesh has a repeated directed edge (not an oriented manifold)");
-        }
+    // hinges: one per undirected edge a<b, T1 holds a->b, T2 holds b->a.
+    // The directed edges leaving each vertex, in triangle order (a CSR table
+    // built by counting); an edge's twin is found among the few edges
+    // leaving its end vertex.
+    std::vector<int> out_ptr(nv + 1, 0);
+    for (int k = 0; k < 3 * nt; ++k) out_ptr[tris[k] + 1]++;
+    for (int v = 0; v < nv; ++v) out_ptr[v + 1] += out_ptr[v];
+    std::vector<int> out_edge(3 * (size_t)nt);  // directed edge id 3 t + s (from corner s of t to corner s+1)
+    {
+        std::vector<int> fill(out_ptr.begin(), out_ptr.end() - 1);
+        for (int t = 0; t < nt; ++t)
+            for (int s = 0; s < 3; ++s) out_edge[fill[tris[3 * t + s]]++] = 3 * t + s;
+    }
+    auto edge_to = [&](int e) { return tris[3 * (e / 3) + (e % 3 + 1) % 3]; };
+    for (int v = 0; v < nv; ++v)
+        for (int p = out_ptr[v]; p < out_ptr[v + 1]; ++p)
+            for (int q = out_ptr[v]; q < p; ++q)
+                if (edge_to(out_edge[p]) == edge_to(out_edge[q]))
+                    return fail(c, LBIB_EINVAL, "mesh has a repeated directed edge (not an oriented manifold)");
     std::vector<int4> hinge;
     std::vector<int> htri;
     for (int t = 0; t < nt; ++t)
         for (int s = 0; s < 3; ++s) {
             const int a = tris[3 * t + s], bb = tris[3 * t + (s + 1) % 3];
-            const unsigned long long rkey = (unsigned long long)bb * nv + (unsigned long long)a;
-            auto it = dir.find(rkey);
-            if (it == dir.end()) return fail(c, LBIB_EINVAL, "mesh is not closed (edge without a twin)");
+            int twin = -1;  // the edge bb -> a
+            for (int p = out_ptr[bb]; p < out_ptr[bb + 1]; ++p)
+                if (edge_to(out_edge[p]) == a) twin = out_edge[p];
+            if (twin < 0) return fail(c, LBIB_EINVAL, "mesh is not closed (edge without a twin)");
             if (a < bb) {
-                hinge.push_back(make_int4(a, bb, tris[3 * t + (s + 2) % 3], it->second.second));
+                hinge.push_back(make_int4(a, bb, tris[3 * t + (s + 2) % 3], tris[3 * (twin / 3) + (twin % 3 + 2) % 3]));
                 htri.push_back(t);
-                htri.push_back(it->second.first);
+                htri.push_back(twin / 3);
             }
         }
     const int nh = (int)hinge.size();
@@ -750,22 +759,30 @@ int lbib_add_body(void *h, const double *verts, int nv, const int *tris, int nt,
     b.mv = bp->mass_model == 1 ? bp->density_ratio * V0 / nv : bp->density_ratio * bp->thickness * A0 / nv;
     for (int v = 0; v < nv; ++v)
         for (int a = 0; a < 3; ++a) b.origin[a] += verts[3 * v + a] / nv;
-    // vertex -> (hinge, role) and vertex -> (triangle, corner) lists
-    std::vector<std::vector<int>> vh(nv), vt(nv);
+    // vertex -> (hinge, role) and vertex -> (triangle, corner) lists (CSR by
+    // counting; each vertex's entries in increasing hinge or triangle order)
+    std::vector<int> vh_ptr(nv + 1, 0), vt_ptr(nv + 1, 0);
     for (int h2 = 0; h2 < nh; ++h2) {
-        vh[hinge[h2].x].push_back(4 * h2 + 0);
-        vh[hinge[h2].y].push_back(4 * h2 + 1);
-        vh[hinge[h2].z].push_back(4 * h2 + 2);
-        vh[hinge[h2].w].push_back(4 * h2 + 3);
+        vh_ptr[hinge[h2].x + 1]++;
+        vh_ptr[hinge[h2].y + 1]++;
+        vh_ptr[hinge[h2].z + 1]++;
+        vh_ptr[hinge[h2].w + 1]++;
     }
-    for (int t = 0; t < nt; ++t)
-        for (int q = 0; q < 3; ++q) vt[tris[3 * t + q]].push_back(3 * t + q);
-    std::vector<int> vh_ptr(nv + 1, 0), vt_ptr(nv + 1, 0), vh_list, vt_list;
+    for (int k = 0; k < 3 * nt; ++k) vt_ptr[tris[k] + 1]++;
     for (int v = 0; v < nv; ++v) {
-        vh_ptr[v + 1] = vh_ptr[v] + (int)vh[v].size();
-        vt_ptr[v + 1] = vt_ptr[v] + (int)vt[v].size();
-        vh_list.insert(vh_list.end(), vh[v].begin(), vh[v].end());
-        vt_list.insert(vt_list.end(), vt[v].begin(), vt[v].end());
+        vh_ptr[v + 1] += vh_ptr[v];
+        vt_ptr[v + 1] += vt_ptr[v];
+    }
+    std::vector<int> vh_list((size_t)vh_ptr[nv]), vt_list((size_t)vt_ptr[nv]);
+    {
+        std::vector<int> fh(vh_ptr.begin(), vh_ptr.end() - 1), ft(vt_ptr.begin(), vt_ptr.end() - 1);
+        for (int h2 = 0; h2 < nh; ++h2) {
+            vh_list[fh[hinge[h2].x]++] = 4 * h2 + 0;
+            vh_list[fh[hinge[h2].y]++] = 4 * h2 + 1;
+            vh_list[fh[hinge[h2].z]++] = 4 * h2 + 2;
+            vh_list[fh[hinge[h2].w]++] = 4 * h2 + 3;
+        }
+        for (int k = 0; k < 3 * nt; ++k) vt_list[ft[tris[k]]++] = k;
     }
     int rc = 0;
     std::vector<double> X(verts, verts + 3 * (size_t)nv);

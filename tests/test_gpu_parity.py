@@ -629,3 +629,20 @@ def test_plane_offsets_at_the_32_bit_limit(lbib, nz):
     assert torch.equal(u_b, want_u)
     del u_b, want_u
     torch.cuda.empty_cache()
+
+
+def test_add_body_rejects_meshes_that_are_not_closed_oriented_manifolds(lbib):
+    """The hinge set-up needs every directed edge once and its twin: an
+    open mesh, a repeated triangle (its directed edges twice) and an inward
+    orientation (negative enclosed volume) are LBIB_EINVAL, and the context
+    stays usable."""
+    v, f = W.icosphere(2, 4.0, (8.0, 8.0, 8.0))
+    ctx = lbib.Context((16, 16, 16), 0.8, precision=lbib.LBIB_FP64)
+    for bad in (f[1:], np.concatenate([f, f[:1]]), f[:, ::-1].copy()):
+        with pytest.raises(lbib.LbibError) as ei:
+            ctx.add_body(v, bad, **W.Body(v, bad, ks0=1e-3, ref_radius=4.0).kwargs())
+        assert ei.value.code == lbib.LBIB_EINVAL
+    ctx.add_body(v, f, **W.Body(v, f, ks0=1e-3, ref_radius=4.0).kwargs())
+    ctx.step(2)
+    assert np.isfinite(ctx.markers(0)[0]).all()
+    ctx.close()
