@@ -979,18 +979,25 @@ __device__ __forceinline__ void rigid_forces_body(const BodyView &B, const int v
         s_last = atomicAdd(B.vol_count, 1u) == (unsigned)nvb - 1;
     }
     __syncthreads();
-    if (!s_last || warp != 0) return;
+    if (!s_last) return;
     __threadfence();
-    // totals: lane q < 6 sums partial q over the blocks in block order
-    if (lane < 6) {
+    // totals: warp q < 6 sums partial q over the blocks, lane l taking blocks
+    // l, l + 32, ... and the warp's fixed butterfly adding the lanes
+    // (deterministic whichever block is last)
+    if (warp < 6) {
         double acc = 0.0;
-        for (int b = 0; b < nvb; ++b) acc += __ldcg(B.vol_part + 6 * b + lane);
-        if (lane < 3) acc += (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + lane];
-        // momentum exchange: the fluid inside moves with the body, rho_f V du/dt
-        if (lane < 3 && B.rigid_force)
-            acc += S[RigidState::VOL] * (S[RigidState::U + lane] - S[RigidState::UP + lane]);
-        sF[lane] = acc;
+        for (int b = lane; b < nvb; b += 32) acc += __ldcg(B.vol_part + 6 * b + warp);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            if (warp < 3) acc += (S[RigidState::DENS] - 1.0) * S[RigidState::VOL] * S[RigidState::GRAV + warp];
+            // momentum exchange: the fluid inside moves with the body, rho_f V du/dt
+            if (warp < 3 && B.rigid_force)
+                acc += S[RigidState::VOL] * (S[RigidState::U + warp] - S[RigidState::UP + warp]);
+            sF[warp] = acc;
+        }
     }
+    __syncthreads();
+    if (warp != 0) return;
     if (lane == 0) *B.vol_count = 0u;
     __syncwarp();
     const double *q = S + RigidState::Q4;
