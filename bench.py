@@ -474,28 +474,28 @@ def batch_leg(args):
 SERVE_STREAMS = {
     # the serving configuration as stated: Poisson 4/s, cubic N 32..192,
     # 2000..30000 steps, capsules (N >= 48) in the validated parameter box
-    "baseline": dict(count=64, seed=4, rate=4.0, n_range=(32, 192), step_range=(2000, 30000)),
+    "stated": dict(count=64, seed=4, rate=4.0, n_range=(32, 192), step_range=(2000, 30000)),
     # the same stream with the capsule parameter box as stated (Ca 0.005..0.3,
     # Eb 0..0.05, mass ratio 0.5/1/2) and capsules from N = 32: runs that
     # diverge fail with LBIB_EDIVERGED and leave the batch
-    "baseline_full": dict(count=64, seed=4, rate=4.0, n_range=(32, 192), step_range=(2000, 30000),
+    "stated_full": dict(count=64, seed=4, rate=4.0, n_range=(32, 192), step_range=(2000, 30000),
                           capsule_min_n=32),
     # many small lattices, where one run alone leaves the GPU idle
     "small": dict(count=64, seed=9, rate=40.0, n_range=(32, 64), step_range=(500, 2000)),
 }
 
 
-def serve_leg(args, mode, precision, max_active=64, batch_cells=0, stream_kind="baseline", batch_order=0):
+def serve_leg(args, mode, precision, max_active=64, batch_cells=0, stream_kind="stated", batch_order=0):
     """A seeded Poisson stream of capsule-in-shear and settling-sphere runs
     through the serving engine; latency from submission to completion.  The
     step counts of the stated streams are scaled by args.serve_steps_scale."""
     from paper_2207_06029_gb300 import lbib
     from paper_2207_06029_gb300 import workloads as W
     kw = dict(SERVE_STREAMS[stream_kind])
-    if stream_kind.startswith("baseline"):
+    if stream_kind.startswith("stated"):
         scale = getattr(args, "serve_steps_scale", 1.0)
         kw["step_range"] = tuple(max(1, int(round(scale * x))) for x in kw["step_range"])
-    if stream_kind == "baseline_full":
+    if stream_kind == "stated_full":
         kw.update(Ca_range=W.FULL_CA, Eb_range=W.FULL_EB, mass_ratios=W.FULL_MASS_RATIOS)
     stream = W.serve_stream(precision=precision, **kw)
     server = lbib.lbib_serve_create(hbm_budget=150 << 30, chunk_steps=500, max_active=max_active, mode=mode,
@@ -756,7 +756,7 @@ def main():
     if args.serve and rank == 0 and world == 1:
         from paper_2207_06029_gb300 import lbib
         from paper_2207_06029_gb300 import workloads as W
-        lo, hi = (max(1, int(round(args.serve_steps_scale * x))) for x in SERVE_STREAMS["baseline"]["step_range"])
+        lo, hi = (max(1, int(round(args.serve_steps_scale * x))) for x in SERVE_STREAMS["stated"]["step_range"])
         stream = (f"64 requests, Poisson 4/s, half capsule-in-shear half settling sphere, cubic N~U{{32..192}}, "
                   f"steps~U{{{lo}..{hi}}} (the stated 2000..30000 x {args.serve_steps_scale:g}), budget 150 GB")
         line["serve"] = {
@@ -770,7 +770,7 @@ def main():
                                         "mass ratio 0.5/1/2): diverging runs fail with LBIB_EDIVERGED (-4)",
             "full_box_batched_fp32_oldest_1M": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32,
                                                          batch_cells=1 << 20, batch_order=lbib.LBIB_SERVE_OLDEST,
-                                                         stream_kind="baseline_full"),
+                                                         stream_kind="stated_full"),
             "small_stream": "64 requests, Poisson 40/s, same mix, cubic N~U{32..64} (capsules 48..64), "
                             "steps~U{500..2000}",
             "small_batched_fp32": serve_leg(args, lbib.LBIB_SERVE_BATCHED, W.PREC_FP32, stream_kind="small"),
