@@ -154,7 +154,7 @@ struct MlsSmem {
     // (with kShfl the offsets x_k - X are formed again from fracR instead)
     R W[kPts][27];
     R d[kShfl ? 1 : kPts][27][3];
-    // per point: A = sum W p p^T, b_f = sum W p f for f = rho - 1, u_x, u_y, u_z
+    // per point: A = sum W p p^T, b_f = sum W p (f - f_c) for f = rho - 1, u_x, u_y, u_z
     R sums[kPts][kSums];
     R ref[kPts][4];   // the fitted fields at the support's centre node (the fits are of f - ref)
     R row0[kPts][4];  // first row of A^-1
@@ -307,11 +307,11 @@ __device__ __forceinline__ double dist2_exact(double a, double b, double c) {
 //           nearest node base = floor(X + 1/2) and the exact offset X - base;
 //  phase 1: one warp per point, one lane per support node: weight
 //           W = exp(-(r/alpha)^2) for r <= 1 (the cut-off decided exactly as
-//           in FP64), node moments less those of the centre node, the 26
-//           products W p p^T and W p f, summed over the nodes;
+//           in FP64), node moments less those of the centre node f_c, the
+//           26 products W p p^T and W p (f - f_c), summed over the nodes;
 //  phase 2: one lane per point: inverse of A (FP64 adjugate in the FP64
 //           path, FP32 Cholesky in the FP32 one); markers get
-//           U = (A^-1 b_u)_0 (Eq. uLag), probes the pressure c_s^2 rho and
+//           U = (A^-1 b_u)_0 + u_c (Eq. uLag), probes the pressure c_s^2 rho and
 //           the traction rho nu (grad u + grad u^T) . n from the fits;
 //  phase 3: markers keep phi_k = W_k (A^-1 p_k)_0 for spreading.
 template <typename R, bool kCG = false, bool kShfl = false>
